@@ -1,0 +1,191 @@
+/*
+ * tdvp.h -- C ABI of the B300 one-site TDVP projector-splitting (TDVP-PS) library.
+ *
+ * The library advances matrix product states (MPS) of Frenkel-Holstein chains in
+ * time with the one-site TDVP-PS integrator of Li, Ren, Shuai (arXiv:1907.12044,
+ * Sec. II.A.2 "TDVP-PS"): every time step is the symmetric second-order split of
+ * Eq. ps_trotter, i.e. a left-to-right half sweep with tau/2 (forward site
+ * evolution Eq. tdvp2_C, QR gauge shift Eq. QR, backward bond evolution
+ * Eq. tdvp2_D, absorption C_{i+1} = D_i R_{i+1}), the last site with tau, and the
+ * mirror right-to-left half sweep.  Each local exponential is a Lanczos Krylov
+ * exponential.  All arithmetic of a step runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: TDVP_OK (0) or a negative TDVP_ERR_* code.  No C++ exception
+ *    crosses the ABI.  tdvp_last_error() gives a message for the last failure.
+ *  - Host arrays passed in are owned by the caller and copied before return.
+ *  - The context owns all device memory it allocates (cudaMalloc on the device
+ *    given at creation) and frees it in tdvp_destroy().
+ *  - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  Entry points that return host data
+ *    synchronise that stream; tdvp_ps_step() may synchronise it to read Krylov
+ *    convergence flags.
+ *  - Complex numbers are interleaved (re, im) doubles.  A site tensor A[l][s][r]
+ *    of bond dims (Dl, Dr) and local dimension d is stored row-major with r
+ *    fastest: element (l, s, r) at offset 2*((l*d + s)*Dr + r).
+ *  - Units: energies and frequencies in cm^-1, times in fs (hbar = 1, phase
+ *    2*pi*c*E*t with 2*pi*c = 1.883651567e-4 rad/(cm^-1 fs)).
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef TDVP_H
+#define TDVP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdvp_ctx tdvp_ctx;
+
+/* Frenkel-Holstein Hamiltonian, Eq. holstein (Sec. II.C):
+ *   H = sum_m (E_m - energy_offset) n_m + sum_{m!=n} J_mn a_m^+ a_n
+ *     + sum_{m,l} w_ml (b^+ b [+ 1/2 if include_zpe])
+ *     + sum_{m,l} g_ml w_ml (b^+ + b) n_m
+ * Electronic sites are two-level (|0>, |1>); mode (m, l) has n_levels levels.
+ * Chain order: for m in el_order, electronic site m followed by its modes in the
+ * order given (the paper's layout, Sec. II.C).  All pointers are host memory. */
+typedef struct {
+  int n_el;                /* number of electronic sites, >= 1 */
+  const double* E;         /* [n_el] site energies (cm^-1) */
+  const double* J;         /* [n_el*n_el] row-major couplings (cm^-1); must be symmetric; diagonal ignored */
+  const int* n_modes;      /* [n_el] number of modes attached to each electronic site */
+  const double* omega;     /* [sum n_modes] mode frequencies (cm^-1), site 0's modes first */
+  const double* g;         /* [sum n_modes] dimensionless couplings (Huang-Rhys S = g^2) */
+  const int* n_levels;     /* [sum n_modes] phonon levels of each mode, >= 1 */
+  const int* el_order;     /* [n_el] permutation of 0..n_el-1: chain order of electronic sites */
+  double energy_offset;    /* subtracted from every E_m (keeps the shifted spectrum small) */
+  int include_zpe;         /* 1: add w/2 per mode; 0: omit the zero-point constant */
+} tdvp_fh_params;
+
+/* Status codes. */
+#define TDVP_OK                        0
+#define TDVP_ERR_INVALID_ARG          -1  /* bad size, pointer, index or mismatched structure */
+#define TDVP_ERR_CUDA                 -2  /* a CUDA runtime call failed */
+#define TDVP_ERR_OOM                  -3  /* cudaMalloc failed */
+#define TDVP_ERR_KRYLOV_NOT_CONVERGED -4  /* Lanczos hit k_max above the tolerance (result still written) */
+#define TDVP_ERR_DEVICE_TIMEOUT       -5  /* a bounded device-side wait gave up */
+#define TDVP_ERR_NAN                  -6  /* a non-finite norm was met */
+#define TDVP_ERR_STATE                -7  /* call out of order (e.g. step before init) */
+
+/* Arithmetic of the contractions (H_eff.A, zero-site H0.D, environments). */
+#define TDVP_PREC_FP64   0   /* complex double on the FP64 pipe */
+
+/* Krylov dimension control. */
+#define TDVP_KRYLOV_ADAPTIVE 0   /* grow k until the a-posteriori estimate meets the tolerance */
+
+/* Create a context on CUDA device `device` working on `cuda_stream`, holding
+ * `n_realisations` independent trajectories (>= 1) that share one chain layout,
+ * with at most `kmax` (1..128) Krylov vectors per local exponential. */
+int tdvp_create(tdvp_ctx** ctx, int device, void* cuda_stream, int n_realisations, int kmax);
+
+/* Build the MPO of Eq. holstein (Eq. mpo, finite-state construction with bond
+ * dimension 2 + 2*min(k_left, k_right) (+1 inside a mode block), k = electronic
+ * sites on each side) for realisation r and upload it.  Every realisation must
+ * have the same chain layout (n_el, modes, levels, order); values may differ. */
+int tdvp_build_mpo(tdvp_ctx* ctx, int r, const tdvp_fh_params* p);
+
+/* Initial state of Sec. II.C for realisation r: exciton on electronic site
+ * `exciton_site`, every mode in its ground level, embedded at bond dims
+ * D_b = min(D, prod d left, prod d right).  Site i viewed as a Dl x (d*Dr)
+ * matrix gets row 0 = the occupied path and rows j >= 1 = the standard basis
+ * vectors at the successive (s, r) positions other than (occupied, 0), ordered by
+ * r first and s second, which makes it right-canonical (Eq. rcanon).  Builds all right
+ * environments h[i+1:N] (Eq. tdvp1_hiN).  Requires tdvp_build_mpo first. */
+int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site);
+
+/* Explicit initial tensors for realisation r: bond_dims[0..N] (bond_dims[0] =
+ * bond_dims[N] = 1) and re_im = all site tensors concatenated in site order,
+ * each in the layout above.  The state is right-canonicalised on the device by
+ * LQ from the last site (Eq. QR, "RQ" direction), normalised, and the right
+ * environments are built. */
+int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const double* re_im);
+
+/* Advance every realisation by n_steps steps of dt_fs with Eq. ps_trotter.
+ * precision: TDVP_PREC_*; krylov_mode: TDVP_KRYLOV_*; krylov_tol: absolute
+ * tolerance on the a-posteriori Lanczos estimate ||v|| beta_k |[exp(zT_k)e_1]_k|
+ * (e.g. 1e-12).  On return the state is right-canonical with the centre at site 0.
+ * Returns TDVP_ERR_KRYLOV_NOT_CONVERGED if some exponential stopped at kmax (the
+ * step is still complete). */
+int tdvp_ps_step(tdvp_ctx* ctx, double dt_fs, int n_steps, int precision, int krylov_mode,
+                 double krylov_tol);
+
+/* Observables of realisation r (synchronises the stream):
+ *   pops[n_el]: exciton populations P^(n) = <n_n>/<Psi|Psi> by electronic label (Eq. error);
+ *   energy: <Psi|H|Psi>/<Psi|Psi> in the shifted frame (cm^-1);  norm: ||Psi||.
+ * Any output pointer may be NULL. */
+int tdvp_observables(tdvp_ctx* ctx, int r, double* pops, double* energy, double* norm);
+
+/* Chain layout: n_sites; phys_dims[n_sites]; bond_dims[n_sites+1] of realisation
+ * r; mpo_dims[n_sites+1].  Array pointers may be NULL. */
+int tdvp_chain_info(tdvp_ctx* ctx, int r, int* n_sites, int* phys_dims, int* bond_dims,
+                    int* mpo_dims);
+
+/* Copy site tensor i of realisation r to the host (Dl*d*Dr complex, layout above). */
+int tdvp_get_site(tdvp_ctx* ctx, int r, int i, double* re_im);
+
+/* Move the gauge centre of realisation r from site 0 to site `site` by QR
+ * (Eq. QR) and build the left environments h[1:i-1] on the way; the state must
+ * have its centre at site 0 (after init or a step).  Used to probe H_eff at
+ * interior sites.  Call tdvp_center_to_zero() before the next tdvp_ps_step(). */
+int tdvp_move_center(tdvp_ctx* ctx, int r, int site);
+int tdvp_center_to_zero(tdvp_ctx* ctx, int r);
+
+/* y = H[i] x for the effective Hamiltonian of Eq. tdvp1_H at site i of
+ * realisation r, with the stored environments (valid at the current centre).
+ * x, y: host arrays of Dl*d*Dr complex. */
+int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, const double* x, double* y);
+
+/* Gauge-shift decomposition of Eq. QR on the device, exposed for testing:
+ * C (m x n, m >= n, row-major complex, host) = Q R with Q orthonormal columns
+ * and R upper triangular; rank-deficient columns (residual <= rtol*||C||_F after
+ * two Gram-Schmidt passes) get R[j][j] = 0 and Q[:,j] completed from the first
+ * standard basis vector at distance >= 1/2 from the span so far. */
+int tdvp_debug_qr(tdvp_ctx* ctx, int m, int n, const double* C, double* Q, double* R);
+
+/* Lanczos exponential exp(z H) v with H = H[i] of realisation r at the current
+ * centre (same requirements as tdvp_apply_heff), z = z_re + i z_im.  Exposed for
+ * testing; k_out receives the Krylov dimension used. */
+int tdvp_debug_expm(tdvp_ctx* ctx, int r, int i, double z_re, double z_im, double tol,
+                    const double* v, double* out, int* k_out);
+
+/* Kernel categories of the optional per-launch timing (tdvp_set_profiling). */
+#define TDVP_CAT_GEMM    0   /* contraction GEMMs: H_eff stages 1/3, environments, H0, absorption */
+#define TDVP_CAT_WAPPLY  1   /* sparse MPO middle stage of H_eff and the environments */
+#define TDVP_CAT_LZVEC   2   /* Lanczos orthogonalisation (dots, two Gram-Schmidt passes), start, combination */
+#define TDVP_CAT_TRIDIAG 3   /* tridiagonal exponential, convergence test, next Krylov vector */
+#define TDVP_CAT_QR      4   /* gauge-shift QR/LQ and its transposes */
+#define TDVP_CAT_OTHER   5
+#define TDVP_NCAT        6
+
+typedef struct {
+  long long steps;             /* completed time steps (per realisation) */
+  long long site_updates;      /* forward site evolutions, all realisations (2N-1 per step each) */
+  long long matvecs;           /* H_eff and H0 applications, all realisations */
+  long long krylov_solves;     /* local exponentials */
+  long long krylov_dim_sum;    /* sum of Krylov dimensions over those solves */
+  int krylov_dim_max;
+  long long host_syncs;        /* stream synchronisations made inside tdvp_ps_step */
+  long long kernel_launches;   /* kernels enqueued by this context */
+  long long not_converged;     /* solves that stopped at kmax above tolerance */
+  /* filled only while profiling is on: per category, summed CUDA-event time of each launch
+   * (recorded on the context stream right before and after it), launch count, and the
+   * algorithmic real flops of the contraction GEMMs (8 per complex multiply-add). */
+  double prof_ms[TDVP_NCAT];
+  long long prof_launches[TDVP_NCAT];
+  double prof_flops[TDVP_NCAT];
+} tdvp_stats_t;
+
+/* Turn per-launch CUDA-event timing on (1) or off (0).  While on, every kernel launch is
+ * bracketed by two events on the context stream; the times are collected into tdvp_stats at
+ * the end of each tdvp_ps_step (which then synchronises the stream). */
+int tdvp_set_profiling(tdvp_ctx* ctx, int on);
+
+int tdvp_stats(tdvp_ctx* ctx, tdvp_stats_t* out);
+void tdvp_reset_stats(tdvp_ctx* ctx);
+
+const char* tdvp_last_error(const tdvp_ctx* ctx);
+void tdvp_destroy(tdvp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDVP_H */

@@ -15,23 +15,42 @@ from .linalg import lq_rr
 
 
 def heff_apply(L, W, R, A):
-    """H[i] C of Eq. tdvp2_C with H[i] from Eq. tdvp1_H: sum L W A R."""
-    return np.einsum("xwa,wvts,asb,yvb->xty", L, W, A, R, optimize=True)
+    """H[i] C of Eq. tdvp2_C with H[i] from Eq. tdvp1_H, contracted stage by stage.
+
+    T1[x,w,s,b] = sum_a L[x,w,a] A[a,s,b]; T2 = sum_{w,s} T1 W[w,v,t,s];
+    out[x,t,y] = sum_{v,b} T2[x,b,v,t] R[y,v,b].
+    """
+    T1 = np.tensordot(L, A, axes=(2, 0))                    # [x, w, s, b]
+    T2 = np.tensordot(T1, W, axes=([1, 2], [0, 3]))         # [x, b, v, t]
+    return np.tensordot(T2, R, axes=([1, 2], [2, 1]))       # [x, t, y]
 
 
 def h0_apply(L, R, D):
-    """Zero-site Hamiltonian of Eq. tdvp2_D: sum_w h[1:i]_w D h[i+1:N]_w^T."""
-    return np.einsum("xwa,ab,ywb->xy", L, D, R, optimize=True)
+    """Zero-site Hamiltonian of Eq. tdvp2_D: out[x,y] = sum_{w,a,b} L[x,w,a] D[a,b] R[y,w,b]."""
+    T = np.tensordot(L, D, axes=(2, 0))                     # [x, w, b]
+    return np.tensordot(T, R, axes=([1, 2], [1, 2]))        # [x, y]
 
 
 def env_left(L, A, W):
-    """h[1:i] from h[1:i-1] and site i (Eq. tdvp1_h1i with Eq. tdvp1_h)."""
-    return np.einsum("xwy,xtp,wvts,ysq->pvq", L, A.conj(), W, A, optimize=True)
+    """h[1:i] from h[1:i-1] and site i (Eq. tdvp1_h1i with Eq. tdvp1_h).
+
+    Lnew[p,v,q] = sum L[x,w,y] conj(A[x,t,p]) W[w,v,t,s] A[y,s,q].
+    """
+    T1 = np.tensordot(L, A, axes=(2, 0))                    # [x, w, s, q]
+    T2 = np.tensordot(T1, W, axes=([1, 2], [0, 3]))         # [x, q, v, t]
+    out = np.tensordot(A.conj(), T2, axes=([0, 1], [0, 3])) # [p, q, v]
+    return out.transpose(0, 2, 1)
 
 
 def env_right(R, A, W):
-    """h[i:N] from h[i+1:N] and site i (Eq. tdvp1_hiN with Eq. tdvp1_h)."""
-    return np.einsum("ptx,wvts,qsy,xvy->pwq", A.conj(), W, A, R, optimize=True)
+    """h[i:N] from h[i+1:N] and site i (Eq. tdvp1_hiN with Eq. tdvp1_h).
+
+    Rnew[p,w,q] = sum conj(A[p,t,x]) W[w,v,t,s] A[q,s,y] R[x,v,y].
+    """
+    T1 = np.tensordot(A, R, axes=(2, 2))                    # [q, s, x, v]
+    T2 = np.tensordot(T1, W, axes=([1, 3], [3, 1]))         # [q, x, w, t]
+    out = np.tensordot(A.conj(), T2, axes=([1, 2], [3, 1])) # [p, q, w]
+    return out.transpose(0, 2, 1)
 
 
 def product_mps(d, bd, occ):
@@ -40,7 +59,9 @@ def product_mps(d, bd, occ):
     Reading of the basis completion the paper asks for (Sec. II.A.2, end of
     TDVP-PS; Sec. II.C): row 0 of site i (viewed as a Dl x (d*Dr) matrix) is the
     occupied path, A[0, occ_i, 0] = 1; row j >= 1 is the standard basis vector at
-    the j-th position (s, r) in lexicographic order that differs from (occ_i, 0).
+    the j-th position (s, r) other than (occ_i, 0), positions ordered by r first
+    and s second, so that the local excitations of the occupied right path come
+    first.
     Distinct standard basis rows are orthonormal, so every site is
     right-canonical (Eq. rcanon) and the state is the product state.
     """
@@ -50,8 +71,8 @@ def product_mps(d, bd, occ):
         A = np.zeros((Dl, di, Dr), dtype=complex)
         A[0, occ[i], 0] = 1.0
         j = 1
-        for s in range(di):
-            for r in range(Dr):
+        for r in range(Dr):
+            for s in range(di):
                 if j >= Dl:
                     break
                 if s == occ[i] and r == 0:

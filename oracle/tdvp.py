@@ -92,8 +92,9 @@ def _expect_local(mps, ops_at):
     E = np.ones((1, 1), dtype=complex)
     for i, A in enumerate(mps):
         O = ops_at.get(i)
-        B = A if O is None else np.einsum("ts,asb->atb", O, A)
-        E = np.einsum("xy,xtp,ytq->pq", E, A.conj(), B)
+        B = A if O is None else np.tensordot(O, A, axes=(1, 1)).transpose(1, 0, 2)
+        T = np.tensordot(E, B, axes=(1, 0))                     # [x, t, q]
+        E = np.tensordot(A.conj(), T, axes=([0, 1], [0, 1]))   # [p, q]
     return E[0, 0]
 
 

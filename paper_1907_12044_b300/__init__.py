@@ -1,0 +1,12 @@
+"""B300-native one-site TDVP projector-splitting (TDVP-PS) for Frenkel-Holstein chains.
+
+The time evolution runs in ``libtdvp.so`` (hand-written CUDA for sm_103a behind a C ABI, see
+``include/tdvp.h``); this package only loads the library and marshals arguments.  There is no
+CPU path: if the library is missing, ``Engine`` raises.
+"""
+from ._lib import (Engine, TDVPError, load_library, library_path, PREC_FP64, KRYLOV_ADAPTIVE,
+                   EXPORTED_SYMBOLS)
+from .build import build
+
+__all__ = ["Engine", "TDVPError", "load_library", "library_path", "build", "PREC_FP64",
+           "KRYLOV_ADAPTIVE", "EXPORTED_SYMBOLS"]

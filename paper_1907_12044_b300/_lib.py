@@ -1,0 +1,241 @@
+"""ctypes binding of libtdvp (argument marshalling only; every step runs in the CUDA library)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+PREC_FP64 = 0
+KRYLOV_ADAPTIVE = 0
+
+ERRORS = {
+    -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
+    -4: "Krylov solve stopped at kmax above the tolerance", -5: "device wait timed out",
+    -6: "non-finite value", -7: "call out of order",
+}
+
+EXPORTED_SYMBOLS = [
+    "tdvp_create", "tdvp_build_mpo", "tdvp_init_mps", "tdvp_init_mps_tensors", "tdvp_ps_step",
+    "tdvp_observables", "tdvp_chain_info", "tdvp_get_site", "tdvp_move_center",
+    "tdvp_center_to_zero", "tdvp_apply_heff", "tdvp_debug_qr", "tdvp_debug_expm", "tdvp_stats",
+    "tdvp_reset_stats", "tdvp_last_error", "tdvp_destroy", "tdvp_set_profiling",
+]
+
+
+class TDVPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libtdvp error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class FHParamsC(C.Structure):
+    _fields_ = [("n_el", C.c_int), ("E", C.POINTER(C.c_double)), ("J", C.POINTER(C.c_double)),
+                ("n_modes", C.POINTER(C.c_int)), ("omega", C.POINTER(C.c_double)),
+                ("g", C.POINTER(C.c_double)), ("n_levels", C.POINTER(C.c_int)),
+                ("el_order", C.POINTER(C.c_int)), ("energy_offset", C.c_double),
+                ("include_zpe", C.c_int)]
+
+
+NCAT = 6
+CATEGORIES = ["gemm", "wapply", "lanczos_vec", "tridiag", "qr", "other"]
+
+
+class StatsC(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("site_updates", C.c_longlong), ("matvecs", C.c_longlong),
+                ("krylov_solves", C.c_longlong), ("krylov_dim_sum", C.c_longlong),
+                ("krylov_dim_max", C.c_int), ("host_syncs", C.c_longlong),
+                ("kernel_launches", C.c_longlong), ("not_converged", C.c_longlong),
+                ("prof_ms", C.c_double * NCAT), ("prof_launches", C.c_longlong * NCAT),
+                ("prof_flops", C.c_double * NCAT)]
+
+
+def library_path():
+    return os.path.join(HERE, "libtdvp.so")
+
+
+_LIB = None
+
+
+def load_library():
+    """Load libtdvp.so from the package directory (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1907_12044_b300.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int)
+    lib.tdvp_create.argtypes = [C.POINTER(P), C.c_int, P, C.c_int, C.c_int]
+    lib.tdvp_build_mpo.argtypes = [P, C.c_int, C.POINTER(FHParamsC)]
+    lib.tdvp_init_mps.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.tdvp_init_mps_tensors.argtypes = [P, C.c_int, ip, dp]
+    lib.tdvp_ps_step.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_int, C.c_double]
+    lib.tdvp_observables.argtypes = [P, C.c_int, dp, dp, dp]
+    lib.tdvp_chain_info.argtypes = [P, C.c_int, ip, ip, ip, ip]
+    lib.tdvp_get_site.argtypes = [P, C.c_int, C.c_int, dp]
+    lib.tdvp_move_center.argtypes = [P, C.c_int, C.c_int]
+    lib.tdvp_center_to_zero.argtypes = [P, C.c_int]
+    lib.tdvp_apply_heff.argtypes = [P, C.c_int, C.c_int, dp, dp]
+    lib.tdvp_debug_qr.argtypes = [P, C.c_int, C.c_int, dp, dp, dp]
+    lib.tdvp_debug_expm.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, ip]
+    lib.tdvp_stats.argtypes = [P, C.POINTER(StatsC)]
+    lib.tdvp_set_profiling.argtypes = [P, C.c_int]
+    lib.tdvp_reset_stats.argtypes = [P]
+    lib.tdvp_reset_stats.restype = None
+    lib.tdvp_last_error.argtypes = [P]
+    lib.tdvp_last_error.restype = C.c_char_p
+    lib.tdvp_destroy.argtypes = [P]
+    lib.tdvp_destroy.restype = None
+    _LIB = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class Engine:
+    """One libtdvp context: ``n_realisations`` trajectories on one GPU and one CUDA stream.
+
+    ``stream`` is a raw cudaStream_t value (int); by default the current PyTorch stream of the
+    device is used.
+    """
+
+    def __init__(self, n_realisations=1, kmax=64, device=0, stream=None):
+        self.lib = load_library()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self._h = C.c_void_p()
+        self.R = n_realisations
+        rc = self.lib.tdvp_create(C.byref(self._h), device, C.c_void_p(stream), n_realisations, kmax)
+        if rc != 0:
+            raise TDVPError(rc, "tdvp_create failed")
+        self._keep = []
+        self.n_el = None
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TDVPError(rc, self.lib.tdvp_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if self._h:
+            self.lib.tdvp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up -----------------------------------------------------------------------------
+    def build_mpo(self, r, params):
+        """``params``: an object with ``.flat()`` (dict of E, J, n_modes, omega, g, n_levels,
+        el_order), ``energy_offset`` and ``include_zpe``."""
+        f = params.flat()
+        arrs = {k: np.ascontiguousarray(v, dtype=np.int32 if k in ("n_modes", "n_levels", "el_order") else np.float64)
+                for k, v in f.items()}
+        p = FHParamsC(len(arrs["E"]), _dptr(arrs["E"]), _dptr(arrs["J"]), _iptr(arrs["n_modes"]),
+                      _dptr(arrs["omega"]), _dptr(arrs["g"]), _iptr(arrs["n_levels"]), _iptr(arrs["el_order"]),
+                      float(params.energy_offset), int(bool(params.include_zpe)))
+        self._check(self.lib.tdvp_build_mpo(self._h, r, C.byref(p)))
+        self.n_el = len(arrs["E"])
+
+    def init_mps(self, r, D, exciton_site):
+        self._check(self.lib.tdvp_init_mps(self._h, r, int(D), int(exciton_site)))
+
+    def init_mps_tensors(self, r, tensors):
+        bd = [1] + [int(t.shape[2]) for t in tensors]
+        bd = np.asarray(bd, dtype=np.int32)
+        flat = np.concatenate([np.ascontiguousarray(t, dtype=np.complex128).reshape(-1) for t in tensors])
+        buf = np.ascontiguousarray(flat.view(np.float64))
+        self._check(self.lib.tdvp_init_mps_tensors(self._h, r, _iptr(bd), _dptr(buf)))
+
+    # -- time evolution -----------------------------------------------------------------------
+    def step(self, dt_fs, n_steps=1, precision=PREC_FP64, krylov_mode=KRYLOV_ADAPTIVE, tol=1e-12):
+        self._check(self.lib.tdvp_ps_step(self._h, float(dt_fs), int(n_steps), int(precision),
+                                          int(krylov_mode), float(tol)))
+
+    def observables(self, r=0):
+        pops = np.zeros(self.n_el)
+        e = C.c_double()
+        n = C.c_double()
+        self._check(self.lib.tdvp_observables(self._h, r, _dptr(pops), C.byref(e), C.byref(n)))
+        return pops, e.value, n.value
+
+    # -- inspection and components ----------------------------------------------------------
+    def chain_info(self, r=0):
+        n = C.c_int()
+        self._check(self.lib.tdvp_chain_info(self._h, r, C.byref(n), None, None, None))
+        N = n.value
+        d = np.zeros(N, np.int32)
+        bd = np.zeros(N + 1, np.int32)
+        w = np.zeros(N + 1, np.int32)
+        self._check(self.lib.tdvp_chain_info(self._h, r, C.byref(n), _iptr(d), _iptr(bd), _iptr(w)))
+        return d, bd, w
+
+    def get_site(self, r, i):
+        d, bd, _ = self.chain_info(r)
+        out = np.zeros((bd[i], d[i], bd[i + 1]), dtype=np.complex128)
+        self._check(self.lib.tdvp_get_site(self._h, r, i, _dptr(out.view(np.float64))))
+        return out
+
+    def get_mps(self, r=0):
+        d, _, _ = self.chain_info(r)
+        return [self.get_site(r, i) for i in range(len(d))]
+
+    def move_center(self, r, site):
+        self._check(self.lib.tdvp_move_center(self._h, r, site))
+
+    def center_to_zero(self, r):
+        self._check(self.lib.tdvp_center_to_zero(self._h, r))
+
+    def apply_heff(self, r, i, x):
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        y = np.zeros_like(x)
+        self._check(self.lib.tdvp_apply_heff(self._h, r, i, _dptr(x.view(np.float64)), _dptr(y.view(np.float64))))
+        return y
+
+    def debug_qr(self, Cm):
+        Cm = np.ascontiguousarray(Cm, dtype=np.complex128)
+        m, n = Cm.shape
+        Q = np.zeros((m, n), np.complex128)
+        R = np.zeros((n, n), np.complex128)
+        self._check(self.lib.tdvp_debug_qr(self._h, m, n, _dptr(Cm.view(np.float64)), _dptr(Q.view(np.float64)),
+                                           _dptr(R.view(np.float64))))
+        return Q, R
+
+    def debug_expm(self, r, i, z, tol, v):
+        v = np.ascontiguousarray(v, dtype=np.complex128)
+        out = np.zeros_like(v)
+        k = C.c_int()
+        self._check(self.lib.tdvp_debug_expm(self._h, r, i, float(np.real(z)), float(np.imag(z)), float(tol),
+                                             _dptr(v.view(np.float64)), _dptr(out.view(np.float64)), C.byref(k)))
+        return out, k.value
+
+    def stats(self):
+        s = StatsC()
+        self._check(self.lib.tdvp_stats(self._h, C.byref(s)))
+        out = {}
+        for k, _ in StatsC._fields_:
+            v = getattr(s, k)
+            out[k] = {c: v[i] for i, c in enumerate(CATEGORIES)} if k.startswith("prof_") else v
+        return out
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.tdvp_set_profiling(self._h, 1 if on else 0))
+
+    def reset_stats(self):
+        self.lib.tdvp_reset_stats(self._h)

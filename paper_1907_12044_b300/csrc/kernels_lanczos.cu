@@ -1,0 +1,430 @@
+// Lanczos exponential exp(i theta H) v of the TDVP-PS local steps (Sec. II.A.2, TDVP-PS: the
+// Krylov subspace method, Lanczos for a Hermitian operator, dimension adaptive until the result
+// converges).  FP64 throughout.
+//
+// Per iteration j the host enqueues: matvec (x -> w), then
+//   dots     p_t = <V_t, w>                         (partial sums per chunk)
+//   upd1     h1 = sum p; w -= V h1; p2_t = <V_t, w>  (first Gram-Schmidt pass)
+//   upd2     h2 = sum p2; w -= V h2; |w|^2 partials  (re-orthogonalisation pass)
+//   tri      beta_j = |w|; alpha_j = Re(h1_j + h2_j); c = exp(i theta T_{j+1}) e_1 (Chebyshev);
+//            stop when ||v|| beta_j |c_j| <= tol, or k = kcap, or beta_j = 0
+//   next     V_{j+1} = x = w / beta_j
+// Every kernel of an iteration returns at once when the solve of its realisation is done, so
+// the host may enqueue more iterations than needed.  Reductions are two-level with a fixed
+// order, so results are bit-reproducible run to run.
+#include "tdvp_internal.cuh"
+#include <cmath>
+
+namespace {
+
+constexpr int NT = TDVP_VEC_THREADS;
+constexpr int PSTRIDE = TDVP_KMAX_HARD + 2;
+
+struct VecGeom {
+  long long n;       // vector length
+  int nblk;          // chunks used by this realisation
+  long long c0, c1;  // chunk of this block
+};
+
+__device__ __forceinline__ long long vec_len(const SiteDev* sdr, int site, int kind) {
+  const SiteDev& s = sdr[site];
+  return kind == 0 ? (long long)s.Dl * s.d * s.Dr : (long long)s.Dr * s.Dr;
+}
+
+__device__ __forceinline__ VecGeom geom(long long n, int b) {
+  VecGeom g;
+  g.n = n;
+  long long nb = (n + 511) / 512;
+  if (nb > TDVP_MAX_VEC_BLOCKS) nb = TDVP_MAX_VEC_BLOCKS;
+  if (nb < 1) nb = 1;
+  g.nblk = (int)nb;
+  const long long ch = (n + nb - 1) / nb;
+  g.c0 = (long long)b * ch;
+  g.c1 = g.c0 + ch < n ? g.c0 + ch : n;
+  return g;
+}
+
+__device__ __forceinline__ zc* P(const WorkDev& W, int tab, int b, int t) {
+  return W.part + ((long long)tab * TDVP_MAX_VEC_BLOCKS + b) * PSTRIDE + t;
+}
+
+__device__ __forceinline__ zc* src_ptr(const WorkDev& W, const SiteDev* sdr, int site, int which) {
+  if (which == 0) return W.x;
+  if (which == 1) return sdr[site].A;
+  if (which == 2) return W.bond;
+  return W.w;
+}
+
+// Block-wide sum of a complex value; result valid in every thread.  `red` holds 2*(NT/32) doubles.
+__device__ __forceinline__ zc block_zsum(zc v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  __syncthreads();
+  if (lane == 0) { red[2 * wid] = v.x; red[2 * wid + 1] = v.y; }
+  __syncthreads();
+  zc s = zmake(0, 0);
+  for (int i = 0; i < NT / 32; ++i) { s.x += red[2 * i]; s.y += red[2 * i + 1]; }
+  return s;
+}
+
+// h[t] = sum_b P(tab, b, t) for t <= j, one warp per t in a fixed order (same in every block).
+__device__ void reduce_partials(const WorkDev& W, int tab, int nblk, int j, zc* h) {
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  for (int t = wid; t <= j; t += NT / 32) {
+    zc s = zmake(0, 0);
+    for (int b = lane; b < nblk; b += 32) s = zadd(s, *P(W, tab, b, t));
+    for (int o = 16; o > 0; o >>= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    }
+    if (lane == 0) h[t] = s;
+  }
+  __syncthreads();
+}
+
+// Partial dots p_t = sum_{e in chunk} conj(V_t[e]) w[e] for t <= j into table `tab`.
+__device__ void chunk_dots(const WorkDev& W, const VecGeom& g, int j, int tab, int b, double* red) {
+  constexpr int G = 8;
+  for (int t0 = 0; t0 <= j; t0 += G) {
+    zc acc[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) acc[q] = zmake(0, 0);
+    for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) {
+      const zc we = W.w[e];
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+        if (t0 + q <= j) acc[q] = zcfma(W.V[(t0 + q) * W.ldV + e], we, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      if (t0 + q > j) break;
+      const zc s = block_zsum(acc[q], red);
+      if (threadIdx.x == 0) *P(W, tab, b, t0 + q) = s;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT) lz_start1(LzArgs a) {
+  __shared__ double red[2 * NT / 32];
+  const int r = blockIdx.y, b = blockIdx.x;
+  const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
+  const WorkDev& W = a.wk[r];
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  if (b >= g.nblk) return;
+  const zc* src = src_ptr(W, sdr, a.site, a.src);
+  zc acc = zmake(0, 0);
+  for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) acc.x += zabs2(src[e]);
+  const zc s = block_zsum(acc, red);
+  if (threadIdx.x == 0) *P(W, 2, b, 0) = s;
+}
+
+__global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
+  __shared__ zc h[1];
+  const int r = blockIdx.y, b = blockIdx.x;
+  const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
+  const WorkDev& W = a.wk[r];
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  if (b >= g.nblk) return;
+  reduce_partials(W, 2, g.nblk, 0, h);
+  const double nrm = sqrt(h[0].x);
+  const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
+  const zc* src = src_ptr(W, sdr, a.site, a.src);
+  for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) {
+    const zc v = zscale(src[e], inv);
+    W.V[e] = v;
+    W.x[e] = v;
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    KState* ks = W.ks;
+    ks->nrm = nrm;
+    ks->k = 0;
+    ks->n = (int)g.n;
+    ks->kcap = (int)(g.n < a.kmax ? g.n : a.kmax);
+    ks->notconv = 0;
+    ks->err = 0;
+    const bool bad = !isfinite(nrm);
+    ks->status = bad ? -6 : 0;
+    ks->done = (nrm == 0.0 || bad) ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
+  __shared__ double red[2 * NT / 32];
+  const int r = blockIdx.y, b = blockIdx.x;
+  const WorkDev& W = a.wk[r];
+  if (W.ks->done) return;
+  const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  if (b >= g.nblk) return;
+  chunk_dots(W, g, j, 0, b, red);
+}
+
+// pass 1 (tab_in = 0, tab_out = 1) or pass 2 (tab_in = 1, norm partials into table 2)
+__global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
+  __shared__ double red[2 * NT / 32];
+  __shared__ zc h[TDVP_KMAX_HARD];
+  const int r = blockIdx.y, b = blockIdx.x;
+  const WorkDev& W = a.wk[r];
+  if (W.ks->done) return;
+  const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  if (b >= g.nblk) return;
+  reduce_partials(W, pass == 1 ? 0 : 1, g.nblk, j, h);
+  double nn = 0;
+  for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) {
+    zc we = W.w[e];
+    for (int t = 0; t <= j; ++t) we = zfms(h[t], W.V[t * W.ldV + e], we);
+    W.w[e] = we;
+    nn += zabs2(we);
+  }
+  if (pass == 1) {
+    __syncthreads();
+    chunk_dots(W, g, j, 1, b, red);
+    if (b == 0 && threadIdx.x == 0) W.ks->alpha[j] = h[j].x;
+  } else {
+    const zc s = block_zsum(zmake(nn, 0), red);
+    if (threadIdx.x == 0) *P(W, 2, b, 0) = s;
+    if (b == 0 && threadIdx.x == 0) W.ks->alpha[j] += h[j].x;
+  }
+}
+
+// Bessel functions J_0..J_N at x >= 0 by Miller's downward recurrence J_{n-1} = (2n/x) J_n - J_{n+1},
+// normalised with J_0 + 2 sum_{k>=1} J_{2k} = 1.  Single thread.
+__device__ void bessel_j(double x, int N, double* J) {
+  for (int n = 0; n <= N; ++n) J[n] = 0.0;
+  if (x < 1e-14) { J[0] = 1.0; return; }
+  int m = N + 24 + (int)x;
+  m += (m & 1);
+  double jp1 = 0.0, jn = 1e-200, S = 2.0 * jn;   // m even: contributes 2 J_m
+  for (int n = m; n >= 1; --n) {
+    const double jm1 = (2.0 * n / x) * jn - jp1;
+    jp1 = jn;
+    jn = jm1;
+    const int idx = n - 1;
+    if (idx <= N) J[idx] = jn;
+    if ((idx & 1) == 0) S += (idx == 0 ? 1.0 : 2.0) * jn;
+    if (fabs(jn) > 1e150) {
+      jn *= 1e-150; jp1 *= 1e-150; S *= 1e-150;
+      for (int q = idx; q <= N; ++q) J[q] *= 1e-150;
+    }
+  }
+  const double inv = 1.0 / S;
+  for (int n = 0; n <= N; ++n) J[n] *= inv;
+}
+
+constexpr int TRI_THREADS = 128;
+constexpr int MAX_CHEB = 512;
+
+// c = exp(i theta T) e_1 for T = tridiag(beta[0..k-2], alpha[0..k-1]) by a Chebyshev expansion on
+// the Gershgorin interval [lo, hi]: exp(i x T~) = sum_n (2 - delta_n0) i^n J_n(x) T_n(T~)
+// (Jacobi-Anger), T~ = (T - c0)/h, x = theta h.  The vectors T_n(T~) e_1 are real.
+// Thread t (< k) owns component t.  Returns false when the expansion would need too many terms.
+__device__ bool tridiag_expi(const double* alpha, const double* beta, int k, double theta, zc* out,
+                             double* sh /* >= 3*TRI_THREADS + MAX_CHEB + 8 doubles */) {
+  const int t = threadIdx.x;
+  double* vcur = sh;                       // [TRI_THREADS]
+  double* J = sh + TRI_THREADS;            // [MAX_CHEB]
+  double* red = J + MAX_CHEB;              // [8]
+  double* bnd = red + 8;                   // lo, hi
+  // Gershgorin bounds
+  double lo = 1e300, hi = -1e300;
+  double at = 0, bl = 0, br = 0;
+  if (t < k) {
+    at = alpha[t];
+    bl = t > 0 ? beta[t - 1] : 0.0;
+    br = t < k - 1 ? beta[t] : 0.0;
+    const double rad = fabs(bl) + fabs(br);
+    lo = at - rad;
+    hi = at + rad;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (t % 32 == 0) { red[2 * (t / 32)] = lo; red[2 * (t / 32) + 1] = hi; }
+  __syncthreads();
+  if (t == 0) {
+    double l = red[0], h2 = red[1];
+    for (int w = 1; w < TRI_THREADS / 32; ++w) { l = fmin(l, red[2 * w]); h2 = fmax(h2, red[2 * w + 1]); }
+    bnd[0] = l; bnd[1] = h2;
+  }
+  __syncthreads();
+  const double c0 = 0.5 * (bnd[0] + bnd[1]);
+  const double h = 0.5 * (bnd[1] - bnd[0]);
+  double sr, cr;
+  sincos(theta * c0, &sr, &cr);
+  const zc ph = zmake(cr, sr);                  // exp(i theta c0)
+  const double x = theta * h;
+  const double ax = fabs(x);
+  const int N = (int)ceil(ax) + 30;
+  if (h <= 0.0 || ax < 1e-14) {                 // T is a multiple of the identity
+    if (t < k) out[t] = t == 0 ? ph : zmake(0, 0);
+    __syncthreads();
+    return true;
+  }
+  if (N + 1 > MAX_CHEB) return false;
+  if (t == 0) bessel_j(ax, N, J);
+  __syncthreads();
+  const double sgn = x >= 0 ? 1.0 : -1.0;      // J_n(-a) = (-1)^n J_n(a)
+  const double ih = 1.0 / h;
+  // coefficient of T_n: (2 - delta) i^n J_n(x); i^n cycles 1, i, -1, -i
+  double vprev = (t == 0) ? 1.0 : 0.0;          // T_0 e_1
+  vcur[t] = vprev;
+  __syncthreads();
+  double v1 = 0;
+  if (t < k) {
+    const double left = t > 0 ? vcur[t - 1] : 0.0, right = t < k - 1 ? vcur[t + 1] : 0.0;
+    v1 = ((at - c0) * vprev + bl * left + br * right) * ih;   // T_1 e_1
+  }
+  zc acc = zmake(J[0] * vprev, 0.0);
+  {
+    const double cf = 2.0 * J[1] * sgn;         // i^1 * sgn
+    acc.y += cf * v1;
+  }
+  __syncthreads();
+  vcur[t] = v1;
+  double vc = v1;
+  __syncthreads();
+  for (int n = 1; n < N; ++n) {
+    double vn = 0;
+    if (t < k) {
+      const double left = t > 0 ? vcur[t - 1] : 0.0, right = t < k - 1 ? vcur[t + 1] : 0.0;
+      vn = 2.0 * ((at - c0) * vc + bl * left + br * right) * ih - vprev;
+    }
+    const int m = n + 1;
+    double cf = 2.0 * J[m];
+    if (sgn < 0 && (m & 1)) cf = -cf;
+    switch (m & 3) {
+      case 0: acc.x += cf * vn; break;
+      case 1: acc.y += cf * vn; break;
+      case 2: acc.x -= cf * vn; break;
+      default: acc.y -= cf * vn; break;
+    }
+    vprev = vc;
+    vc = vn;
+    __syncthreads();
+    vcur[t] = vn;
+    __syncthreads();
+  }
+  if (t < k) out[t] = zmul(ph, acc);
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flags) {
+  __shared__ double sh[3 * TRI_THREADS + MAX_CHEB + 16];
+  __shared__ zc c[TRI_THREADS];
+  __shared__ double betaj_s;
+  const int r = blockIdx.x;
+  const WorkDev& W = a.wk[r];
+  KState* ks = W.ks;
+  if (ks->done) return;
+  const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), 0);
+  if (threadIdx.x < 32) {
+    double s = 0;
+    for (int b = threadIdx.x; b < g.nblk; b += 32) s += P(W, 2, b, 0)->x;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) betaj_s = sqrt(s);
+  }
+  __syncthreads();
+  const double beta = betaj_s;
+  const int k = j + 1;
+  if (!isfinite(beta) || !isfinite(ks->alpha[j])) {
+    if (threadIdx.x == 0) { ks->status = -6; ks->done = 1; ks->k = 0; flags[r] = -1; }
+    return;
+  }
+  const bool last = (k >= ks->kcap) || beta == 0.0;
+  if (k < a.jcheck && !last) {
+    if (threadIdx.x == 0) { ks->beta[j] = beta; ks->inv_beta = 1.0 / beta; }
+    return;
+  }
+  const bool ok = tridiag_expi(ks->alpha, ks->beta, k, a.theta, c, sh);
+  if (!ok) {
+    if (threadIdx.x == 0) { ks->status = -1; ks->done = 1; ks->k = 0; flags[r] = -1; }
+    return;
+  }
+  const double err = ks->nrm * beta * sqrt(zabs2(c[k - 1]));
+  const bool conv = err <= a.tol;
+  if (conv || last) {
+    if (threadIdx.x < k) ks->coef[threadIdx.x] = zscale(c[threadIdx.x], ks->nrm);
+    if (threadIdx.x == 0) {
+      ks->err = err;
+      ks->k = k;
+      ks->notconv = (!conv && beta > 0.0) ? 1 : 0;
+      ks->done = 1;
+      flags[r] = k | (ks->notconv << 16);
+    }
+  } else if (threadIdx.x == 0) {
+    ks->err = err;
+    ks->beta[j] = beta;
+    ks->inv_beta = 1.0 / beta;
+  }
+}
+
+__global__ void __launch_bounds__(NT) lz_next(LzArgs a, int j) {
+  const int r = blockIdx.y, b = blockIdx.x;
+  const WorkDev& W = a.wk[r];
+  if (W.ks->done) return;
+  const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  if (b >= g.nblk) return;
+  const double ib = W.ks->inv_beta;
+  zc* Vn = W.V + (j + 1) * W.ldV;
+  for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) {
+    const zc v = zscale(W.w[e], ib);
+    Vn[e] = v;
+    W.x[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(NT) lz_combine(LzArgs a) {
+  __shared__ zc cf[TDVP_KMAX_HARD];
+  const int r = blockIdx.y, b = blockIdx.x;
+  const WorkDev& W = a.wk[r];
+  const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  if (b >= g.nblk) return;
+  const int k = W.ks->k;
+  for (int t = threadIdx.x; t < k; t += NT) cf[t] = W.ks->coef[t];
+  __syncthreads();
+  zc* dst = src_ptr(W, sdr, a.site, a.dst);
+  for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) {
+    zc acc = zmake(0, 0);
+    for (int t = 0; t < k; ++t) acc = zfma(cf[t], W.V[t * W.ldV + e], acc);
+    dst[e] = acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st) {
+  dim3 grid(a.nblk, a.R);
+  lz_start1<<<grid, NT, 0, st>>>(a);
+  lz_start2<<<grid, NT, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_iter_pre(const LzArgs& a, int j, cudaStream_t st) {
+  dim3 grid(a.nblk, a.R);
+  lz_dots<<<grid, NT, 0, st>>>(a, j);
+  lz_upd<<<grid, NT, 0, st>>>(a, j, 1);
+  lz_upd<<<grid, NT, 0, st>>>(a, j, 2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_iter_post(const LzArgs& a, int j, cudaStream_t st) {
+  lz_tri<<<a.R, TRI_THREADS, 0, st>>>(a, j, a.flags);
+  dim3 grid(a.nblk, a.R);
+  lz_next<<<grid, NT, 0, st>>>(a, j);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_combine(const LzArgs& a, cudaStream_t st) {
+  dim3 grid(a.nblk, a.R);
+  lz_combine<<<grid, NT, 0, st>>>(a);
+  return cudaGetLastError();
+}

@@ -1,0 +1,1002 @@
+// Host side of libtdvp: context, MPO construction, initial states, the TDVP-PS sweep driver
+// (Eq. ps_trotter), observables and the component entry points.  All arithmetic on the state is
+// done by the kernels in kernels_*.cu; this file sizes buffers, builds the device tables and
+// enqueues launches on the caller's stream.
+#include "tdvp_internal.cuh"
+#include "../../include/tdvp.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr double kPhasePerCmFs = 2.0 * 3.14159265358979323846 * 2.99792458e-5;   // 2 pi c
+constexpr double kRankRtol = 1e-13;
+
+struct RealHost {
+  bool mpo = false, mps = false;
+  std::vector<int> bd;                 // bond dims, N+1
+  std::vector<void*> mpo_allocs;       // CSR buffers
+  std::vector<void*> mps_allocs;       // tensors, environments, work buffers
+  std::vector<std::vector<double>> W;  // dense MPO per site [Wl][Wr][d][d]
+};
+
+}  // namespace
+
+struct tdvp_ctx {
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  int R = 1;
+  int kmax = 64;
+  // chain layout (shared by all realisations)
+  int N = 0, n_el = 0;
+  std::vector<int> d, Wb, is_el, label;   // Wb: MPO bond dims N+1
+  std::vector<int> n_modes, levels;        // layout check
+  std::vector<int> el_order;
+  std::vector<RealHost> rh;
+  std::vector<SiteDev> h_sites;
+  SiteDev* d_sites = nullptr;
+  std::vector<WorkDev> h_work;
+  WorkDev* d_work = nullptr;
+  int* d_flags = nullptr;
+  int* h_flags = nullptr;     // pinned
+  int* d_err = nullptr;       // [R] device error words
+  int* h_err = nullptr;       // pinned
+  double* h_obs = nullptr;    // pinned, (n_el+4) per realisation
+  std::vector<int> khist;     // last Krylov dim per (site, kind)
+  int qr_cap = 0;
+  int check_every = 1;
+  // per-launch timing
+  int prof = 0;
+  std::vector<cudaEvent_t> ev;   // pairs
+  std::vector<int> ev_cat;
+  size_t ev_used = 0;
+  std::string err;
+  tdvp_stats_t stats{};
+};
+
+namespace {
+
+int fail(tdvp_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? TDVP_ERR_OOM : TDVP_ERR_CUDA,       \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+int prof_begin(tdvp_ctx* ctx, int cat);
+int prof_end(tdvp_ctx* ctx);
+
+#define LAUNCHC(cat, call)                                    \
+  do {                                                        \
+    if (ctx->prof) { int pr_ = prof_begin(ctx, cat); if (pr_) return pr_; } \
+    CK(call);                                                 \
+    if (ctx->prof) { int pr_ = prof_end(ctx); if (pr_) return pr_; }        \
+    ctx->stats.kernel_launches++;                             \
+  } while (0)
+#define LAUNCH(call) LAUNCHC(TDVP_CAT_OTHER, call)
+
+template <class T>
+int dalloc(tdvp_ctx* ctx, std::vector<void*>& owner, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return fail(ctx, TDVP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  cudaMemsetAsync(q, 0, std::max<size_t>(count, 1) * sizeof(T), ctx->st);
+  owner.push_back(q);
+  *p = static_cast<T*>(q);
+  return TDVP_OK;
+}
+
+void free_all(std::vector<void*>& v) {
+  for (void* p : v) cudaFree(p);
+  v.clear();
+}
+
+int prof_begin(tdvp_ctx* ctx, int cat) {
+  if (ctx->ev_used + 2 > ctx->ev.size()) {
+    for (int q = 0; q < 512; ++q) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
+    ctx->ev_cat.resize(ctx->ev.size() / 2);
+  }
+  ctx->ev_cat[ctx->ev_used / 2] = cat;
+  CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->st));
+  return TDVP_OK;
+}
+
+int prof_end(tdvp_ctx* ctx) {
+  CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->st));
+  ctx->ev_used += 2;
+  return TDVP_OK;
+}
+
+// Fold the recorded event pairs into the statistics (synchronises the stream).
+int prof_collect(tdvp_ctx* ctx) {
+  if (ctx->ev_used == 0) return TDVP_OK;
+  CK(cudaStreamSynchronize(ctx->st));
+  for (size_t q = 0; q < ctx->ev_used; q += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev[q], ctx->ev[q + 1]));
+    const int cat = ctx->ev_cat[q / 2];
+    ctx->stats.prof_ms[cat] += ms;
+    ctx->stats.prof_launches[cat]++;
+  }
+  ctx->ev_used = 0;
+  return TDVP_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// MPO of Eq. holstein as a finite-state machine (Eq. mpo).  Channel 0 of a cut = nothing placed,
+// channel 1 = a complete term placed.  A cut with k electronic sites to its left (of M) carries
+// 2*min(k, M-k) hopping channels, labelled by the left site while k <= M-k (an a^+ or a placed
+// there, waiting for its partner), afterwards by the right site n (sum_m J a_m^+ or sum_m J a_m
+// placed, waiting for a_n or a_n^+ at n).  Inside the mode block of electronic site m one more
+// channel carries n_m waiting for (b^+ + b) on one of its modes.  The left end keeps only
+// channel 0, the right end only channel 1.
+struct MpoBuilder {
+  int N, M;
+  std::vector<int> d, is_el, label, elpos, nleft;   // elpos: position of label along el order
+  std::vector<int> order;
+  bool zpe;
+  double off;
+  const double *E, *J, *om, *gg;
+  std::vector<int> mode_index;   // flat mode index of vib sites
+
+  int regime_left(int k) const { return k <= M - k; }       // true: channels indexed by left sites
+  int nhop(int k) const { return 2 * std::min(k, M - k); }
+  bool has_ph(int cut) const { return cut > 0 && cut < N && !is_el[cut]; }
+  int width(int cut) const {
+    if (cut == 0 || cut == N) return 1;
+    return 2 + nhop(nleft[cut]) + (has_ph(cut) ? 1 : 0);
+  }
+  // channel index; kind: 0 idle, 1 done, 2 cr(j), 3 an(j), 4 ph ; j = position along el order
+  int chan(int cut, int kind, int j) const {
+    if (cut == 0) return kind == 0 ? 0 : -1;
+    if (cut == N) return kind == 1 ? 0 : -1;
+    const int k = nleft[cut];
+    if (kind <= 1) return kind;
+    if (kind == 4) return has_ph(cut) ? 2 + nhop(k) : -1;
+    int slot;
+    if (regime_left(k)) { if (j < 0 || j >= k) return -1; slot = j; }
+    else { if (j < k || j >= M) return -1; slot = j - k; }
+    return 2 + 2 * slot + (kind == 2 ? 0 : 1);
+  }
+};
+
+void add_op(std::vector<double>& T, int Wr, int dd, int wl, int wr, const std::vector<double>& op, double coef) {
+  if (wl < 0 || wr < 0 || coef == 0.0) return;
+  double* base = &T[((size_t)wl * Wr + wr) * dd * dd];
+  for (int q = 0; q < dd * dd; ++q) base[q] += coef * op[q];
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------------------------- ABI
+extern "C" {
+
+int tdvp_create(tdvp_ctx** out, int device, void* cuda_stream, int n_realisations, int kmax) {
+  if (!out || n_realisations < 1 || kmax < 1 || kmax > TDVP_KMAX_HARD) return TDVP_ERR_INVALID_ARG;
+  *out = nullptr;
+  tdvp_ctx* ctx = new tdvp_ctx();
+  ctx->dev = device;
+  ctx->st = static_cast<cudaStream_t>(cuda_stream);
+  ctx->R = n_realisations;
+  ctx->kmax = kmax;
+  ctx->rh.resize(n_realisations);
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) { delete ctx; return TDVP_ERR_CUDA; }
+  if (cudaMalloc(&ctx->d_work, sizeof(WorkDev) * ctx->R) != cudaSuccess ||
+      cudaMalloc(&ctx->d_flags, sizeof(int) * ctx->R) != cudaSuccess ||
+      cudaMalloc(&ctx->d_err, sizeof(int) * ctx->R) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_flags, sizeof(int) * ctx->R) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_err, sizeof(int) * ctx->R) != cudaSuccess) {
+    tdvp_destroy(ctx);
+    return TDVP_ERR_OOM;
+  }
+  cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * ctx->R, ctx->st);
+  ctx->h_work.assign(ctx->R, WorkDev{});
+  ctx->qr_cap = qr_max_coresident_blocks(device);
+  if (ctx->qr_cap < ctx->R) { tdvp_destroy(ctx); return TDVP_ERR_INVALID_ARG; }
+  *out = ctx;
+  return TDVP_OK;
+}
+
+void tdvp_destroy(tdvp_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->dev);
+  if (ctx->st) cudaStreamSynchronize(ctx->st); else cudaDeviceSynchronize();
+  for (auto& r : ctx->rh) { free_all(r.mpo_allocs); free_all(r.mps_allocs); }
+  cudaFree(ctx->d_sites);
+  cudaFree(ctx->d_work);
+  cudaFree(ctx->d_flags);
+  cudaFree(ctx->d_err);
+  cudaFreeHost(ctx->h_flags);
+  cudaFreeHost(ctx->h_err);
+  cudaFreeHost(ctx->h_obs);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* tdvp_last_error(const tdvp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tdvp_build_mpo(tdvp_ctx* ctx, int r, const tdvp_fh_params* p) {
+  if (!ctx) return TDVP_ERR_INVALID_ARG;
+  if (r < 0 || r >= ctx->R || !p || p->n_el < 1 || !p->E || !p->J || !p->n_modes || !p->el_order)
+    return fail(ctx, TDVP_ERR_INVALID_ARG, "build_mpo: bad arguments");
+  CK(cudaSetDevice(ctx->dev));
+  const int M = p->n_el;
+  int nm_tot = 0;
+  for (int m = 0; m < M; ++m) {
+    if (p->n_modes[m] < 0) return fail(ctx, TDVP_ERR_INVALID_ARG, "build_mpo: negative n_modes");
+    nm_tot += p->n_modes[m];
+  }
+  if (nm_tot > 0 && (!p->omega || !p->g || !p->n_levels))
+    return fail(ctx, TDVP_ERR_INVALID_ARG, "build_mpo: mode arrays missing");
+  std::vector<int> seen(M, 0);
+  for (int j = 0; j < M; ++j) {
+    const int m = p->el_order[j];
+    if (m < 0 || m >= M || seen[m]) return fail(ctx, TDVP_ERR_INVALID_ARG, "build_mpo: el_order is not a permutation");
+    seen[m] = 1;
+  }
+  for (int m = 0; m < M; ++m)
+    for (int n = 0; n < M; ++n)
+      if (m != n && p->J[m * M + n] != p->J[n * M + m])
+        return fail(ctx, TDVP_ERR_INVALID_ARG, "build_mpo: J must be symmetric");
+  std::vector<int> mode_off(M, 0);
+  for (int m = 1; m < M; ++m) mode_off[m] = mode_off[m - 1] + p->n_modes[m - 1];
+  for (int q = 0; q < nm_tot; ++q)
+    if (p->n_levels[q] < 1 || p->n_levels[q] > 64) return fail(ctx, TDVP_ERR_INVALID_ARG, "build_mpo: n_levels out of range");
+
+  // chain layout
+  MpoBuilder B;
+  B.M = M; B.zpe = p->include_zpe != 0; B.off = p->energy_offset;
+  B.E = p->E; B.J = p->J; B.om = p->omega; B.gg = p->g;
+  B.order.assign(p->el_order, p->el_order + M);
+  B.elpos.assign(M, 0);
+  for (int j = 0; j < M; ++j) B.elpos[B.order[j]] = j;
+  for (int j = 0; j < M; ++j) {
+    const int m = B.order[j];
+    B.d.push_back(2); B.is_el.push_back(1); B.label.push_back(m); B.mode_index.push_back(-1);
+    for (int q = 0; q < p->n_modes[m]; ++q) {
+      B.d.push_back(p->n_levels[mode_off[m] + q]); B.is_el.push_back(0); B.label.push_back(m);
+      B.mode_index.push_back(mode_off[m] + q);
+    }
+  }
+  B.N = (int)B.d.size();
+  B.nleft.assign(B.N + 1, 0);
+  for (int c = 1; c <= B.N; ++c) B.nleft[c] = B.nleft[c - 1] + B.is_el[c - 1];
+
+  std::vector<int> nmv(p->n_modes, p->n_modes + M);
+  std::vector<int> lev(p->n_levels, p->n_levels + nm_tot);
+  if (ctx->N == 0) {
+    ctx->N = B.N; ctx->n_el = M; ctx->d = B.d; ctx->is_el = B.is_el; ctx->label = B.label;
+    ctx->n_modes = nmv; ctx->levels = lev; ctx->el_order = B.order;
+    ctx->Wb.resize(B.N + 1);
+    for (int c = 0; c <= B.N; ++c) ctx->Wb[c] = B.width(c);
+    ctx->h_sites.assign((size_t)ctx->R * ctx->N, SiteDev{});
+    CK(cudaMalloc(&ctx->d_sites, sizeof(SiteDev) * ctx->R * ctx->N));
+    CK(cudaMallocHost(&ctx->h_obs, sizeof(double) * (M + 4) * ctx->R));
+    ctx->khist.assign(2 * ctx->N, 0);
+  } else if (ctx->n_el != M || ctx->n_modes != nmv || ctx->levels != lev || ctx->el_order != B.order) {
+    return fail(ctx, TDVP_ERR_INVALID_ARG, "build_mpo: chain layout differs from realisation 0");
+  }
+  RealHost& H = ctx->rh[r];
+  if (H.mps) return fail(ctx, TDVP_ERR_STATE, "build_mpo: realisation already initialised");
+  free_all(H.mpo_allocs);
+  H.W.assign(B.N, {});
+
+  for (int i = 0; i < B.N; ++i) {
+    const int dd = B.d[i], Wl = B.width(i), Wr = B.width(i + 1);
+    std::vector<double>& T = H.W[i];
+    T.assign((size_t)Wl * Wr * dd * dd, 0.0);
+    // local operators, op[s'*dd + s]
+    std::vector<double> I(dd * dd, 0.0);
+    for (int s = 0; s < dd; ++s) I[s * dd + s] = 1.0;
+    const int cl = i, cr = i + 1;
+    add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 0, 0), I, 1.0);
+    add_op(T, Wr, dd, B.chan(cl, 1, 0), B.chan(cr, 1, 0), I, 1.0);
+    if (B.is_el[i]) {
+      const int m = B.label[i], jm = B.elpos[m];
+      std::vector<double> cre(4, 0.0), ann(4, 0.0), num(4, 0.0);
+      cre[1 * 2 + 0] = 1.0;   // |1><0|
+      ann[0 * 2 + 1] = 1.0;   // |0><1|
+      num[1 * 2 + 1] = 1.0;
+      add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 1, 0), num, B.E[m] - B.off);
+      add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 4, 0), num, 1.0);
+      const int kL = B.nleft[cl], kR = B.nleft[cr];
+      const bool leftL = B.regime_left(kL), leftR = B.regime_left(kR);
+      // terms completed here (this site is the right partner)
+      if (leftL) {
+        for (int j = 0; j < kL; ++j) {
+          const int src = B.order[j];
+          add_op(T, Wr, dd, B.chan(cl, 2, j), B.chan(cr, 1, 0), ann, B.J[src * M + m]);
+          add_op(T, Wr, dd, B.chan(cl, 3, j), B.chan(cr, 1, 0), cre, B.J[m * M + src]);
+        }
+      } else {
+        add_op(T, Wr, dd, B.chan(cl, 2, jm), B.chan(cr, 1, 0), ann, 1.0);
+        add_op(T, Wr, dd, B.chan(cl, 3, jm), B.chan(cr, 1, 0), cre, 1.0);
+      }
+      // terms opened here (this site is the left partner)
+      if (leftR) {
+        add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 2, jm), cre, 1.0);
+        add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 3, jm), ann, 1.0);
+      } else {
+        for (int j = kR; j < M; ++j) {
+          const int n = B.order[j];
+          add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 2, j), cre, B.J[m * M + n]);
+          add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 3, j), ann, B.J[n * M + m]);
+        }
+      }
+      // pending terms passing through
+      if (leftL && leftR) {
+        for (int j = 0; j < kL; ++j) {
+          add_op(T, Wr, dd, B.chan(cl, 2, j), B.chan(cr, 2, j), I, 1.0);
+          add_op(T, Wr, dd, B.chan(cl, 3, j), B.chan(cr, 3, j), I, 1.0);
+        }
+      } else if (leftL && !leftR) {
+        for (int j = 0; j < kL; ++j) {
+          const int src = B.order[j];
+          for (int q = kR; q < M; ++q) {
+            const int n = B.order[q];
+            add_op(T, Wr, dd, B.chan(cl, 2, j), B.chan(cr, 2, q), I, B.J[src * M + n]);
+            add_op(T, Wr, dd, B.chan(cl, 3, j), B.chan(cr, 3, q), I, B.J[n * M + src]);
+          }
+        }
+      } else {
+        for (int q = kR; q < M; ++q) {
+          add_op(T, Wr, dd, B.chan(cl, 2, q), B.chan(cr, 2, q), I, 1.0);
+          add_op(T, Wr, dd, B.chan(cl, 3, q), B.chan(cr, 3, q), I, 1.0);
+        }
+      }
+    } else {
+      const int q = B.mode_index[i];
+      const double w = B.om[q], g = B.gg[q];
+      std::vector<double> nb(dd * dd, 0.0), xb(dd * dd, 0.0);
+      for (int s = 0; s < dd; ++s) nb[s * dd + s] = s;
+      for (int s = 1; s < dd; ++s) {
+        const double v = std::sqrt((double)s);
+        xb[(s - 1) * dd + s] = v;   // b
+        xb[s * dd + (s - 1)] = v;   // b^+
+      }
+      add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 1, 0), nb, w);
+      if (B.zpe) add_op(T, Wr, dd, B.chan(cl, 0, 0), B.chan(cr, 1, 0), I, 0.5 * w);
+      add_op(T, Wr, dd, B.chan(cl, 4, 0), B.chan(cr, 1, 0), xb, g * w);
+      add_op(T, Wr, dd, B.chan(cl, 4, 0), B.chan(cr, 4, 0), I, 1.0);
+      const int k = B.nleft[cl];
+      const int lo = B.regime_left(k) ? 0 : k, hi = B.regime_left(k) ? k : M;
+      for (int j = lo; j < hi; ++j) {
+        add_op(T, Wr, dd, B.chan(cl, 2, j), B.chan(cr, 2, j), I, 1.0);
+        add_op(T, Wr, dd, B.chan(cl, 3, j), B.chan(cr, 3, j), I, 1.0);
+      }
+    }
+    // CSR of the middle stage: forward rows (w', s') and backward rows (w, s')
+    std::vector<int> fptr(Wr * dd + 1, 0), bptr(Wl * dd + 1, 0);
+    std::vector<int> fci, fsi, bci, bsi;
+    std::vector<double> fval, bval;
+    for (int wr = 0; wr < Wr; ++wr)
+      for (int so = 0; so < dd; ++so) {
+        for (int wl = 0; wl < Wl; ++wl)
+          for (int s = 0; s < dd; ++s) {
+            const double v = T[(((size_t)wl * Wr + wr) * dd + so) * dd + s];
+            if (v != 0.0) { fci.push_back(wl); fsi.push_back(s); fval.push_back(v); }
+          }
+        fptr[wr * dd + so + 1] = (int)fval.size();
+      }
+    for (int wl = 0; wl < Wl; ++wl)
+      for (int so = 0; so < dd; ++so) {
+        for (int wr = 0; wr < Wr; ++wr)
+          for (int s = 0; s < dd; ++s) {
+            const double v = T[(((size_t)wl * Wr + wr) * dd + so) * dd + s];
+            if (v != 0.0) { bci.push_back(wr); bsi.push_back(s); bval.push_back(v); }
+          }
+        bptr[wl * dd + so + 1] = (int)bval.size();
+      }
+    SiteDev& S = ctx->h_sites[(size_t)r * ctx->N + i];
+    int *dfp, *dfc, *dfs, *dbp, *dbc, *dbs;
+    double *dfv, *dbv;
+    int rc;
+    if ((rc = dalloc(ctx, H.mpo_allocs, &dfp, fptr.size()))) return rc;
+    if ((rc = dalloc(ctx, H.mpo_allocs, &dfc, fci.size()))) return rc;
+    if ((rc = dalloc(ctx, H.mpo_allocs, &dfs, fsi.size()))) return rc;
+    if ((rc = dalloc(ctx, H.mpo_allocs, &dfv, fval.size()))) return rc;
+    if ((rc = dalloc(ctx, H.mpo_allocs, &dbp, bptr.size()))) return rc;
+    if ((rc = dalloc(ctx, H.mpo_allocs, &dbc, bci.size()))) return rc;
+    if ((rc = dalloc(ctx, H.mpo_allocs, &dbs, bsi.size()))) return rc;
+    if ((rc = dalloc(ctx, H.mpo_allocs, &dbv, bval.size()))) return rc;
+    CK(cudaMemcpy(dfp, fptr.data(), fptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!fci.empty()) {
+      CK(cudaMemcpy(dfc, fci.data(), fci.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dfs, fsi.data(), fsi.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dfv, fval.data(), fval.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(dbp, bptr.data(), bptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!bci.empty()) {
+      CK(cudaMemcpy(dbc, bci.data(), bci.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dbs, bsi.data(), bsi.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dbv, bval.data(), bval.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    S.fw = WCsr{dfp, dfc, dfs, dfv};
+    S.bw = WCsr{dbp, dbc, dbs, dbv};
+    S.d = dd; S.Wl = Wl; S.Wr = Wr;
+  }
+  H.mpo = true;
+  return TDVP_OK;
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------------------------------------------
+// internal helpers
+namespace {
+
+inline int cdivi(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+struct Views {
+  const SiteDev* sd;
+  const WorkDev* wk;
+  int R;
+  int* flags;
+  int r0;
+};
+
+// maxima over the realisations in [r0, r0+R)
+struct Dims { int Dl, Dr; };
+Dims maxdims(tdvp_ctx* ctx, int site, const Views& v) {
+  Dims m{0, 0};
+  for (int r = v.r0; r < v.r0 + v.R; ++r) {
+    m.Dl = std::max(m.Dl, ctx->rh[r].bd[site]);
+    m.Dr = std::max(m.Dr, ctx->rh[r].bd[site + 1]);
+  }
+  return m;
+}
+
+Views all_views(tdvp_ctx* ctx) { return Views{ctx->d_sites, ctx->d_work, ctx->R, ctx->d_flags, 0}; }
+Views one_view(tdvp_ctx* ctx, int r) {
+  return Views{ctx->d_sites + (size_t)r * ctx->N, ctx->d_work + r, 1, ctx->d_flags + r, r};
+}
+
+// algorithmic real flops of one batched GEMM launch (8 per complex multiply-add)
+double gemm_flops(tdvp_ctx* ctx, const Views& v, int op, int site) {
+  double f = 0;
+  for (int r = v.r0; r < v.r0 + v.R; ++r) {
+    const auto& bd = ctx->rh[r].bd;
+    const double Dl = bd[site], Dr = bd[site + 1], d = ctx->d[site];
+    const double Wl = ctx->Wb[site], Wr = ctx->Wb[site + 1];
+    switch (op) {
+      case OP_MV1: case OP_EL1: case OP_HX1: f += Wl * Dl * d * Dr * Dl; break;
+      case OP_MV3: f += Wr * Dl * d * Dr * Dr; break;
+      case OP_EL3: f += Wr * Dr * Dr * Dl * d; break;
+      case OP_ER1: f += Wr * Dl * d * Dr * Dr; break;
+      case OP_ER3: f += Wl * Dl * Dl * d * Dr; break;
+      case OP_Z1: case OP_Z3: f += Wr * Dr * Dr * Dr; break;
+      case OP_ABS_L: { const double Dn = bd[site + 2 <= (int)bd.size() - 1 ? site + 2 : site + 1];
+                       f += Dr * Dr * ctx->d[site + 1] * Dn; break; }
+      case OP_ABS_R: { const double Dp = bd[site - 1]; f += Dp * ctx->d[site - 1] * Dl * Dl; break; }
+      case OP_TR1: f += Dl * Dl * d * Dr; break;
+      case OP_TR3: f += Dr * Dr * Dl * d; break;
+    }
+  }
+  return 8.0 * f;
+}
+
+int g_op(tdvp_ctx* ctx, const Views& v, int op, int site, int M, int Nn, int nb) {
+  LAUNCHC(TDVP_CAT_GEMM, launch_gemm(op, site, v.sd, v.wk, v.R, ctx->N, M, Nn, nb, ctx->st));
+  if (ctx->prof) ctx->stats.prof_flops[TDVP_CAT_GEMM] += gemm_flops(ctx, v, op, site);
+  return TDVP_OK;
+}
+
+int matvec_site(tdvp_ctx* ctx, const Views& v, int i, int first_op) {
+  const Dims m = maxdims(ctx, i, v);
+  const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
+  int rc;
+  if ((rc = g_op(ctx, v, first_op, i, m.Dl, d * m.Dr, Wl))) return rc;
+  LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply(0, i, first_op == OP_MV1 ? 1 : 0, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wr * d, ctx->st));
+  return g_op(ctx, v, OP_MV3, i, m.Dl * d, m.Dr, 1);
+}
+
+int matvec_bond(tdvp_ctx* ctx, const Views& v, int i) {
+  const Dims m = maxdims(ctx, i, v);
+  const int Wr = ctx->Wb[i + 1];
+  int rc;
+  if ((rc = g_op(ctx, v, OP_Z1, i, m.Dr, m.Dr, Wr))) return rc;
+  return g_op(ctx, v, OP_Z3, i, m.Dr, m.Dr, 1);
+}
+
+int env_left(tdvp_ctx* ctx, const Views& v, int i) {
+  const Dims m = maxdims(ctx, i, v);
+  const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
+  int rc;
+  if ((rc = g_op(ctx, v, OP_EL1, i, m.Dl, d * m.Dr, Wl))) return rc;
+  LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply(0, i, 0, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wr * d, ctx->st));
+  return g_op(ctx, v, OP_EL3, i, m.Dr, m.Dr, Wr);
+}
+
+int env_right(tdvp_ctx* ctx, const Views& v, int i) {
+  const Dims m = maxdims(ctx, i, v);
+  const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
+  int rc;
+  if ((rc = g_op(ctx, v, OP_ER1, i, m.Dl * d, m.Dr, Wr))) return rc;
+  LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply(1, i, 0, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wl * d, ctx->st));
+  return g_op(ctx, v, OP_ER3, i, m.Dl, m.Dl, Wl);
+}
+
+int qr_blocks(tdvp_ctx* ctx, int R, int m) {
+  int B = cdivi(m, 32);
+  B = std::max(1, std::min(B, 148));
+  B = std::min(B, std::max(1, ctx->qr_cap / std::max(1, R)));
+  return B;
+}
+
+// dir 0: C_i = L_i D (left-to-right), dir 1: C_i = D R_i (right-to-left); D lands in `bond`
+int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
+  const Dims m = maxdims(ctx, i, v);
+  const int d = ctx->d[i];
+  if (dir == 0) {
+    LAUNCHC(TDVP_CAT_QR, launch_transpose_site(1, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, ctx->st));
+    LAUNCHC(TDVP_CAT_QR, launch_row_qr(0, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, m.Dl * d), kRankRtol, 0, 0, ctx->st));
+    LAUNCHC(TDVP_CAT_QR, launch_transpose_site(0, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, ctx->st));
+  } else {
+    LAUNCHC(TDVP_CAT_QR, launch_row_qr(1, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, d * m.Dr), kRankRtol, 0, 0, ctx->st));
+  }
+  return TDVP_OK;
+}
+
+int nblk_for(long long n) {
+  long long nb = (n + 511) / 512;
+  return (int)std::max(1LL, std::min<long long>(nb, TDVP_MAX_VEC_BLOCKS));
+}
+
+// exp(i theta H) applied to the start vector `src` (0 = x, 1 = site tensor, 2 = bond) with
+// H = H[site] (kind 0) or the zero-site H0 of bond (site, site+1) (kind 1); the result goes to
+// `dst` (1 = site tensor, 2 = bond, 3 = w).  Returns TDVP_OK or an error; sets *notconv.
+int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
+         int* notconv) {
+  const Dims m = maxdims(ctx, site, v);
+  const long long n = kind == 0 ? (long long)m.Dl * ctx->d[site] * m.Dr : (long long)m.Dr * m.Dr;
+  LzArgs a;
+  a.sd = v.sd; a.wk = v.wk; a.R = v.R; a.N_sites = ctx->N; a.site = site; a.kind = kind;
+  a.src = src; a.dst = dst; a.theta = theta; a.tol = tol; a.kmax = ctx->kmax;
+  a.nblk = nblk_for(n); a.flags = v.flags;
+  int& kh = ctx->khist[2 * site + kind];
+  const int guess = kh > 0 ? kh : 6;
+  a.jcheck = ctx->check_every ? 1 : std::max(1, guess - 1);
+  CK(cudaMemsetAsync(v.flags, 0, sizeof(int) * v.R, ctx->st));
+  LAUNCHC(TDVP_CAT_LZVEC, launch_lz_start(a, ctx->st));
+  int j = 0, batch = guess, rc;
+  bool all_done = false;
+  while (j < ctx->kmax && !all_done) {
+    for (int q = 0; q < batch && j < ctx->kmax; ++q, ++j) {
+      if (kind == 0) { if ((rc = matvec_site(ctx, v, site, OP_MV1))) return rc; }
+      else if ((rc = matvec_bond(ctx, v, site))) return rc;
+      LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));
+      LAUNCHC(TDVP_CAT_TRIDIAG, launch_lz_iter_post(a, j, ctx->st));
+      ctx->stats.matvecs += v.R;
+    }
+    CK(cudaMemcpyAsync(ctx->h_flags + v.r0, v.flags, sizeof(int) * v.R, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->stats.host_syncs++;
+    all_done = true;
+    for (int r = 0; r < v.R; ++r) if (ctx->h_flags[v.r0 + r] == 0) all_done = false;
+    batch = 2;
+  }
+  LAUNCHC(TDVP_CAT_LZVEC, launch_lz_combine(a, ctx->st));
+  int kmaxr = 0;
+  for (int r = 0; r < v.R; ++r) {
+    const int f = ctx->h_flags[v.r0 + r];
+    if (f < 0) return fail(ctx, TDVP_ERR_NAN, "Lanczos: non-finite value or unsupported exponent");
+    if (f == 0) return fail(ctx, TDVP_ERR_KRYLOV_NOT_CONVERGED, "Lanczos: solve did not finish");
+    const int k = f & 0xffff;
+    if (f >> 16) { ctx->stats.not_converged++; if (notconv) *notconv = 1; }
+    kmaxr = std::max(kmaxr, k);
+    ctx->stats.krylov_dim_sum += k;
+    ctx->stats.krylov_dim_max = std::max(ctx->stats.krylov_dim_max, k);
+  }
+  ctx->stats.krylov_solves += v.R;
+  kh = kmaxr;
+  return TDVP_OK;
+}
+
+int check_device_errors(tdvp_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int) * ctx->R, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int r = 0; r < ctx->R; ++r)
+    if (ctx->h_err[r] != 0) {
+      const int code = ctx->h_err[r];
+      cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * ctx->R, ctx->st);
+      return fail(ctx, code == -5 ? TDVP_ERR_DEVICE_TIMEOUT : TDVP_ERR_INVALID_ARG,
+                  code == -5 ? "device barrier timed out" : "device kernel rejected its sizes");
+    }
+  return TDVP_OK;
+}
+
+int upload_tables(tdvp_ctx* ctx, int r) {
+  CK(cudaMemcpyAsync(ctx->d_sites + (size_t)r * ctx->N, ctx->h_sites.data() + (size_t)r * ctx->N,
+                     sizeof(SiteDev) * ctx->N, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->d_work + r, &ctx->h_work[r], sizeof(WorkDev), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return TDVP_OK;
+}
+
+// Allocate tensors, environments and work buffers of realisation r at bond dims bd.
+int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
+  RealHost& H = ctx->rh[r];
+  free_all(H.mps_allocs);
+  H.bd = bd;
+  const int N = ctx->N;
+  long long nmax = 1, Dmax = 1, mmax = 1;
+  int Wmax = 1;
+  for (int i = 0; i < N; ++i) {
+    const long long n = (long long)bd[i] * ctx->d[i] * bd[i + 1];
+    nmax = std::max(nmax, n);
+    Dmax = std::max<long long>(Dmax, std::max(bd[i], bd[i + 1]));
+    mmax = std::max<long long>(mmax, std::max<long long>((long long)bd[i] * ctx->d[i], (long long)ctx->d[i] * bd[i + 1]));
+    Wmax = std::max(Wmax, std::max(ctx->Wb[i], ctx->Wb[i + 1]));
+  }
+  nmax = std::max(nmax, Dmax * Dmax);
+  const long long ldV = (nmax + 31) / 32 * 32;
+  int rc;
+  for (int i = 0; i < N; ++i) {
+    SiteDev& S = ctx->h_sites[(size_t)r * N + i];
+    S.Dl = bd[i]; S.Dr = bd[i + 1];
+    if ((rc = dalloc(ctx, H.mps_allocs, &S.A, (size_t)S.Dl * S.d * S.Dr))) return rc;
+    if ((rc = dalloc(ctx, H.mps_allocs, &S.Lenv, (size_t)S.Wl * S.Dl * S.Dl))) return rc;
+    if ((rc = dalloc(ctx, H.mps_allocs, &S.Renv, (size_t)S.Wr * S.Dr * S.Dr))) return rc;
+  }
+  WorkDev& W = ctx->h_work[r];
+  W.ldV = ldV;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.x, nmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.w, nmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.V, (size_t)ldV * ctx->kmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.T1, (size_t)Wmax * nmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.T2, (size_t)Wmax * nmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.bond, (size_t)Dmax * Dmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.bond2, (size_t)Dmax * Dmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.scratch, nmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.part, (size_t)3 * TDVP_MAX_VEC_BLOCKS * (TDVP_KMAX_HARD + 2)))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.qpart, (size_t)3 * 148 * (Dmax + 4)))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.qhp, Dmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.colsq, mmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.obs, ctx->n_el + 4))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.ks, 1))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.bar, 2))) return rc;
+  W.err = ctx->d_err + r;
+  // boundary environments are the scalar 1
+  const zc one = zmake(1.0, 0.0);
+  CK(cudaMemcpyAsync(ctx->h_sites[(size_t)r * N].Lenv, &one, sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->h_sites[(size_t)r * N + N - 1].Renv, &one, sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
+  return upload_tables(ctx, r);
+}
+
+int build_right_envs(tdvp_ctx* ctx, const Views& v) {
+  for (int i = ctx->N - 1; i >= 1; --i) {
+    int rc = env_right(ctx, v, i);
+    if (rc) return rc;
+  }
+  return TDVP_OK;
+}
+
+bool all_ready(tdvp_ctx* ctx) {
+  if (ctx->N == 0) return false;
+  for (auto& h : ctx->rh) if (!h.mps) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site) {
+  if (!ctx) return TDVP_ERR_INVALID_ARG;
+  if (r < 0 || r >= ctx->R || D < 1 || D > 512) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps: bad r or D");
+  if (!ctx->rh[r].mpo) return fail(ctx, TDVP_ERR_STATE, "init_mps: build_mpo first");
+  if (exciton_site < 0 || exciton_site >= ctx->n_el) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps: bad exciton site");
+  CK(cudaSetDevice(ctx->dev));
+  const int N = ctx->N;
+  std::vector<int> bd(N + 1, 1);
+  for (int b = 1; b < N; ++b) {
+    double left = 1, right = 1;
+    for (int i = 0; i < b; ++i) left = std::min(left * ctx->d[i], 1e12);
+    for (int i = b; i < N; ++i) right = std::min(right * ctx->d[i], 1e12);
+    bd[b] = (int)std::min<double>(D, std::min(left, right));
+  }
+  int rc;
+  if ((rc = alloc_realisation(ctx, r, bd))) return rc;
+  // right-canonical product state: row 0 = occupied path, rows j>=1 = successive unit vectors,
+  // positions (s, r) ordered by r first, then s
+  for (int i = 0; i < N; ++i) {
+    const int Dl = bd[i], d = ctx->d[i], Dr = bd[i + 1];
+    const int occ = (ctx->is_el[i] && ctx->label[i] == exciton_site) ? 1 : 0;
+    std::vector<zc> A((size_t)Dl * d * Dr, zmake(0, 0));
+    A[((size_t)0 * d + occ) * Dr + 0] = zmake(1, 0);
+    int j = 1;
+    for (int rr = 0; rr < Dr && j < Dl; ++rr)
+      for (int s = 0; s < d && j < Dl; ++s) {
+        if (s == occ && rr == 0) continue;
+        A[((size_t)j * d + s) * Dr + rr] = zmake(1, 0);
+        ++j;
+      }
+    CK(cudaMemcpyAsync(ctx->h_sites[(size_t)r * N + i].A, A.data(), A.size() * sizeof(zc), cudaMemcpyHostToDevice,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  if ((rc = build_right_envs(ctx, one_view(ctx, r)))) return rc;
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->rh[r].mps = true;
+  return check_device_errors(ctx);
+}
+
+int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const double* re_im) {
+  if (!ctx) return TDVP_ERR_INVALID_ARG;
+  if (r < 0 || r >= ctx->R || !bond_dims || !re_im) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: bad args");
+  if (!ctx->rh[r].mpo) return fail(ctx, TDVP_ERR_STATE, "init_mps_tensors: build_mpo first");
+  CK(cudaSetDevice(ctx->dev));
+  const int N = ctx->N;
+  std::vector<int> bd(bond_dims, bond_dims + N + 1);
+  if (bd[0] != 1 || bd[N] != 1) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: open ends must be 1");
+  for (int i = 0; i < N; ++i) {
+    if (bd[i] < 1 || bd[i] > 512) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: bond dim out of range");
+    if (i > 0 && bd[i] > ctx->d[i] * bd[i + 1]) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: Dl > d*Dr");
+    if (bd[i + 1] > ctx->d[i] * bd[i]) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: Dr > Dl*d");
+  }
+  int rc;
+  if ((rc = alloc_realisation(ctx, r, bd))) return rc;
+  size_t off = 0;
+  for (int i = 0; i < N; ++i) {
+    const size_t n = (size_t)bd[i] * ctx->d[i] * bd[i + 1];
+    CK(cudaMemcpyAsync(ctx->h_sites[(size_t)r * N + i].A, re_im + 2 * off, n * sizeof(zc), cudaMemcpyHostToDevice,
+                       ctx->st));
+    off += n;
+  }
+  const Views v = one_view(ctx, r);
+  // right-canonicalise: C_i = D_i R_i from the last site, D_i absorbed into site i-1
+  for (int i = N - 1; i >= 1; --i) {
+    if ((rc = gauge_qr(ctx, v, i, 1))) return rc;
+    const Dims m = maxdims(ctx, i - 1, v);
+    if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
+    LAUNCH(launch_copy_vec(1, i - 1, v.sd, v.wk, v.R, N, m.Dl * ctx->d[i - 1] * m.Dr, ctx->st));
+  }
+  // normalise the centre: x = C/||C||, C <- x
+  {
+    LzArgs a{};
+    const Dims m = maxdims(ctx, 0, v);
+    a.sd = v.sd; a.wk = v.wk; a.R = 1; a.N_sites = N; a.site = 0; a.kind = 0; a.src = 1; a.dst = 1;
+    a.kmax = ctx->kmax; a.nblk = nblk_for((long long)m.Dl * ctx->d[0] * m.Dr); a.flags = v.flags;
+    LAUNCH(launch_lz_start(a, ctx->st));
+    LAUNCH(launch_copy_vec(1, 0, v.sd, v.wk, 1, N, m.Dl * ctx->d[0] * m.Dr, ctx->st));
+  }
+  if ((rc = build_right_envs(ctx, v))) return rc;
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->rh[r].mps = true;
+  return check_device_errors(ctx);
+}
+
+int tdvp_ps_step(tdvp_ctx* ctx, double dt_fs, int n_steps, int precision, int krylov_mode, double krylov_tol) {
+  if (!ctx) return TDVP_ERR_INVALID_ARG;
+  if (n_steps < 0 || !(krylov_tol >= 0) || !std::isfinite(dt_fs)) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: bad args");
+  if (precision != TDVP_PREC_FP64) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported precision");
+  if (krylov_mode != TDVP_KRYLOV_ADAPTIVE) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported krylov mode");
+  if (!all_ready(ctx)) return fail(ctx, TDVP_ERR_STATE, "ps_step: every realisation needs build_mpo and init");
+  CK(cudaSetDevice(ctx->dev));
+  const Views v = all_views(ctx);
+  const int N = ctx->N;
+  const double tau = dt_fs * kPhasePerCmFs;
+  int rc, nc = 0;
+  for (int step = 0; step < n_steps; ++step) {
+    if (N == 1) {
+      if ((rc = expm(ctx, v, 0, 0, 1, 1, -tau, krylov_tol, &nc))) return rc;
+    } else {
+      for (int i = 0; i < N - 1; ++i) {
+        if ((rc = expm(ctx, v, 0, i, i == 0 ? 1 : 0, 1, -0.5 * tau, krylov_tol, &nc))) return rc;
+        if ((rc = gauge_qr(ctx, v, i, 0))) return rc;
+        if ((rc = env_left(ctx, v, i))) return rc;
+        if ((rc = expm(ctx, v, 1, i, 2, 2, 0.5 * tau, krylov_tol, &nc))) return rc;
+        const Dims m = maxdims(ctx, i + 1, v);
+        if ((rc = g_op(ctx, v, OP_ABS_L, i, m.Dl, ctx->d[i + 1] * m.Dr, 1))) return rc;
+      }
+      if ((rc = expm(ctx, v, 0, N - 1, 0, 1, -tau, krylov_tol, &nc))) return rc;
+      for (int i = N - 1; i >= 1; --i) {
+        if ((rc = gauge_qr(ctx, v, i, 1))) return rc;
+        if ((rc = env_right(ctx, v, i))) return rc;
+        if ((rc = expm(ctx, v, 1, i - 1, 2, 2, 0.5 * tau, krylov_tol, &nc))) return rc;
+        const Dims m = maxdims(ctx, i - 1, v);
+        if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
+        if ((rc = expm(ctx, v, 0, i - 1, 0, 1, -0.5 * tau, krylov_tol, &nc))) return rc;
+      }
+    }
+    ctx->stats.steps++;
+    ctx->stats.site_updates += (long long)(2 * N - 1) * ctx->R;
+  }
+  if ((rc = check_device_errors(ctx))) return rc;
+  if (ctx->prof && (rc = prof_collect(ctx))) return rc;
+  if (nc) return fail(ctx, TDVP_ERR_KRYLOV_NOT_CONVERGED, "some Lanczos solve stopped at kmax above the tolerance");
+  return TDVP_OK;
+}
+
+int tdvp_observables(tdvp_ctx* ctx, int r, double* pops, double* energy, double* norm) {
+  if (!ctx) return TDVP_ERR_INVALID_ARG;
+  if (r < 0 || r >= ctx->R) return fail(ctx, TDVP_ERR_INVALID_ARG, "observables: bad r");
+  if (!ctx->rh[r].mps) return fail(ctx, TDVP_ERR_STATE, "observables: not initialised");
+  CK(cudaSetDevice(ctx->dev));
+  const Views v = one_view(ctx, r);
+  const int N = ctx->N, M = ctx->n_el;
+  int rc;
+  LAUNCH(launch_set_identity_bond2(v.wk, 1, 1, ctx->st));
+  for (int i = 0; i < N; ++i) {
+    const Dims m = maxdims(ctx, i, v);
+    if ((rc = g_op(ctx, v, OP_TR1, i, m.Dl, ctx->d[i] * m.Dr, 1))) return rc;
+    if (ctx->is_el[i]) LAUNCH(launch_obs_local(i, ctx->label[i], v.sd, v.wk, 1, N, ctx->st));
+    if ((rc = g_op(ctx, v, OP_TR3, i, m.Dr, m.Dr, 1))) return rc;
+  }
+  LAUNCH(launch_obs_norm(N - 1, M, v.wk, 1, ctx->st));
+  // energy: <C|H[0]|C>/<C|C> at the centre (site 0)
+  LAUNCH(launch_reset_ks(v.wk, 1, ctx->st));
+  if ((rc = matvec_site(ctx, v, 0, OP_HX1))) return rc;
+  LAUNCH(launch_obs_energy(M + 1, v.sd, v.wk, 1, N, ctx->st));
+  double* h = ctx->h_obs + (size_t)r * (M + 4);
+  CK(cudaMemcpyAsync(h, ctx->h_work[r].obs, sizeof(double) * (M + 3), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  const double nn = h[M];
+  if (pops) for (int m = 0; m < M; ++m) pops[m] = h[m] / nn;
+  if (norm) *norm = std::sqrt(std::max(nn, 0.0));
+  if (energy) *energy = h[M + 1] / h[M + 2];
+  return check_device_errors(ctx);
+}
+
+int tdvp_chain_info(tdvp_ctx* ctx, int r, int* n_sites, int* phys_dims, int* bond_dims, int* mpo_dims) {
+  if (!ctx || r < 0 || r >= ctx->R) return TDVP_ERR_INVALID_ARG;
+  if (ctx->N == 0) return fail(ctx, TDVP_ERR_STATE, "chain_info: build_mpo first");
+  if (n_sites) *n_sites = ctx->N;
+  if (phys_dims) std::copy(ctx->d.begin(), ctx->d.end(), phys_dims);
+  if (mpo_dims) std::copy(ctx->Wb.begin(), ctx->Wb.end(), mpo_dims);
+  if (bond_dims) {
+    if (!ctx->rh[r].mps) return fail(ctx, TDVP_ERR_STATE, "chain_info: not initialised");
+    std::copy(ctx->rh[r].bd.begin(), ctx->rh[r].bd.end(), bond_dims);
+  }
+  return TDVP_OK;
+}
+
+int tdvp_get_site(tdvp_ctx* ctx, int r, int i, double* re_im) {
+  if (!ctx || r < 0 || r >= ctx->R || !re_im) return TDVP_ERR_INVALID_ARG;
+  if (!ctx->rh[r].mps || i < 0 || i >= ctx->N) return fail(ctx, TDVP_ERR_INVALID_ARG, "get_site: bad site");
+  CK(cudaSetDevice(ctx->dev));
+  const SiteDev& S = ctx->h_sites[(size_t)r * ctx->N + i];
+  CK(cudaMemcpyAsync(re_im, S.A, sizeof(zc) * (size_t)S.Dl * S.d * S.Dr, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return TDVP_OK;
+}
+
+int tdvp_move_center(tdvp_ctx* ctx, int r, int site) {
+  if (!ctx || r < 0 || r >= ctx->R) return TDVP_ERR_INVALID_ARG;
+  if (!ctx->rh[r].mps || site < 0 || site >= ctx->N) return fail(ctx, TDVP_ERR_INVALID_ARG, "move_center: bad site");
+  CK(cudaSetDevice(ctx->dev));
+  const Views v = one_view(ctx, r);
+  int rc;
+  for (int i = 0; i < site; ++i) {
+    if ((rc = gauge_qr(ctx, v, i, 0))) return rc;
+    if ((rc = env_left(ctx, v, i))) return rc;
+    const Dims m = maxdims(ctx, i + 1, v);
+    if ((rc = g_op(ctx, v, OP_ABS_L, i, m.Dl, ctx->d[i + 1] * m.Dr, 1))) return rc;
+    LAUNCH(launch_copy_vec(1, i + 1, v.sd, v.wk, 1, ctx->N, m.Dl * ctx->d[i + 1] * m.Dr, ctx->st));
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  return check_device_errors(ctx);
+}
+
+int tdvp_center_to_zero(tdvp_ctx* ctx, int r) {
+  if (!ctx || r < 0 || r >= ctx->R) return TDVP_ERR_INVALID_ARG;
+  if (!ctx->rh[r].mps) return fail(ctx, TDVP_ERR_STATE, "center_to_zero: not initialised");
+  CK(cudaSetDevice(ctx->dev));
+  const Views v = one_view(ctx, r);
+  int rc;
+  for (int i = ctx->N - 1; i >= 1; --i) {
+    if ((rc = gauge_qr(ctx, v, i, 1))) return rc;
+    if ((rc = env_right(ctx, v, i))) return rc;
+    const Dims m = maxdims(ctx, i - 1, v);
+    if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
+    LAUNCH(launch_copy_vec(1, i - 1, v.sd, v.wk, 1, ctx->N, m.Dl * ctx->d[i - 1] * m.Dr, ctx->st));
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  return check_device_errors(ctx);
+}
+
+int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, const double* x, double* y) {
+  if (!ctx || r < 0 || r >= ctx->R || !x || !y) return TDVP_ERR_INVALID_ARG;
+  if (!ctx->rh[r].mps || i < 0 || i >= ctx->N) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_heff: bad site");
+  CK(cudaSetDevice(ctx->dev));
+  const Views v = one_view(ctx, r);
+  const SiteDev& S = ctx->h_sites[(size_t)r * ctx->N + i];
+  const size_t n = (size_t)S.Dl * S.d * S.Dr;
+  CK(cudaMemcpyAsync(ctx->h_work[r].x, x, n * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
+  LAUNCH(launch_reset_ks(v.wk, 1, ctx->st));
+  int rc;
+  if ((rc = matvec_site(ctx, v, i, OP_MV1))) return rc;
+  CK(cudaMemcpyAsync(y, ctx->h_work[r].w, n * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return TDVP_OK;
+}
+
+int tdvp_debug_qr(tdvp_ctx* ctx, int m, int n, const double* C, double* Q, double* Rout) {
+  if (!ctx || !C || !Q || !Rout || n < 1 || m < n) return TDVP_ERR_INVALID_ARG;
+  if (!ctx->rh[0].mps) return fail(ctx, TDVP_ERR_STATE, "debug_qr: realisation 0 must be initialised");
+  CK(cudaSetDevice(ctx->dev));
+  // the kernel works on rows: X = C^T (n x m)
+  long long nmax = 1, Dmax = 1, mmax = 1;
+  const auto& bd = ctx->rh[0].bd;
+  for (int i = 0; i < ctx->N; ++i) {
+    nmax = std::max(nmax, (long long)bd[i] * ctx->d[i] * bd[i + 1]);
+    Dmax = std::max<long long>(Dmax, std::max(bd[i], bd[i + 1]));
+    mmax = std::max<long long>(mmax, std::max<long long>((long long)bd[i] * ctx->d[i], (long long)ctx->d[i] * bd[i + 1]));
+  }
+  if ((long long)m * n > nmax || n > Dmax || m > mmax || n > 512)
+    return fail(ctx, TDVP_ERR_INVALID_ARG, "debug_qr: matrix larger than the work buffers");
+  std::vector<zc> X((size_t)n * m);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < n; ++b) X[(size_t)b * m + a] = zmake(C[2 * ((size_t)a * n + b)], C[2 * ((size_t)a * n + b) + 1]);
+  const Views v = one_view(ctx, 0);
+  CK(cudaMemcpyAsync(ctx->h_work[0].scratch, X.data(), X.size() * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
+  LAUNCH(launch_row_qr(2, 0, v.sd, v.wk, 1, ctx->N, qr_blocks(ctx, 1, m), kRankRtol, n, m, ctx->st));
+  std::vector<zc> R((size_t)n * n);
+  CK(cudaMemcpyAsync(X.data(), ctx->h_work[0].scratch, X.size() * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(R.data(), ctx->h_work[0].bond, R.size() * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < n; ++b) {
+      Q[2 * ((size_t)a * n + b)] = X[(size_t)b * m + a].x;
+      Q[2 * ((size_t)a * n + b) + 1] = X[(size_t)b * m + a].y;
+    }
+  std::memcpy(Rout, R.data(), R.size() * sizeof(zc));
+  return check_device_errors(ctx);
+}
+
+int tdvp_debug_expm(tdvp_ctx* ctx, int r, int i, double z_re, double z_im, double tol, const double* vin,
+                    double* out, int* k_out) {
+  if (!ctx || r < 0 || r >= ctx->R || !vin || !out) return TDVP_ERR_INVALID_ARG;
+  if (z_re != 0.0) return fail(ctx, TDVP_ERR_INVALID_ARG, "debug_expm: exponent must be purely imaginary");
+  if (!ctx->rh[r].mps || i < 0 || i >= ctx->N) return fail(ctx, TDVP_ERR_INVALID_ARG, "debug_expm: bad site");
+  CK(cudaSetDevice(ctx->dev));
+  const Views v = one_view(ctx, r);
+  const SiteDev& S = ctx->h_sites[(size_t)r * ctx->N + i];
+  const size_t n = (size_t)S.Dl * S.d * S.Dr;
+  CK(cudaMemcpyAsync(ctx->h_work[r].x, vin, n * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
+  int nc = 0, rc;
+  const int saved = ctx->khist[2 * i];
+  if ((rc = expm(ctx, v, 0, i, 0, 3, z_im, tol, &nc))) return rc;
+  if (k_out) *k_out = ctx->h_flags[r] & 0xffff;
+  ctx->khist[2 * i] = saved;
+  CK(cudaMemcpyAsync(out, ctx->h_work[r].w, n * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return TDVP_OK;
+}
+
+int tdvp_stats(tdvp_ctx* ctx, tdvp_stats_t* out) {
+  if (!ctx || !out) return TDVP_ERR_INVALID_ARG;
+  *out = ctx->stats;
+  return TDVP_OK;
+}
+
+void tdvp_reset_stats(tdvp_ctx* ctx) {
+  if (ctx) ctx->stats = tdvp_stats_t{};
+}
+
+int tdvp_set_profiling(tdvp_ctx* ctx, int on) {
+  if (!ctx) return TDVP_ERR_INVALID_ARG;
+  if (!on && ctx->prof) {
+    int rc = prof_collect(ctx);
+    if (rc) return rc;
+  }
+  ctx->prof = on ? 1 : 0;
+  return TDVP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// Internal declarations shared by the CUDA translation units of libtdvp.
+//
+// Layout conventions (row-major, complex interleaved as double2):
+//   site tensor        A[l][s][r]                   Dl*d*Dr
+//   left environment   L[w][l'][l]   (sites < i)    Wl*Dl*Dl   (h[1:i-1] of Eq. tdvp1_h1i)
+//   right environment  R[w][r'][r]   (sites > i)    Wr*Dr*Dr   (h[i+1:N] of Eq. tdvp1_hiN)
+//   MPO                W[w][w'][s'][s]               (Eq. mpo; s' is the bra index)
+//   contraction scratch T[c][x][s][y] with channel c, x = left bond, y = right bond.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+typedef double2 zc;
+
+#define TDVP_KMAX_HARD 128        // largest Krylov dimension supported
+#define TDVP_VEC_THREADS 256      // threads of the Lanczos vector kernels
+#define TDVP_MAX_VEC_BLOCKS 160   // chunks per vector (bounds the partial-sum table)
+#define TDVP_QR_THREADS 256
+
+__host__ __device__ __forceinline__ zc zmake(double re, double im) { return make_double2(re, im); }
+__host__ __device__ __forceinline__ zc zadd(zc a, zc b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ zc zsub(zc a, zc b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ zc zconj(zc a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ zc zscale(zc a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ zc zmul(zc a, zc b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b
+__host__ __device__ __forceinline__ zc zfma(zc a, zc b, zc acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc + conj(a)*b
+__host__ __device__ __forceinline__ zc zcfma(zc a, zc b, zc acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+// acc - a*b
+__host__ __device__ __forceinline__ zc zfms(zc a, zc b, zc acc) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+__host__ __device__ __forceinline__ double zabs2(zc a) { return a.x * a.x + a.y * a.y; }
+
+// Sparse MPO action used by the middle contraction stage:
+//   out[co][x][so][y] = sum_e val[e] * in[ci[e]][x][si[e]][y],  e in row (co*d + so).
+struct WCsr {
+  const int* ptr;     // [n_out*d + 1]
+  const int* ci;      // input channel
+  const int* si;      // input local index
+  const double* val;  // coefficient (the Hamiltonian is real)
+};
+
+// One site of one realisation.
+struct SiteDev {
+  zc* A;        // [Dl][d][Dr]
+  zc* Lenv;     // [Wl][Dl][Dl]
+  zc* Renv;     // [Wr][Dr][Dr]
+  int Dl, d, Dr, Wl, Wr;
+  WCsr fw;      // rows (w', s'), entries (w, s): used in H_eff.A and the left environment
+  WCsr bw;      // rows (w, s'), entries (w', s): used in the right environment
+};
+
+// Krylov (Lanczos) state of one realisation for the exponential in flight.
+struct KState {
+  double alpha[TDVP_KMAX_HARD];
+  double beta[TDVP_KMAX_HARD];
+  zc coef[TDVP_KMAX_HARD];     // ||v|| * exp(z T_k) e_1 once done
+  double nrm;                  // ||v|| of the start vector
+  double inv_beta;             // 1/beta_j of the last accepted step
+  double err;                  // last a-posteriori estimate
+  int k;                       // Krylov dimension when done
+  int done;                    // 1: the remaining iteration kernels of this solve are no-ops
+  int kcap;                    // min(kmax, vector length)
+  int n;                       // vector length of the solve
+  int notconv;                 // stopped at kcap above tolerance
+  int status;                  // 0 ok, TDVP_ERR_NAN ...
+  int pad[2];
+};
+
+// Per-realisation work buffers.
+struct WorkDev {
+  zc* x;        // matvec input (current Krylov vector)            [nmax]
+  zc* w;        // matvec output / residual                        [nmax]
+  zc* V;        // Krylov basis, V_t = V + t*ldV                   [kmax*ldV]
+  long long ldV;
+  zc* T1;       // contraction scratch                             [Wmax*nmax]
+  zc* T2;       // contraction scratch                             [Wmax*nmax]
+  zc* bond;     // bond matrix D                                   [Dmax*Dmax]
+  zc* bond2;    // second square buffer (transfer matrices)        [Dmax*Dmax]
+  zc* scratch;  // QR transpose buffer                             [nmax]
+  zc* part;     // partial sums, 3 tables of [TDVP_MAX_VEC_BLOCKS][TDVP_KMAX_HARD+2]
+  zc* qpart;    // QR partial sums [qr_blocks][Dmax+4] x 3
+  zc* qhp;      // QR completion coefficients [Dmax]
+  double* colsq;// QR column norms [d*Dmax]
+  double* obs;  // observables: [n_el] <n>, then <Psi|Psi>, energy numerator
+  KState* ks;
+  unsigned* bar;// [0]=count, [1]=generation of the QR group barrier
+  int* err;     // device-side error flag of this realisation
+};
+
+// Operation selectors of the batched complex GEMM (descriptors are derived on the device).
+enum GemmOp {
+  OP_MV1 = 0,   // T1[w] = L_w x                     (H_eff stage 1)
+  OP_MV3,       // w = sum_w' T2[w'] R_w'^T           (H_eff stage 3)
+  OP_EL1,       // T1[w] = L_w A                     (left environment stage 1)
+  OP_EL3,       // Lnew_w' = A^H T2[w']              (left environment stage 3)
+  OP_ER1,       // T1[w'] = A R_w'^T                 (right environment stage 1)
+  OP_ER3,       // Rnew_w = conj(A) T2[w]^T          (right environment stage 3)
+  OP_Z1,        // T1[w] = Lb_w x                    (zero-site stage 1)
+  OP_Z3,        // w = sum_w T1[w] Rb_w^T            (zero-site stage 2)
+  OP_ABS_L,     // x = D A_{i+1}                     (gauge centre moves right)
+  OP_ABS_R,     // x = A_{i-1} D                     (gauge centre moves left)
+  OP_TR1,       // T1 = E A                          (transfer pass, norm/populations)
+  OP_TR3,       // E' = A^H T1
+  OP_HX1,       // T1[w] = L_w A  with x = site tensor (energy: H_eff C)
+};
+
+struct GemmDesc {
+  const zc* A;
+  const zc* B;
+  zc* C;
+  int M, N, K;
+  int lda, ldb, ldc;
+  int nz;                 // inner sum: C = sum_z op(A_z) op(B_z)
+  long long sAz, sBz;
+  int opA, opB;           // 0: as stored, 1: transpose, 2: conjugate transpose, 3: conjugate
+  const int* skip;        // if non-null and *skip != 0 the block does nothing
+};
+
+struct Ctx;  // host context (tdvp_ctx.cu)
+
+// Kernel launchers (each returns the cudaError_t of the launch).
+cudaError_t launch_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                        int maxM, int maxN, int nbatch, cudaStream_t st);
+cudaError_t launch_wapply(int dir, int site, int lanczos, const SiteDev* sd, const WorkDev* wk, int R,
+                          int N_sites, int max_xy, int n_rows, cudaStream_t st);
+cudaError_t launch_transpose_site(int to_scratch, int site, const SiteDev* sd, const WorkDev* wk, int R,
+                                  int N_sites, int maxRows, int maxCols, cudaStream_t st);
+
+// Lanczos (kind: 0 = site vector of `site`, 1 = bond matrix between `site` and `site+1`).
+struct LzArgs {
+  const SiteDev* sd;
+  const WorkDev* wk;
+  int R, N_sites, site, kind;
+  int src;          // start vector: 0 = x buffer, 1 = site tensor, 2 = bond buffer
+  int dst;          // result: 1 = site tensor, 2 = bond buffer, 3 = w buffer
+  double theta;     // z = i*theta (purely imaginary exponent)
+  double tol;
+  int kmax;
+  int jcheck;       // convergence is tested only once k >= jcheck
+  int nblk;         // chunks per vector (max over realisations)
+  int* flags;       // [R] device: Krylov dimension once a solve is done, -1 on failure
+};
+cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st);
+cudaError_t launch_lz_iter_pre(const LzArgs& a, int j, cudaStream_t st);   // orthogonalisation
+cudaError_t launch_lz_iter_post(const LzArgs& a, int j, cudaStream_t st);  // tridiagonal exp, next vector
+cudaError_t launch_lz_combine(const LzArgs& a, cudaStream_t st);
+
+// QR of the gauge shift (dir 0: left-to-right on site tensor via transpose scratch, result
+// L = Q in A[site], D = R in bond; dir 1: right-to-left LQ in place, D = L-factor in bond;
+// dir 2: debug matrix in scratch (n x m rows), R to bond).
+cudaError_t launch_row_qr(int dir, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                          int blocks_per_r, double rtol, int dbg_n, int dbg_m, cudaStream_t st);
+int qr_max_coresident_blocks(int device);
+
+// Observables helpers.
+cudaError_t launch_set_identity_bond2(const WorkDev* wk, int R, int n, cudaStream_t st);
+cudaError_t launch_obs_local(int site, int slot, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                             cudaStream_t st);
+cudaError_t launch_obs_norm(int site, int slot, const WorkDev* wk, int R, cudaStream_t st);
+cudaError_t launch_obs_energy(int slot, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                              cudaStream_t st);
+cudaError_t launch_copy_vec(int what, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                            int maxn, cudaStream_t st);
+cudaError_t launch_reset_ks(const WorkDev* wk, int R, cudaStream_t st);

@@ -1,0 +1,38 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry point of include/tdvp.h."""
+import os
+import re
+
+import pytest
+
+import paper_1907_12044_b300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(tdvp_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = pkg.build()
+    assert os.path.exists(path)
+    lib = pkg.load_library()
+    declared = _declared()
+    assert len(declared) >= 17
+    missing = [n for n in declared if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(pkg.EXPORTED_SYMBOLS) == declared
+
+
+def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):
+    import paper_1907_12044_b300._lib as L
+    monkeypatch.setattr(L, "_LIB", None)
+    monkeypatch.setattr(L, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        L.load_library()

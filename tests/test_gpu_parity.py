@@ -1,0 +1,231 @@
+"""CUDA path vs CPU oracle, element by element on the same seeded inputs (FP64 path).
+
+Tolerances: the FP64 kernels follow the oracle's arithmetic up to summation order, so single
+operations agree to ~1e-13 relative; whole time steps are compared on populations with the
+bound max_n |dP_n| / max_n P_n <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from workloads import PHASE_PER_CM_FS
+from oracle import (qr_rr, lanczos_expm, heff_apply, env_left, env_right, TDVPState, tdvp_ps_step,
+                    populations, energy)
+from oracle.dense import hamiltonian_kron, product_state, propagate_exact, populations_dense
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1907_12044_b300 as pkg  # noqa: E402
+from gpu_util import engine_for, oracle_from_gpu_tensors, rel_pop_err  # noqa: E402
+
+POP_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def c1_random():
+    p = wl.fmo_sized()
+    tens = wl.random_mps_tensors(p.phys_dims(), 64, seed=21)
+    eng = engine_for(p, tensors=tens)
+    return p, eng
+
+
+# ------------------------------------------------------------------ gauge-shift QR (Eq. QR)
+
+@pytest.mark.parametrize("m,n", [(640, 64), (100, 37), (33, 33), (40, 12), (257, 5), (64, 1)])
+def test_qr_full_rank_matches_oracle(c1_random, m, n):
+    _, eng = c1_random
+    rng = np.random.default_rng(m * 1000 + n)
+    C = rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n))
+    Q, R = eng.debug_qr(C)
+    Qo, Ro = qr_rr(C)
+    assert np.abs(Q - Qo).max() < 1e-12
+    assert np.abs(R - Ro).max() < 1e-12 * np.abs(Ro).max()
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() < 1e-13
+
+
+def test_qr_rank_deficient_matches_oracle(c1_random):
+    _, eng = c1_random
+    rng = np.random.default_rng(5)
+    cases = []
+    X = (rng.normal(size=(200, 5)) + 1j * rng.normal(size=(200, 5))) @ rng.normal(size=(5, 20))
+    cases.append(X)
+    Z = np.zeros((64, 8), complex)
+    cases.append(Z)
+    E = np.zeros((30, 6), complex)
+    E[2, 0] = 2.0
+    E[2, 1] = 1.0
+    E[7, 3] = 1j
+    cases.append(E)
+    for C in cases:
+        Q, R = eng.debug_qr(C)
+        Qo, Ro = qr_rr(C)
+        assert np.abs(Q - Qo).max() < 1e-12
+        assert np.abs(R - Ro).max() < 1e-11 * max(1.0, np.abs(Ro).max())
+
+
+# ------------------------------------------------------------------ H_eff and Lanczos at full size
+
+@pytest.mark.parametrize("site", [0, 5, 38, 76])
+def test_heff_and_expm_match_oracle_at_c1_sites(c1_random, site):
+    p, eng = c1_random
+    eng.move_center(0, site)
+    try:
+        mps = eng.get_mps(0)
+        W = TDVPState.start(p, D=1).W
+        L = np.ones((1, 1, 1), complex)
+        for j in range(site):
+            L = env_left(L, mps[j], W[j])
+        R = np.ones((1, 1, 1), complex)
+        for j in range(len(mps) - 1, site, -1):
+            R = env_right(R, mps[j], W[j])
+        rng = np.random.default_rng(site)
+        x = rng.normal(size=mps[site].shape) + 1j * rng.normal(size=mps[site].shape)
+        y = eng.apply_heff(0, site, x)
+        yo = heff_apply(L, W[site], R, x)
+        assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
+        C = mps[site]
+        tau = 10.0 * PHASE_PER_CM_FS / 2
+        out, k = eng.debug_expm(0, site, -1j * tau, 1e-12, C)
+        ks = []
+        outo = lanczos_expm(lambda v: heff_apply(L, W[site], R, v), C, -1j * tau, 1e-12, 64, stats=ks)
+        # the Krylov dimension at which the a-posteriori estimate first meets the tolerance may
+        # differ near its rounding floor; the exponentials themselves must agree
+        assert 1 <= k <= 64 and 1 <= ks[0] <= 64
+        assert np.abs(out - outo).max() <= 1e-10 * np.abs(outo).max()
+    finally:
+        eng.center_to_zero(0)
+
+
+# ------------------------------------------------------------------ whole time steps
+
+def test_full_bond_dim_tiny_chain_is_exact_on_gpu():
+    p = wl.tiny_chain()
+    eng = engine_for(p, D=32)
+    H = hamiltonian_kron(p)
+    times = 10.0 * np.arange(1, 101)
+    exact = propagate_exact(H, product_state(p), times)
+    worst = 0.0
+    for s in range(100):
+        eng.step(10.0)
+        P, E, nrm = eng.observables(0)
+        worst = max(worst, np.abs(P - populations_dense(exact[s], p)).max())
+    assert worst <= POP_TOL
+
+
+@pytest.mark.parametrize("start", ["product", "random"])
+def test_truncated_tiny_chain_matches_oracle(start):
+    p = wl.tiny_chain()
+    if start == "product":
+        eng = engine_for(p, D=16)
+        st = TDVPState.start(p, D=16)
+    else:
+        tens = wl.random_mps_tensors(p.phys_dims(), 16, seed=9)
+        eng = engine_for(p, tensors=tens)
+        st = TDVPState.start(p, tensors=tens)
+    for s in range(20):
+        eng.step(10.0)
+        tdvp_ps_step(st, 10.0)
+        P, E, nrm = eng.observables(0)
+        assert rel_pop_err(P, populations(st, p)) <= POP_TOL
+        assert abs(E - energy(st)) <= 1e-9 * max(1.0, abs(energy(st)))
+
+
+@pytest.mark.parametrize("start", ["product", "random"])
+def test_fmo_sized_step_matches_oracle(start):
+    p = wl.fmo_sized()
+    if start == "product":
+        eng = engine_for(p, D=64)
+        st = TDVPState.start(p, D=64)
+    else:
+        tens = wl.random_mps_tensors(p.phys_dims(), 64, seed=33)
+        eng = engine_for(p, tensors=tens)
+        st = TDVPState.start(p, tensors=tens)
+    eng.step(10.0)
+    tdvp_ps_step(st, 10.0)
+    P, E, nrm = eng.observables(0)
+    Po = populations(st, p)
+    assert rel_pop_err(P, Po) <= POP_TOL
+    assert abs(E - energy(st)) <= 1e-9 * max(1.0, abs(energy(st)))
+    assert abs(nrm - 1.0) < 1e-10
+
+
+def test_fmo_sized_invariants_over_steps():
+    p = wl.fmo_sized()
+    eng = engine_for(p, D=64)
+    _, E0, _ = eng.observables(0)
+    for _ in range(3):
+        eng.step(10.0)
+        P, E, nrm = eng.observables(0)
+        assert abs(nrm - 1.0) < 1e-10
+        assert abs(P.sum() - 1.0) < 1e-10
+        assert abs(E - E0) < 1e-8 * max(1.0, abs(E0))
+
+
+def test_rabi_and_single_site_edge_cases():
+    p = wl.two_level_rabi()
+    eng = engine_for(p, D=2)
+    Om = np.sqrt((p.E[0] - p.E[1]) ** 2 + 4 * p.J[0, 1] ** 2)
+    for s in range(1, 21):
+        eng.step(10.0)
+        t = 10.0 * s * PHASE_PER_CM_FS
+        P1 = 1 - 4 * p.J[0, 1] ** 2 / Om ** 2 * np.sin(Om * t / 2) ** 2
+        assert abs(eng.observables(0)[0][0] - P1) < 1e-11
+    # one electronic site, no modes: a single-site chain (N = 1)
+    q = wl.FHParams(E=np.array([12400.0]), J=np.zeros((1, 1)), omega=[np.zeros(0)], g=[np.zeros(0)],
+                    n_levels=[np.zeros(0, int)], el_order=[0], exciton_site=0, energy_offset=12000.0)
+    eng1 = engine_for(q, D=1)
+    eng1.step(10.0, n_steps=3)
+    P, E, nrm = eng1.observables(0)
+    assert abs(P[0] - 1.0) < 1e-14 and abs(E - 400.0) < 1e-10 and abs(nrm - 1) < 1e-14
+
+
+def test_bond_dim_one_product_dynamics():
+    p = wl.tiny_chain()
+    eng = engine_for(p, D=1)
+    st = TDVPState.start(p, D=1)
+    for _ in range(5):
+        eng.step(10.0)
+        tdvp_ps_step(st, 10.0)
+    assert rel_pop_err(eng.observables(0)[0], populations(st, p)) <= POP_TOL
+
+
+def test_batched_ragged_realisations_match_single_runs():
+    base = wl.tiny_chain()
+    Ds = [4, 16, 8]
+    params = [wl.disorder_realisation(base, r) for r in range(3)]
+    eng = pkg.Engine(n_realisations=3)
+    for r, (q, D) in enumerate(zip(params, Ds)):
+        eng.build_mpo(r, q)
+        eng.init_mps(r, D, q.exciton_site)
+    states = [TDVPState.start(q, D=D) for q, D in zip(params, Ds)]
+    for _ in range(5):
+        eng.step(10.0)
+        for st in states:
+            tdvp_ps_step(st, 10.0)
+    for r, (q, st) in enumerate(zip(params, states)):
+        assert rel_pop_err(eng.observables(r)[0], populations(st, q)) <= POP_TOL
+
+
+def test_errors_are_reported_not_crashing():
+    p = wl.tiny_chain()
+    eng = pkg.Engine()
+    with pytest.raises(pkg.TDVPError) as e:
+        eng.step(10.0)
+    assert e.value.code == -7
+    eng.build_mpo(0, p)
+    with pytest.raises(pkg.TDVPError) as e:
+        eng.init_mps(0, 0, 0)
+    assert e.value.code == -1
+    bad = wl.tiny_chain()
+    bad.J = np.array([[0.0, 1.0], [2.0, 0.0]])
+    eng2 = pkg.Engine()
+    with pytest.raises(pkg.TDVPError):
+        eng2.build_mpo(0, bad)
+    eng.init_mps(0, 8, 0)
+    with pytest.raises(pkg.TDVPError) as e:
+        eng.step(10.0, precision=99)
+    assert e.value.code == -1
