@@ -182,6 +182,32 @@ int tdvp_set_profiling(tdvp_ctx* ctx, int on);
 int tdvp_stats(tdvp_ctx* ctx, tdvp_stats_t* out);
 void tdvp_reset_stats(tdvp_ctx* ctx);
 
+/* Right-to-left gauge shift without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory themselves or have
+ * it allocated for them, e.g. code running inside a framework that owns every byte of device
+ * memory through its own pool, or a latency-critical path where the implicit device
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.
+ *
+ * Computes X = L Q for X (n x m, row-major complex, interleaved, device memory), with Q
+ * (n x m, device) having orthonormal rows and L (n x n, device) lower triangular, by the same
+ * rule as the library's gauge shift: rows orthogonalised in order by Gram-Schmidt with one
+ * re-orthogonalisation pass; a row whose residual is <= 1e-13 ||X||_F gets L[j][j] = 0 and is
+ * replaced by the first unit vector at distance >= 1/2 from the rows so far.  No context is
+ * needed; the work runs on the current device and `cuda_stream`, and the call returns after it
+ * has finished (it synchronises the stream).
+ *
+ * Limits: 1 <= n <= 256, n <= m <= 16384; anything else returns TDVP_ERR_INVALID_ARG without
+ * touching the device.  X must not overlap Q or L.
+ *
+ * Memory: the scratch space (partial sums, column norms, barrier words; about 0.9 MB) is one
+ * static device array of fixed size in the library, held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up its address
+ * (cudaGetSymbolAddress) and the co-resident block count; make that first call before any
+ * stream capture.  All calls on a device share that one array, so calls that overlap on the
+ * GPU (other streams, other host threads) race and give wrong results; serialise them.
+ * Returns TDVP_ERR_DEVICE_TIMEOUT if a bounded device-side wait gave up. */
+int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* cuda_stream);
+
 const char* tdvp_last_error(const tdvp_ctx* ctx);
 void tdvp_destroy(tdvp_ctx* ctx);
 

@@ -22,6 +22,7 @@ EXPORTED_SYMBOLS = [
     "tdvp_observables", "tdvp_chain_info", "tdvp_get_site", "tdvp_move_center",
     "tdvp_center_to_zero", "tdvp_apply_heff", "tdvp_debug_qr", "tdvp_debug_expm", "tdvp_stats",
     "tdvp_reset_stats", "tdvp_last_error", "tdvp_destroy", "tdvp_set_profiling",
+    "tdvp_lq_noalloc",
 ]
 
 
@@ -86,6 +87,7 @@ def load_library():
     lib.tdvp_debug_expm.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, ip]
     lib.tdvp_stats.argtypes = [P, C.POINTER(StatsC)]
     lib.tdvp_set_profiling.argtypes = [P, C.c_int]
+    lib.tdvp_lq_noalloc.argtypes = [C.c_int, C.c_int, P, P, P, P]
     lib.tdvp_reset_stats.argtypes = [P]
     lib.tdvp_reset_stats.restype = None
     lib.tdvp_last_error.argtypes = [P]
@@ -239,3 +241,16 @@ class Engine:
 
     def reset_stats(self):
         self.lib.tdvp_reset_stats(self._h)
+
+
+def lq_noalloc(n, m, x_ptr, q_ptr, l_ptr, stream):
+    """X = L Q on device buffers (raw device pointers as ints) with no device allocation.
+
+    For callers that must not allocate device memory; see tdvp_lq_noalloc in include/tdvp.h.
+    Raises TDVPError on a non-zero status.
+    """
+    lib = load_library()
+    rc = lib.tdvp_lq_noalloc(int(n), int(m), C.c_void_p(x_ptr), C.c_void_p(q_ptr), C.c_void_p(l_ptr),
+                             C.c_void_p(stream))
+    if rc != 0:
+        raise TDVPError(rc, "tdvp_lq_noalloc failed")
