@@ -90,7 +90,7 @@ int tdvp_build_mpo(tdvp_ctx* ctx, int r, const tdvp_fh_params* p);
  * vectors at the successive (s, r) positions other than (occupied, 0), ordered by
  * r first and s second, which makes it right-canonical (Eq. rcanon).  Builds all right
  * environments h[i+1:N] (Eq. tdvp1_hiN).  Requires tdvp_build_mpo first. */
-int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site);
+int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site);   /* 1 <= D <= 256 */
 
 /* Explicit initial tensors for realisation r: bond_dims[0..N] (bond_dims[0] =
  * bond_dims[N] = 1) and re_im = all site tensors concatenated in site order,

@@ -25,7 +25,7 @@ __device__ bool make_desc(int op, int site, int b, const SiteDev* sdr, const Wor
   const SiteDev& s = sdr[site];
   const int Dl = s.Dl, d = s.d, Dr = s.Dr;
   const long long nsite = (long long)Dl * d * Dr;
-  g.nz = 1; g.sAz = 0; g.sBz = 0; g.opA = 0; g.opB = 0; g.skip = nullptr;
+  g.nz = 1; g.sAz = 0; g.sBz = 0; g.opA = 0; g.opB = 0; g.skip = nullptr; g.ws = nullptr;
   switch (op) {
     case OP_MV1: case OP_EL1: case OP_HX1: {
       // T1[b] (Dl x d*Dr) = L_b (Dl x Dl) * X (Dl x d*Dr)
@@ -43,6 +43,7 @@ __device__ bool make_desc(int op, int site, int b, const SiteDev* sdr, const Wor
       g.C = wk.w; g.ldc = Dr;
       g.M = Dl * d; g.N = Dr; g.K = Dr; g.nz = s.Wr;
       g.skip = &wk.ks->done;
+      g.ws = wk.T1;
       return true;
     }
     case OP_EL3: {
@@ -51,6 +52,7 @@ __device__ bool make_desc(int op, int site, int b, const SiteDev* sdr, const Wor
       g.B = wk.T2 + b * nsite; g.ldb = Dr;
       g.C = sdr[site + 1].Lenv + (long long)b * Dr * Dr; g.ldc = Dr;
       g.M = Dr; g.N = Dr; g.K = Dl * d;
+      g.ws = wk.T1;
       return true;
     }
     case OP_ER1: {
@@ -67,6 +69,7 @@ __device__ bool make_desc(int op, int site, int b, const SiteDev* sdr, const Wor
       g.B = wk.T2 + b * nsite; g.ldb = d * Dr; g.opB = 1;
       g.C = sdr[site - 1].Renv + (long long)b * Dl * Dl; g.ldc = Dl;
       g.M = Dl; g.N = Dl; g.K = d * Dr;
+      g.ws = wk.T1;
       return true;
     }
     case OP_Z1: {
@@ -77,6 +80,7 @@ __device__ bool make_desc(int op, int site, int b, const SiteDev* sdr, const Wor
       g.C = wk.T1 + (long long)b * Db * Db; g.ldc = Db;
       g.M = Db; g.N = Db; g.K = Db;
       g.skip = &wk.ks->done;
+      g.ws = wk.T2;
       return true;
     }
     case OP_Z3: {
@@ -86,6 +90,7 @@ __device__ bool make_desc(int op, int site, int b, const SiteDev* sdr, const Wor
       g.C = wk.w; g.ldc = Db;
       g.M = Db; g.N = Db; g.K = Db; g.nz = s.Wr;
       g.skip = &wk.ks->done;
+      g.ws = wk.T2;
       return true;
     }
     case OP_ABS_L: {
@@ -136,21 +141,27 @@ __device__ __forceinline__ zc load_op(const zc* P, int ld, int op, int row, int 
   }
 }
 
+// grid.z = (realisation, batch entry, K split).  With nsplit > 1 the flattened inner index
+// (z, k-tile) is cut into nsplit contiguous ranges; each block writes its partial tile to the
+// workspace and zgemm_reduce_kernel adds the partials in split order (deterministic).
 __global__ void __launch_bounds__(GEMM_THREADS)
 zgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
-             int nbatch) {
+             int nbatch, int nsplit) {
   __shared__ GemmDesc g;
   __shared__ int live;
   __shared__ zc As[TK][TM + 1];
   __shared__ zc Bs[TK][TN + 1];
-  const int r = blockIdx.z / nbatch;
-  const int b = blockIdx.z % nbatch;
+  const int split = blockIdx.z % nsplit;
+  const int zb = blockIdx.z / nsplit;
+  const int r = zb / nbatch;
+  const int b = zb % nbatch;
   if (threadIdx.x == 0) {
     const SiteDev* sdr = sd + (long long)r * N_sites;
     live = 0;
     if (b < op_batch(op, sdr[site]) && make_desc(op, site, b, sdr, wk[r], g)) {
       const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
       live = (m0 < g.M && n0 < g.N && !(g.skip && *g.skip)) ? 1 : 0;
+      if (nsplit > 1 && !g.ws) live = 0;
     }
   }
   __syncthreads();
@@ -161,41 +172,70 @@ zgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __
   const int M = g.M, N = g.N, K = g.K;
   const bool a_kfast = (g.opA == 0 || g.opA == 3);
   const bool b_nfast = (g.opB == 0 || g.opB == 3);
-  for (int z = 0; z < g.nz; ++z) {
+  const int nkt = (K + TK - 1) / TK;
+  const int ktot = g.nz * nkt;
+  const int kt0 = (int)((long long)ktot * split / nsplit), kt1 = (int)((long long)ktot * (split + 1) / nsplit);
+  for (int kt = kt0; kt < kt1; ++kt) {
+    const int z = kt / nkt, k0 = (kt % nkt) * TK;
     const zc* Az = g.A + z * g.sAz;
     const zc* Bz = g.B + z * g.sBz;
-    for (int k0 = 0; k0 < K; k0 += TK) {
-      // stage op(A)[m0:m0+TM, k0:k0+TK] and op(B)[k0:k0+TK, n0:n0+TN]
-      for (int e = threadIdx.x; e < TM * TK; e += GEMM_THREADS) {
-        int mm, kk;
-        if (a_kfast) { mm = e / TK; kk = e % TK; } else { mm = e % TM; kk = e / TM; }
-        const int gm = m0 + mm, gk = k0 + kk;
-        As[kk][mm] = (gm < M && gk < K) ? load_op(Az, g.lda, g.opA, gm, gk) : zmake(0, 0);
-      }
-      for (int e = threadIdx.x; e < TK * TN; e += GEMM_THREADS) {
-        int kk, nn;
-        if (b_nfast) { kk = e / TN; nn = e % TN; } else { kk = e % TK; nn = e / TK; }
-        const int gk = k0 + kk, gn = n0 + nn;
-        Bs[kk][nn] = (gk < K && gn < N) ? load_op(Bz, g.ldb, g.opB, gk, gn) : zmake(0, 0);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < TK; ++kk) {
-        const zc a0 = As[kk][ty], a1 = As[kk][ty + 16];
-        const zc b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-        acc00 = zfma(a0, b0, acc00);
-        acc01 = zfma(a0, b1, acc01);
-        acc10 = zfma(a1, b0, acc10);
-        acc11 = zfma(a1, b1, acc11);
-      }
-      __syncthreads();
+    // stage op(A)[m0:m0+TM, k0:k0+TK] and op(B)[k0:k0+TK, n0:n0+TN]
+    for (int e = threadIdx.x; e < TM * TK; e += GEMM_THREADS) {
+      int mm, kk;
+      if (a_kfast) { mm = e / TK; kk = e % TK; } else { mm = e % TM; kk = e / TM; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? load_op(Az, g.lda, g.opA, gm, gk) : zmake(0, 0);
     }
+    for (int e = threadIdx.x; e < TK * TN; e += GEMM_THREADS) {
+      int kk, nn;
+      if (b_nfast) { kk = e / TN; nn = e % TN; } else { kk = e % TK; nn = e / TK; }
+      const int gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gk < K && gn < N) ? load_op(Bz, g.ldb, g.opB, gk, gn) : zmake(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      const zc a0 = As[kk][ty], a1 = As[kk][ty + 16];
+      const zc b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      acc00 = zfma(a0, b0, acc00);
+      acc01 = zfma(a0, b1, acc01);
+      acc10 = zfma(a1, b0, acc10);
+      acc11 = zfma(a1, b1, acc11);
+    }
+    __syncthreads();
+  }
+  zc* C = g.C;
+  long long ldc = g.ldc;
+  if (nsplit > 1) {   // partial tile into the workspace, dense M x N per (batch entry, split)
+    C = g.ws + ((long long)b * nsplit + split) * M * N;
+    ldc = N;
   }
   const int r0 = m0 + ty, r1 = m0 + ty + 16, c0 = n0 + tx, c1 = n0 + tx + 16;
-  if (r0 < M && c0 < N) g.C[(long long)r0 * g.ldc + c0] = acc00;
-  if (r0 < M && c1 < N) g.C[(long long)r0 * g.ldc + c1] = acc01;
-  if (r1 < M && c0 < N) g.C[(long long)r1 * g.ldc + c0] = acc10;
-  if (r1 < M && c1 < N) g.C[(long long)r1 * g.ldc + c1] = acc11;
+  if (r0 < M && c0 < N) C[(long long)r0 * ldc + c0] = acc00;
+  if (r0 < M && c1 < N) C[(long long)r0 * ldc + c1] = acc01;
+  if (r1 < M && c0 < N) C[(long long)r1 * ldc + c0] = acc10;
+  if (r1 < M && c1 < N) C[(long long)r1 * ldc + c1] = acc11;
+}
+
+__global__ void __launch_bounds__(256)
+zgemm_reduce_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
+                    int nbatch, int nsplit) {
+  __shared__ GemmDesc g;
+  __shared__ int live;
+  const int r = blockIdx.y / nbatch, b = blockIdx.y % nbatch;
+  if (threadIdx.x == 0) {
+    const SiteDev* sdr = sd + (long long)r * N_sites;
+    live = (b < op_batch(op, sdr[site]) && make_desc(op, site, b, sdr, wk[r], g) && g.ws && !(g.skip && *g.skip));
+  }
+  __syncthreads();
+  if (!live) return;
+  const long long MN = (long long)g.M * g.N;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= MN) return;
+  const zc* P = g.ws + (long long)b * nsplit * MN + e;
+  zc s = P[0];
+  for (int q = 1; q < nsplit; ++q) s = zadd(s, P[q * MN]);
+  g.C[(e / g.N) * g.ldc + e % g.N] = s;
 }
 
 // Middle stage: out[co][x][so][y] = sum_e val * in[ci][x][si][y] (the sparse MPO of Eq. mpo).
@@ -345,10 +385,15 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 }  // namespace
 
 cudaError_t launch_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
-                        int maxN, int nbatch, cudaStream_t st) {
+                        int maxN, int nbatch, int nsplit, cudaStream_t st) {
   if (maxM <= 0 || maxN <= 0 || nbatch <= 0) return cudaSuccess;
-  dim3 grid(cdiv(maxN, TN), cdiv(maxM, TM), R * nbatch);
-  zgemm_kernel<<<grid, GEMM_THREADS, 0, st>>>(op, site, sd, wk, N_sites, nbatch);
+  if (nsplit < 1) nsplit = 1;
+  dim3 grid(cdiv(maxN, TN), cdiv(maxM, TM), R * nbatch * nsplit);
+  zgemm_kernel<<<grid, GEMM_THREADS, 0, st>>>(op, site, sd, wk, N_sites, nbatch, nsplit);
+  if (nsplit > 1) {
+    dim3 g2(cdiv((long long)maxM * maxN, 256), R * nbatch);
+    zgemm_reduce_kernel<<<g2, 256, 0, st>>>(op, site, sd, wk, N_sites, nbatch, nsplit);
+  }
   return cudaGetLastError();
 }
 

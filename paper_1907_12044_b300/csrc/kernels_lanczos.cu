@@ -85,9 +85,41 @@ __device__ void reduce_partials(const WorkDev& W, int tab, int nblk, int j, zc* 
   __syncthreads();
 }
 
+// Sum over the 32 lanes of a warp of G complex values per lane, for all G at once: a butterfly in
+// which each step halves the values a lane keeps and adds its partner's half.  After log2(G) steps
+// lane l holds the warp total of value (l % G) partially reduced over groups of G lanes, which the
+// remaining steps finish.  Returns the total of value (lane % G) (valid in every lane).
+template <int G>
+__device__ __forceinline__ zc warp_transpose_sum(zc (&v)[G]) {
+  const int lane = threadIdx.x % 32;
+#pragma unroll
+  for (int half = G / 2; half >= 1; half >>= 1) {
+    const bool upper = (lane & half) != 0;
+#pragma unroll
+    for (int q = 0; q < half; ++q) {
+      // keep v[q + half] if upper else v[q]; send the other one to the partner lane
+      const zc send = upper ? v[q] : v[q + half];
+      zc got;
+      got.x = __shfl_xor_sync(0xffffffffu, send.x, half);
+      got.y = __shfl_xor_sync(0xffffffffu, send.y, half);
+      const zc keep = upper ? v[q + half] : v[q];
+      v[q] = zadd(keep, got);
+    }
+  }
+  zc s = v[0];   // now lane holds partial of value (lane % G)
+#pragma unroll
+  for (int o = G; o < 32; o <<= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  return s;
+}
+
 // Partial dots p_t = sum_{e in chunk} conj(V_t[e]) w[e] for t <= j into table `tab`.
 __device__ void chunk_dots(const WorkDev& W, const VecGeom& g, int j, int tab, int b, double* red) {
   constexpr int G = 8;
+  zc* wsum = reinterpret_cast<zc*>(red);    // [NT/32][G] complex
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
   for (int t0 = 0; t0 <= j; t0 += G) {
     zc acc[G];
 #pragma unroll
@@ -98,17 +130,20 @@ __device__ void chunk_dots(const WorkDev& W, const VecGeom& g, int j, int tab, i
       for (int q = 0; q < G; ++q)
         if (t0 + q <= j) acc[q] = zcfma(W.V[(t0 + q) * W.ldV + e], we, acc[q]);
     }
-#pragma unroll
-    for (int q = 0; q < G; ++q) {
-      if (t0 + q > j) break;
-      const zc s = block_zsum(acc[q], red);
-      if (threadIdx.x == 0) *P(W, tab, b, t0 + q) = s;
+    const zc s = warp_transpose_sum<G>(acc);
+    if (lane < G) wsum[wid * G + lane] = s;
+    __syncthreads();
+    if (threadIdx.x < G && t0 + (int)threadIdx.x <= j) {
+      zc tot = zmake(0, 0);
+      for (int w = 0; w < NT / 32; ++w) tot = zadd(tot, wsum[w * G + threadIdx.x]);
+      *P(W, tab, b, t0 + threadIdx.x) = tot;
     }
+    __syncthreads();
   }
 }
 
 __global__ void __launch_bounds__(NT) lz_start1(LzArgs a) {
-  __shared__ double red[2 * NT / 32];
+  __shared__ double red[2 * 8 * NT / 32];
   const int r = blockIdx.y, b = blockIdx.x;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const WorkDev& W = a.wk[r];
@@ -152,7 +187,7 @@ __global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
 }
 
 __global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
-  __shared__ double red[2 * NT / 32];
+  __shared__ double red[2 * 8 * NT / 32];
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
   if (W.ks->done) return;
@@ -164,7 +199,7 @@ __global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
 
 // pass 1 (tab_in = 0, tab_out = 1) or pass 2 (tab_in = 1, norm partials into table 2)
 __global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
-  __shared__ double red[2 * NT / 32];
+  __shared__ double red[2 * 8 * NT / 32];
   __shared__ zc h[TDVP_KMAX_HARD];
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
@@ -288,7 +323,9 @@ __device__ bool tridiag_expi(const double* alpha, const double* beta, int k, dou
   vcur[t] = v1;
   double vc = v1;
   __syncthreads();
-  for (int n = 1; n < N; ++n) {
+  int Nlast = N;
+  while (Nlast > 2 && fabs(J[Nlast]) < 1e-18 && fabs(J[Nlast - 1]) < 1e-18) --Nlast;
+  for (int n = 1; n < Nlast; ++n) {
     double vn = 0;
     if (t < k) {
       const double left = t > 0 ? vcur[t - 1] : 0.0, right = t < k - 1 ? vcur[t + 1] : 0.0;

@@ -3,26 +3,33 @@
 // The matrix is handled as X (n rows x m columns, row-major, n <= m): X = Rc * Qr with Qr having
 // orthonormal rows and Rc lower triangular.  For the left-to-right shift X is the transpose of
 // the site tensor C[(l s), r], so Q = Qr^T and R = Rc^T; for the right-to-left shift X is
-// C[l, (s r)] itself.  Rows are orthogonalised one after another by classical Gram-Schmidt with
-// one re-orthogonalisation pass.  A row whose residual is <= rtol*||X||_F is treated as linearly
-// dependent: its diagonal entry is 0 and the row is replaced by the first unit vector e_p whose
-// distance to the span of the rows so far is >= 1/2 (1 - sum_t |Qr[t][p]|^2 >= 1/4), else by the
-// one farthest from it, orthogonalised with the same two passes (the completion of a weakly
-// correlated start that Sec. II.C calls for).
+// C[l, (s r)] itself.
 //
-// One realisation is processed by B blocks, each owning a contiguous slab of columns; every
-// access to X and Qr stays inside the slab, and only per-block partial sums cross blocks.  The
-// blocks of a realisation meet at a group barrier (global counter + generation word) whose wait
-// is bounded: after ~1 s it records TDVP_ERR_DEVICE_TIMEOUT in the realisation's error word and
-// every block returns.  The kernel is launched cooperatively, so all blocks are co-resident.
+// Definition followed (the same as the CPU oracle's): rows are orthogonalised in order by
+// classical Gram-Schmidt with one re-orthogonalisation pass; a row whose residual is
+// <= rtol*||X||_F is linearly dependent, gets a zero diagonal entry, and is replaced by the first
+// unit vector e_p at distance >= 1/2 from the rows so far (1 - sum_t |Qr[t][p]|^2 >= 1/4), else
+// the farthest one, orthogonalised with the same two passes.
+//
+// Blocked evaluation: rows are taken in panels of PB = 8.  A panel is projected twice against all
+// earlier rows (block classical Gram-Schmidt), then orthonormalised inside the panel by two
+// Cholesky-QR passes on its PB x PB Gram matrix.  In exact arithmetic this gives the same Q and
+// R as the row-by-row process.  When the first Gram matrix shows a row whose squared residual is
+// below 1e-10 of its squared norm or below 1e8 rtol^2 ||X||_F^2 (where Cholesky-QR loses accuracy
+// and where the rank decision is taken), the panel is redone row by row with the exact rule.
+//
+// One realisation is processed by B co-resident blocks (cooperative launch).  Dot products over
+// whole rows are spread over all warps of all blocks; updates are done by the block that owns a
+// slab of columns.  Phases are separated by a group barrier whose wait is bounded: after ~1 s it
+// records TDVP_ERR_DEVICE_TIMEOUT in the realisation's error word and every block returns.
 #include "tdvp_internal.cuh"
-#include <cooperative_groups.h>
 
 namespace {
 
 constexpr int QT = TDVP_QR_THREADS;       // 256 threads = 8 warps
 constexpr int NW = QT / 32;
-constexpr int QR_NMAX = 512;              // largest n (bond dimension) handled
+constexpr int QR_NMAX = 256;              // largest n (bond dimension) handled
+constexpr int PB = 8;                     // panel height
 constexpr long long SPIN_LIMIT = 1LL << 24;
 
 struct QrJob {
@@ -68,7 +75,7 @@ __device__ bool group_sync(const WorkDev& W, int nblocks) {
         while (*gen == g) {
           if (*err != 0) { good = 0; break; }
           if (++spins > SPIN_LIMIT) { atomicExch(W.err, -5); good = 0; break; }
-          __nanosleep(64);
+          __nanosleep(32);
         }
       }
       __threadfence();
@@ -79,87 +86,87 @@ __device__ bool group_sync(const WorkDev& W, int nblocks) {
   return ok != 0;
 }
 
-__device__ __forceinline__ zc ldcg(const zc* p) { return __ldcg(p); }
-
-// Partial dots p_t = sum_{c in slab} conj(Q_t[c]) x[c] for t < j: warp per t, lanes over columns.
-__device__ void slab_dots(const zc* X, int m, int j, const zc* x, int c0, int c1, zc* Pout) {
-  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
-  for (int t = wid; t < j; t += NW) {
-    const zc* q = X + (long long)t * m;
-    zc s = zmake(0, 0);
-    for (int c = c0 + lane; c < c1; c += 32) s = zcfma(q[c], x[c], s);
-    for (int o = 16; o > 0; o >>= 1) {
-      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-      s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-    }
-    if (lane == 0) Pout[t] = s;
+// sum_c conj(b[c]) a[c] over the whole row by one warp (rows may be written by other blocks).
+__device__ __forceinline__ zc warp_dot(const zc* a, const zc* b, int m) {
+  const int lane = threadIdx.x % 32;
+  zc s = zmake(0, 0);
+  for (int c = lane; c < m; c += 32) s = zcfma(__ldcg(b + c), __ldcg(a + c), s);
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
   }
+  return s;
 }
 
-// h_t = sum_b P[b][t] for t < cnt in block order (identical in every block).
-__device__ void reduce_over_blocks(const zc* Pbase, int PS, int B, int cnt, zc* h) {
-  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
-  for (int t = wid; t < cnt; t += NW) {
-    zc s = zmake(0, 0);
-    for (int b = lane; b < B; b += 32) s = zadd(s, ldcg(Pbase + (long long)b * PS + t));
-    for (int o = 16; o > 0; o >>= 1) {
-      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-      s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-    }
-    if (lane == 0) h[t] = s;
-  }
-  __syncthreads();
-}
-
-// x[c] -= sum_{t<j} h_t Q_t[c] over the slab: warp w sums t = w (mod 8), then a fixed-order merge.
-__device__ void slab_update(const zc* X, int m, int j, zc* x, int c0, int c1, const zc* h, zc (*buf)[32]) {
-  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
-  for (int cb = c0; cb < c1; cb += 32) {
-    const int c = cb + lane;
+// X[row0 + r][c] -= sum_{t<T} Hs[r*ldh + t] * X[t][c] for r < nb and c in the slab [c0, c1).
+// Several threads share an element and split the t sum; their partial sums are combined by a
+// fixed shuffle tree, so results do not depend on scheduling.
+__device__ void slab_update(zc* X, int m, int row0, int nb, int T, const zc* Hs, int ldh, int c0, int c1) {
+  const int cs = c1 - c0;
+  const int E = nb * cs;
+  if (E <= 0 || T <= 0) return;
+  int tpe = 1;
+  while (tpe * 2 <= 32 && tpe * 2 * E <= QT && tpe * 2 <= T) tpe *= 2;
+  const int total = E * tpe;
+  for (int base = 0; base < total; base += QT) {
+    const int idx = base + threadIdx.x;
+    const bool active = idx < total;
+    const int e = idx / tpe, sub = idx % tpe;
     zc acc = zmake(0, 0);
-    if (c < c1)
-      for (int t = wid; t < j; t += NW) acc = zfma(h[t], X[(long long)t * m + c], acc);
-    buf[wid][lane] = acc;
-    __syncthreads();
-    if (wid == 0 && c < c1) {
-      zc s = buf[0][lane];
-      for (int w = 1; w < NW; ++w) s = zadd(s, buf[w][lane]);
-      x[c] = zsub(x[c], s);
+    int r = 0, c = 0;
+    if (active) {
+      r = e / cs;
+      c = c0 + e % cs;
+      for (int t = sub; t < T; t += tpe) acc = zfma(Hs[r * ldh + t], X[(long long)t * m + c], acc);
     }
-    __syncthreads();
+    for (int o = tpe / 2; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (active && sub == 0) {
+      zc* p = X + (long long)(row0 + r) * m + c;
+      *p = zsub(*p, acc);
+    }
   }
+  __syncthreads();
 }
 
-__device__ double slab_norm2(const zc* x, int c0, int c1, double* red) {
-  double s = 0;
-  for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(x[c]);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
-  if (lane == 0) red[wid] = s;
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
   __syncthreads();
   double t = 0;
   for (int w = 0; w < NW; ++w) t += red[w];
   return t;
 }
 
-__device__ double sum_scalar_over_blocks(const zc* Pbase, int PS, int B, int slot) {
-  // fixed order: lanes stride over blocks, then butterfly; every block gets the same value
+// fixed-order sum of one double per block (every block gets the same value)
+__device__ double sum_over_blocks(const zc* P, int B) {
   const int lane = threadIdx.x % 32;
   double s = 0;
-  for (int b = lane; b < B; b += 32) s += ldcg(Pbase + (long long)b * PS + slot).x;
+  for (int b = lane; b < B; b += 32) s += __ldcg(P + b).x;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;   // valid in every lane of every warp
+  return s;
 }
 
+struct Scratch {
+  zc* H1;     // [PB][n]  first-pass coefficients of the panel rows
+  zc* H2;     // [PB][n]  second-pass coefficients
+  zc* G;      // [PB][PB] Gram matrix
+  zc* hv;     // [2n]     coefficients of the row-by-row path
+  zc* Pn;     // [B]      per-block scalars
+  zc* Pc;     // [2B]     per-block completion candidates
+};
+
 __global__ void __launch_bounds__(QT)
-row_qr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
-              int B, double rtol, int dn, int dm) {
-  __shared__ zc h1[QR_NMAX];
-  __shared__ zc h2[QR_NMAX];
-  __shared__ zc buf[NW][32];
+bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites, int B,
+           double rtol, int dn, int dm) {
+  __shared__ zc Hs[PB * QR_NMAX];
+  __shared__ zc L1[PB][PB];
+  __shared__ zc L2[PB][PB];
   __shared__ double red[NW];
-  __shared__ int sel[4];
+  __shared__ int flag[2];
   const int r = blockIdx.x / B, b = blockIdx.x % B;
   const SiteDev* sdr = sd + (long long)r * N_sites;
   const WorkDev& W = wk[r];
@@ -170,14 +177,18 @@ row_qr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* 
     return;
   }
   const int c0 = (int)((long long)m * b / B), c1 = (int)((long long)m * (b + 1) / B);
+  const int lane = threadIdx.x % 32, gw = b * NW + threadIdx.x / 32, nwarps = B * NW;
   zc* X = J.X;
-  const int PS = n + 4;
-  zc* P1 = W.qpart;
-  zc* P2 = W.qpart + (long long)B * PS;
-  zc* P3 = W.qpart + 2LL * B * PS;
+  Scratch S;
+  S.H1 = W.qpart;
+  S.H2 = S.H1 + PB * n;
+  S.G = S.H2 + PB * n;
+  S.hv = S.G + PB * PB;
+  S.Pn = S.hv + 2 * n;
+  S.Pc = S.Pn + B;
   double* colsq = W.colsq;
 
-  // ||X||_F over the slab
+  // ||X||_F and the rank threshold
   {
     double s = 0;
     const int cs = c1 - c0;
@@ -185,145 +196,213 @@ row_qr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* 
       const int row = (int)(e / cs), c = c0 + (int)(e % cs);
       s += zabs2(X[(long long)row * m + c]);
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int w = 0; w < NW; ++w) t += red[w];
-      P3[(long long)b * PS] = zmake(t, 0);
-    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) S.Pn[b] = zmake(s, 0);
     for (int c = c0 + threadIdx.x; c < c1; c += QT) colsq[c] = 0.0;
   }
   if (!group_sync(W, B)) return;
-  const double thresh = rtol * sqrt(sum_scalar_over_blocks(P3, PS, B, 0));
+  const double fro2 = sum_over_blocks(S.Pn, B);
+  const double thresh = rtol * sqrt(fro2);
 
-  for (int j = 0; j < n; ++j) {
-    zc* x = X + (long long)j * m;
-    // first pass
-    if (j > 0) {
-      slab_dots(X, m, j, x, c0, c1, P1 + (long long)b * PS);
-      if (!group_sync(W, B)) return;
-      reduce_over_blocks(P1, PS, B, j, h1);
-      slab_update(X, m, j, x, c0, c1, h1, buf);
-    }
-    // second pass dots and the norm after the first pass
-    slab_dots(X, m, j, x, c0, c1, P2 + (long long)b * PS);
-    {
-      const double s = slab_norm2(x, c0, c1, red);
-      if (threadIdx.x == 0) P2[(long long)b * PS + n] = zmake(s, 0);
-    }
-    if (!group_sync(W, B)) return;
-    reduce_over_blocks(P2, PS, B, j, h2);
-    const double s1 = sum_scalar_over_blocks(P2, PS, B, n);
-    slab_update(X, m, j, x, c0, c1, h2, buf);
-    double hh = 0;
-    {
-      double v = 0;
-      for (int t = threadIdx.x; t < j; t += QT) v += zabs2(h2[t]);
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      __syncthreads();
-      if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
-      __syncthreads();
-      for (int w = 0; w < NW; ++w) hh += red[w];
-    }
-    double nrm2 = s1 - hh;
-    if (nrm2 <= 1e4 * thresh * thresh) {          // near the rank threshold: measure directly
-      const double s = slab_norm2(x, c0, c1, red);
-      if (threadIdx.x == 0) P3[(long long)b * PS] = zmake(s, 0);
-      if (!group_sync(W, B)) return;
-      nrm2 = sum_scalar_over_blocks(P3, PS, B, 0);
-      if (!group_sync(W, B)) return;              // P3 is reused below
-    }
-    const double nrm = sqrt(nrm2 > 0 ? nrm2 : 0.0);
-    const bool full = nrm > thresh;
-    if (b == 0) {
-      for (int t = threadIdx.x; t < n; t += QT) {
-        zc v = zmake(0, 0);
-        if (t < j) v = zadd(j > 0 ? h1[t] : zmake(0, 0), h2[t]);
-        else if (t == j) v = zmake(full ? nrm : 0.0, 0);
-        const long long o = J.rtrans ? (long long)t * n + j : (long long)j * n + t;
-        J.Rout[o] = v;
+  for (int j0 = 0; j0 < n; j0 += PB) {
+    const int nb = min(PB, n - j0);
+    // ---- two block Gram-Schmidt passes against rows 0..j0-1 ----
+    for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
+      zc* Hb = pass ? S.H2 : S.H1;
+      for (int e = gw; e < nb * j0; e += nwarps) {
+        const int rr = e / j0, t = e % j0;
+        const zc s = warp_dot(X + (long long)(j0 + rr) * m, X + (long long)t * m, m);
+        if (lane == 0) Hb[rr * n + t] = s;
       }
+      if (!group_sync(W, B)) return;
+      for (int e = threadIdx.x; e < nb * j0; e += QT) Hs[(e / j0) * j0 + e % j0] = __ldcg(Hb + (e / j0) * n + e % j0);
+      __syncthreads();
+      slab_update(X, m, j0, nb, j0, Hs, j0, c0, c1);
+      if (!group_sync(W, B)) return;
     }
-    if (full) {
-      const double inv = 1.0 / nrm;
+    // ---- two Cholesky-QR passes inside the panel ----
+    bool fallback = false;
+    for (int it = 0; it < 2; ++it) {
+      for (int e = gw; e < nb * (nb + 1) / 2; e += nwarps) {
+        int rr = 0;
+        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+        const int ss = e - rr * (rr + 1) / 2;
+        const zc s = warp_dot(X + (long long)(j0 + rr) * m, X + (long long)(j0 + ss) * m, m);   // sum x_r conj(x_s)
+        if (lane == 0) S.G[rr * PB + ss] = s;
+      }
+      if (!group_sync(W, B)) return;
+      zc (*Lc)[PB] = it ? L2 : L1;
+      if (threadIdx.x == 0) {
+        int bad = 0;
+        for (int jj = 0; jj < nb; ++jj) {
+          const double gjj = __ldcg(S.G + jj * PB + jj).x;
+          double s = gjj;
+          for (int k = 0; k < jj; ++k) s -= zabs2(Lc[jj][k]);
+          if (!(s > 0.0) || (it == 0 && (s <= 1e-10 * gjj || s <= 1e8 * thresh * thresh))) { bad = it + 1; break; }
+          const double d = sqrt(s);
+          Lc[jj][jj] = zmake(d, 0);
+          const double inv = 1.0 / d;
+          for (int i = jj + 1; i < nb; ++i) {
+            zc v = __ldcg(S.G + i * PB + jj);
+            for (int k = 0; k < jj; ++k) v = zfms(Lc[i][k], zconj(Lc[jj][k]), v);
+            Lc[i][jj] = zscale(v, inv);
+          }
+          for (int i = 0; i < jj; ++i) Lc[i][jj] = zmake(0, 0);
+        }
+        flag[0] = bad;
+      }
+      __syncthreads();
+      if (flag[0] == 2) {              // the rows are already orthonormal to ~1e-6 here
+        if (b == 0 && threadIdx.x == 0) atomicExch(W.err, -6);
+        return;
+      }
+      if (flag[0]) { fallback = true; break; }
+      // x_panel <- Lc^{-1} x_panel on the slab columns
+      for (int c = c0 + threadIdx.x; c < c1; c += QT) {
+        zc y[PB];
+        for (int rr = 0; rr < nb; ++rr) {
+          zc v = X[(long long)(j0 + rr) * m + c];
+          for (int k = 0; k < rr; ++k) v = zfms(Lc[rr][k], y[k], v);
+          y[rr] = zscale(v, 1.0 / Lc[rr][rr].x);
+        }
+        for (int rr = 0; rr < nb; ++rr) X[(long long)(j0 + rr) * m + c] = y[rr];
+      }
+      if (!group_sync(W, B)) return;
+    }
+    if (!fallback) {
+      if (b == 0) {
+        for (int e = threadIdx.x; e < nb * n; e += QT) {
+          const int rr = e / n, t = e % n, j = j0 + rr;
+          zc v = zmake(0, 0);
+          if (t < j0) {
+            v = zadd(__ldcg(S.H1 + rr * n + t), __ldcg(S.H2 + rr * n + t));
+          } else if (t <= j) {
+            const int s2 = t - j0;                       // (L1 L2)[rr][s2]
+            for (int k = s2; k <= rr; ++k) v = zfma(L1[rr][k], L2[k][s2], v);
+          }
+          J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
+        }
+      }
+      for (int c = c0 + threadIdx.x; c < c1; c += QT) {
+        double s = colsq[c];
+        for (int rr = 0; rr < nb; ++rr) s += zabs2(X[(long long)(j0 + rr) * m + c]);
+        colsq[c] = s;
+      }
+      __syncthreads();
+      continue;
+    }
+    // ---- exact row-by-row path for this panel ----
+    for (int j = j0; j < j0 + nb; ++j) {
+      const int rr = j - j0;
+      zc* x = X + (long long)j * m;
+      for (int pass = 0; pass < 2; ++pass) {
+        zc* hb = S.hv + pass * n;
+        for (int t = gw; t < j; t += nwarps) {
+          const zc s = warp_dot(x, X + (long long)t * m, m);
+          if (lane == 0) hb[t] = s;
+        }
+        if (!group_sync(W, B)) return;
+        for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(hb + t);
+        __syncthreads();
+        slab_update(X, m, j, 1, j, Hs, j, c0, c1);
+        if (pass == 0 && !group_sync(W, B)) return;
+      }
+      {
+        double s = 0;
+        for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(x[c]);
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) S.Pn[b] = zmake(s, 0);
+      }
+      if (!group_sync(W, B)) return;
+      const double nrm = sqrt(sum_over_blocks(S.Pn, B));
+      const bool full = nrm > thresh;
+      if (b == 0) {
+        for (int t = threadIdx.x; t < n; t += QT) {
+          zc v = zmake(0, 0);
+          if (t < j) {
+            v = zadd(__ldcg(S.hv + t), __ldcg(S.hv + n + t));
+            if (t < j0) v = zadd(v, zadd(__ldcg(S.H1 + rr * n + t), __ldcg(S.H2 + rr * n + t)));
+          } else if (t == j) {
+            v = zmake(full ? nrm : 0.0, 0);
+          }
+          J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
+        }
+      }
+      if (!full) {
+        // completion by the first unit vector at distance >= 1/2 from rows 0..j-1
+        int first = 0x7fffffff, besti = 0x7fffffff;
+        double bestv = -1.0;
+        for (int c = c0 + threadIdx.x; c < c1; c += QT) {
+          const double dist = 1.0 - colsq[c];
+          if (dist >= 0.25 && c < first) first = c;
+          if (dist > bestv || (dist == bestv && c < besti)) { bestv = dist; besti = c; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const int f2 = __shfl_xor_sync(0xffffffffu, first, o);
+          const double v2 = __shfl_xor_sync(0xffffffffu, bestv, o);
+          const int i2 = __shfl_xor_sync(0xffffffffu, besti, o);
+          first = min(first, f2);
+          if (v2 > bestv || (v2 == bestv && i2 < besti)) { bestv = v2; besti = i2; }
+        }
+        __syncthreads();
+        if (lane == 0) { Hs[2 * (threadIdx.x / 32)] = zmake((double)first, bestv); Hs[2 * (threadIdx.x / 32) + 1] = zmake((double)besti, 0); }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double f = Hs[0].x, bv = Hs[0].y, bi = Hs[1].x;
+          for (int w = 1; w < NW; ++w) {
+            f = fmin(f, Hs[2 * w].x);
+            const double v2 = Hs[2 * w].y, i2 = Hs[2 * w + 1].x;
+            if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
+          }
+          S.Pc[2 * b] = zmake(f, 0);
+          S.Pc[2 * b + 1] = zmake(bv, bi);
+        }
+        if (!group_sync(W, B)) return;
+        if (threadIdx.x == 0) {
+          double f = 2147483647.0, bv = -2.0, bi = 2147483647.0;
+          for (int bb = 0; bb < B; ++bb) {
+            f = fmin(f, __ldcg(S.Pc + 2 * bb).x);
+            const zc q = __ldcg(S.Pc + 2 * bb + 1);
+            if (q.x > bv || (q.x == bv && q.y < bi)) { bv = q.x; bi = q.y; }
+          }
+          flag[1] = (f < 2147483647.0) ? (int)f : (int)bi;
+        }
+        __syncthreads();
+        const int p = flag[1];
+        if (!group_sync(W, B)) return;            // everyone has read the candidates
+        if (p >= c0 && p < c1)
+          for (int t = threadIdx.x; t < j; t += QT) W.qhp[t] = zconj(X[(long long)t * m + p]);
+        if (!group_sync(W, B)) return;
+        for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(W.qhp + t);
+        for (int c = c0 + threadIdx.x; c < c1; c += QT) x[c] = zmake(c == p ? 1.0 : 0.0, 0);
+        __syncthreads();
+        slab_update(X, m, j, 1, j, Hs, j, c0, c1);
+        if (!group_sync(W, B)) return;
+        for (int t = gw; t < j; t += nwarps) {
+          const zc s = warp_dot(x, X + (long long)t * m, m);
+          if (lane == 0) S.hv[t] = s;
+        }
+        if (!group_sync(W, B)) return;
+        for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(S.hv + t);
+        __syncthreads();
+        slab_update(X, m, j, 1, j, Hs, j, c0, c1);
+        {
+          double s = 0;
+          for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(x[c]);
+          s = block_sum(s, red);
+          if (threadIdx.x == 0) S.Pn[b] = zmake(s, 0);
+        }
+        if (!group_sync(W, B)) return;
+      }
+      const double en = full ? nrm : sqrt(sum_over_blocks(S.Pn, B));
+      const double inv = en > 0 ? 1.0 / en : 0.0;
       for (int c = c0 + threadIdx.x; c < c1; c += QT) {
         const zc v = zscale(x[c], inv);
         x[c] = v;
         colsq[c] += zabs2(v);
       }
-      __syncthreads();
-      continue;
+      if (!group_sync(W, B)) return;
     }
-    // ---- completion by a unit vector e_p ----
-    {
-      int first = 0x7fffffff, besti = 0x7fffffff;
-      double bestv = -1.0;
-      for (int c = c0 + threadIdx.x; c < c1; c += QT) {
-        const double dist = 1.0 - colsq[c];
-        if (dist >= 0.25 && c < first) first = c;
-        if (dist > bestv || (dist == bestv && c < besti)) { bestv = dist; besti = c; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const int f2 = __shfl_xor_sync(0xffffffffu, first, o);
-        const double v2 = __shfl_xor_sync(0xffffffffu, bestv, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, besti, o);
-        first = min(first, f2);
-        if (v2 > bestv || (v2 == bestv && i2 < besti)) { bestv = v2; besti = i2; }
-      }
-      __syncthreads();
-      if (threadIdx.x % 32 == 0) { buf[threadIdx.x / 32][0] = zmake((double)first, bestv); buf[threadIdx.x / 32][1] = zmake((double)besti, 0); }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double f = buf[0][0].x, bv = buf[0][0].y, bi = buf[0][1].x;
-        for (int w = 1; w < NW; ++w) {
-          f = fmin(f, buf[w][0].x);
-          const double v2 = buf[w][0].y, i2 = buf[w][1].x;
-          if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
-        }
-        P3[(long long)b * PS + 0] = zmake(f, 0);
-        P3[(long long)b * PS + 1] = zmake(bv, bi);
-      }
-    }
-    if (!group_sync(W, B)) return;
-    if (threadIdx.x == 0) {
-      double f = 2147483647.0, bv = -2.0, bi = 2147483647.0;
-      for (int bb = 0; bb < B; ++bb) {
-        f = fmin(f, ldcg(P3 + (long long)bb * PS).x);
-        const zc q = ldcg(P3 + (long long)bb * PS + 1);
-        if (q.x > bv || (q.x == bv && q.y < bi)) { bv = q.x; bi = q.y; }
-      }
-      sel[0] = (f < 2147483647.0) ? (int)f : (int)bi;
-    }
-    __syncthreads();
-    const int p = sel[0];
-    zc* hp = W.qhp;
-    if (p >= c0 && p < c1)
-      for (int t = threadIdx.x; t < j; t += QT) hp[t] = zconj(X[(long long)t * m + p]);
-    if (!group_sync(W, B)) return;
-    for (int t = threadIdx.x; t < j; t += QT) h1[t] = ldcg(hp + t);
-    __syncthreads();
-    for (int c = c0 + threadIdx.x; c < c1; c += QT) x[c] = zmake(c == p ? 1.0 : 0.0, 0);
-    __syncthreads();
-    slab_update(X, m, j, x, c0, c1, h1, buf);
-    slab_dots(X, m, j, x, c0, c1, P1 + (long long)b * PS);
-    if (!group_sync(W, B)) return;
-    reduce_over_blocks(P1, PS, B, j, h2);
-    slab_update(X, m, j, x, c0, c1, h2, buf);
-    {
-      const double s = slab_norm2(x, c0, c1, red);
-      if (threadIdx.x == 0) P2[(long long)b * PS + n] = zmake(s, 0);
-    }
-    if (!group_sync(W, B)) return;
-    const double en = sqrt(sum_scalar_over_blocks(P2, PS, B, n));
-    const double inv = en > 0 ? 1.0 / en : 0.0;
-    for (int c = c0 + threadIdx.x; c < c1; c += QT) {
-      const zc v = zscale(x[c], inv);
-      x[c] = v;
-      colsq[c] += zabs2(v);
-    }
-    __syncthreads();
   }
 }
 
@@ -334,12 +413,12 @@ cudaError_t launch_row_qr(int dir, int site, const SiteDev* sd, const WorkDev* w
   int B = blocks_per_r < 1 ? 1 : blocks_per_r;
   void* args[] = {&dir, &site, (void*)&sd, (void*)&wk, &N_sites, &B, &rtol, &dbg_n, &dbg_m};
   dim3 grid(R * B), block(QT);
-  return cudaLaunchCooperativeKernel((const void*)row_qr_kernel, grid, block, args, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)bqr_kernel, grid, block, args, 0, st);
 }
 
 int qr_max_coresident_blocks(int device) {
   int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_qr_kernel, QT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bqr_kernel, QT, 0);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   return per_sm * sms;
 }

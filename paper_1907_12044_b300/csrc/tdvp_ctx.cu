@@ -47,8 +47,9 @@ struct tdvp_ctx {
   int* h_err = nullptr;       // pinned
   double* h_obs = nullptr;    // pinned, (n_el+4) per realisation
   std::vector<int> khist;     // last Krylov dim per (site, kind)
+  std::vector<long long> ws_cap;   // elements of T1 (= T2) per realisation
   int qr_cap = 0;
-  int check_every = 1;
+  int check_every = 0;        // 1: test Lanczos convergence at every k (else from the last k - 2 on)
   // per-launch timing
   int prof = 0;
   std::vector<cudaEvent_t> ev;   // pairs
@@ -206,6 +207,7 @@ int tdvp_create(tdvp_ctx** out, int device, void* cuda_stream, int n_realisation
   }
   cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * ctx->R, ctx->st);
   ctx->h_work.assign(ctx->R, WorkDev{});
+  ctx->ws_cap.assign(ctx->R, 0);
   ctx->qr_cap = qr_max_coresident_blocks(device);
   if (ctx->qr_cap < ctx->R) { tdvp_destroy(ctx); return TDVP_ERR_INVALID_ARG; }
   *out = ctx;
@@ -490,8 +492,35 @@ double gemm_flops(tdvp_ctx* ctx, const Views& v, int op, int site) {
   return 8.0 * f;
 }
 
+// K splits for a GEMM with few output tiles: enough blocks to cover every SM twice, limited by the
+// inner tile count and by the workspace (T1 or T2 of each realisation, ws_cap elements).
+int split_for(tdvp_ctx* ctx, const Views& v, int op, int site, int M, int Nn, int nb) {
+  const bool splittable = op == OP_MV3 || op == OP_EL3 || op == OP_ER3 || op == OP_Z1 || op == OP_Z3;
+  if (!splittable) return 1;
+  const long long tiles = (long long)cdivi(M, 32) * cdivi(Nn, 32) * nb * v.R;
+  if (tiles >= 296) return 1;
+  int K = 0, nz = 1;
+  const Dims m = maxdims(ctx, site, v);
+  switch (op) {
+    case OP_MV3: K = m.Dr; nz = ctx->Wb[site + 1]; break;
+    case OP_EL3: K = m.Dl * ctx->d[site]; break;
+    case OP_ER3: K = ctx->d[site] * m.Dr; break;
+    case OP_Z1: K = m.Dr; break;
+    case OP_Z3: K = m.Dr; nz = ctx->Wb[site + 1]; break;
+  }
+  const int kt = nz * cdivi(K, 16);
+  int S = (int)std::min<long long>(cdivi(296, tiles), 16);
+  S = std::min(S, kt);
+  long long cap = 1LL << 62;
+  for (int r = v.r0; r < v.r0 + v.R; ++r) cap = std::min(cap, ctx->ws_cap[r]);
+  const long long need_per_split = (long long)nb * M * Nn;
+  S = (int)std::min<long long>(S, cap / std::max(1LL, need_per_split));
+  return std::max(1, S);
+}
+
 int g_op(tdvp_ctx* ctx, const Views& v, int op, int site, int M, int Nn, int nb) {
-  LAUNCHC(TDVP_CAT_GEMM, launch_gemm(op, site, v.sd, v.wk, v.R, ctx->N, M, Nn, nb, ctx->st));
+  const int S = split_for(ctx, v, op, site, M, Nn, nb);
+  LAUNCHC(TDVP_CAT_GEMM, launch_gemm(op, site, v.sd, v.wk, v.R, ctx->N, M, Nn, nb, S, ctx->st));
   if (ctx->prof) ctx->stats.prof_flops[TDVP_CAT_GEMM] += gemm_flops(ctx, v, op, site);
   return TDVP_OK;
 }
@@ -532,7 +561,7 @@ int env_right(tdvp_ctx* ctx, const Views& v, int i) {
 }
 
 int qr_blocks(tdvp_ctx* ctx, int R, int m) {
-  int B = cdivi(m, 32);
+  int B = cdivi(m, 8);
   B = std::max(1, std::min(B, 148));
   B = std::min(B, std::max(1, ctx->qr_cap / std::max(1, R)));
   return B;
@@ -570,7 +599,7 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
   a.nblk = nblk_for(n); a.flags = v.flags;
   int& kh = ctx->khist[2 * site + kind];
   const int guess = kh > 0 ? kh : 6;
-  a.jcheck = ctx->check_every ? 1 : std::max(1, guess - 1);
+  a.jcheck = ctx->check_every ? 1 : std::max(1, guess - 2);
   CK(cudaMemsetAsync(v.flags, 0, sizeof(int) * v.R, ctx->st));
   LAUNCHC(TDVP_CAT_LZVEC, launch_lz_start(a, ctx->st));
   int j = 0, batch = guess, rc;
@@ -614,8 +643,9 @@ int check_device_errors(tdvp_ctx* ctx) {
     if (ctx->h_err[r] != 0) {
       const int code = ctx->h_err[r];
       cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * ctx->R, ctx->st);
-      return fail(ctx, code == -5 ? TDVP_ERR_DEVICE_TIMEOUT : TDVP_ERR_INVALID_ARG,
-                  code == -5 ? "device barrier timed out" : "device kernel rejected its sizes");
+      return fail(ctx, code == -5 ? TDVP_ERR_DEVICE_TIMEOUT : (code == -6 ? TDVP_ERR_NAN : TDVP_ERR_INVALID_ARG),
+                  code == -5 ? "device barrier timed out"
+                             : (code == -6 ? "gauge-shift QR met a non-positive Gram pivot" : "device kernel rejected its sizes"));
     }
   return TDVP_OK;
 }
@@ -659,6 +689,7 @@ int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
   if ((rc = dalloc(ctx, H.mps_allocs, &W.w, nmax))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.V, (size_t)ldV * ctx->kmax))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.T1, (size_t)Wmax * nmax))) return rc;
+  ctx->ws_cap[r] = (long long)Wmax * nmax;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.T2, (size_t)Wmax * nmax))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.bond, (size_t)Dmax * Dmax))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.bond2, (size_t)Dmax * Dmax))) return rc;
@@ -698,7 +729,7 @@ extern "C" {
 
 int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site) {
   if (!ctx) return TDVP_ERR_INVALID_ARG;
-  if (r < 0 || r >= ctx->R || D < 1 || D > 512) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps: bad r or D");
+  if (r < 0 || r >= ctx->R || D < 1 || D > 256) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps: bad r or D");
   if (!ctx->rh[r].mpo) return fail(ctx, TDVP_ERR_STATE, "init_mps: build_mpo first");
   if (exciton_site < 0 || exciton_site >= ctx->n_el) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps: bad exciton site");
   CK(cudaSetDevice(ctx->dev));
@@ -745,7 +776,7 @@ int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const doub
   std::vector<int> bd(bond_dims, bond_dims + N + 1);
   if (bd[0] != 1 || bd[N] != 1) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: open ends must be 1");
   for (int i = 0; i < N; ++i) {
-    if (bd[i] < 1 || bd[i] > 512) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: bond dim out of range");
+    if (bd[i] < 1 || bd[i] > 256) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: bond dim out of range");
     if (i > 0 && bd[i] > ctx->d[i] * bd[i + 1]) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: Dl > d*Dr");
     if (bd[i + 1] > ctx->d[i] * bd[i]) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: Dr > Dl*d");
   }
@@ -938,7 +969,7 @@ int tdvp_debug_qr(tdvp_ctx* ctx, int m, int n, const double* C, double* Q, doubl
     Dmax = std::max<long long>(Dmax, std::max(bd[i], bd[i + 1]));
     mmax = std::max<long long>(mmax, std::max<long long>((long long)bd[i] * ctx->d[i], (long long)ctx->d[i] * bd[i + 1]));
   }
-  if ((long long)m * n > nmax || n > Dmax || m > mmax || n > 512)
+  if ((long long)m * n > nmax || n > Dmax || m > mmax || n > 256)
     return fail(ctx, TDVP_ERR_INVALID_ARG, "debug_qr: matrix larger than the work buffers");
   std::vector<zc> X((size_t)n * m);
   for (int a = 0; a < m; ++a)

@@ -135,13 +135,14 @@ struct GemmDesc {
   long long sAz, sBz;
   int opA, opB;           // 0: as stored, 1: transpose, 2: conjugate transpose, 3: conjugate
   const int* skip;        // if non-null and *skip != 0 the block does nothing
+  zc* ws;                 // workspace for split-K partials (null: split-K not allowed)
 };
 
 struct Ctx;  // host context (tdvp_ctx.cu)
 
 // Kernel launchers (each returns the cudaError_t of the launch).
 cudaError_t launch_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                        int maxM, int maxN, int nbatch, cudaStream_t st);
+                        int maxM, int maxN, int nbatch, int nsplit, cudaStream_t st);
 cudaError_t launch_wapply(int dir, int site, int lanczos, const SiteDev* sd, const WorkDev* wk, int R,
                           int N_sites, int max_xy, int n_rows, cudaStream_t st);
 cudaError_t launch_transpose_site(int to_scratch, int site, const SiteDev* sd, const WorkDev* wk, int R,
