@@ -40,10 +40,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "tf32x3"],
+                    help="arithmetic of the Lanczos matvecs on the timed arm; FP64 is always timed beside it")
     ap.add_argument("--D", type=int, default=64)
     ap.add_argument("--dt", type=float, default=10.0)
     ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--rank-rtol", type=float, default=1e-6,
+                    help="rank threshold of the gauge-shift QR, the same on both arms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-prof", action="store_true", help="time without per-launch events")
@@ -57,6 +60,7 @@ def workload(args):
                "model": "Frenkel-Holstein (synthetic FMO-sized, Debye bath)",
                "sites": len(p.chain()), "bond_dim": args.D, "dt_fs": args.dt,
                "krylov": f"adaptive Lanczos, tol {args.tol:g}", "precision": args.precision,
+           "rank_rtol": args.rank_rtol,
                "realisations_per_gpu": 1}
 
 
@@ -119,23 +123,25 @@ def flush_l2(buf):
     buf.add_(1)          # 256 MiB read+write through L2 (126 MB), on the current stream
 
 
-def run_ours(args, rank, world):
+PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2}
+TF32_OF_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rate ratio
+
+
+def timed_run(args, p, precision, rank, world, dev, stream, flush, prof):
+    """W warm-up steps, then K timed steps (L2 flushed before each); returns timing and populations."""
     import torch
     import paper_1907_12044_b300 as pkg
-    dev = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(dev)
-    p, cfg = workload(args)
-    N = len(p.chain())
-    stream = torch.cuda.current_stream()
     eng = pkg.Engine(n_realisations=1, stream=stream.cuda_stream)
+    eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
-    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    pops = [eng.observables(0)[0]]
     for _ in range(args.warmup):
-        eng.step(args.dt, 1, tol=args.tol)
+        eng.step(args.dt, 1, precision=PREC[precision], tol=args.tol)
+        pops.append(eng.observables(0)[0])
     torch.cuda.synchronize()
     eng.reset_stats()
-    if not args.no_prof:
+    if prof:
         eng.set_profiling(True)
     times = []
     if world > 1:
@@ -147,47 +153,84 @@ def run_ours(args, rank, world):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            eng.step(args.dt, 1, tol=args.tol)
+            eng.step(args.dt, 1, precision=PREC[precision], tol=args.tol)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+            pops.append(eng.observables(0)[0])
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     st = eng.stats()
     eng.set_profiling(False)
-    ms_local = float(np.sum(times))
-    ms = ms_local
+    eng.close()
+    ms = float(np.sum(times))
     if world > 1:
-        t = torch.tensor([ms_local], device="cuda", dtype=torch.float64)
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    updates_per_step = (2 * N - 1) * 1
-    value = updates_per_step * args.steps * world / (ms / 1e3)
+    return {"ms": ms, "stats": st, "pops": np.array(pops), "clocks": clk.summary()}
+
+
+def run_ours(args, rank, world):
+    import torch
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    p, cfg = workload(args)
+    N = len(p.chain())
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    prof = not args.no_prof
+    ref = timed_run(args, p, "fp64", rank, world, dev, stream, flush, prof)
+    run = ref if args.precision == "fp64" else timed_run(args, p, args.precision, rank, world, dev, stream, flush, prof)
+    updates = (2 * N - 1) * args.steps * world
+    value = updates / (run["ms"] / 1e3)
+    fp64_value = updates / (ref["ms"] / 1e3)
+    # population error of the timed arm against the FP64 arm on the same steps (Eq. error)
+    t = args.dt * np.arange(len(run["pops"]))
+    dP = np.abs(run["pops"] - ref["pops"])
+    err = float(np.sum(0.5 * (dP.sum(1)[1:] + dP.sum(1)[:-1]) * np.diff(t)) / (p.n_el * t[-1])) if len(t) > 1 else 0.0
+    st = run["stats"]
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)",
+           "warmup": args.warmup, "ms_per_step": run["ms"] / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "f64 (complex128)", "tf32": "tf32 tensor cores, f32 accumulate; f64 Lanczos/QR",
+                     "tf32x3": "tf32x3 split tensor cores, f32 accumulate; f64 Lanczos/QR"}[args.precision],
            "data": "synthetic (seeded FMO-sized Frenkel-Holstein chain)",
-           "config": dict(cfg, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+           "config": dict(cfg, precision=args.precision,
+                          parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                           l2="flushed between timed steps (256 MiB write)"),
-           "gpu_launches": int(st["kernel_launches"]), "clocks": clk.summary()}
-    # roofline of the dominant kernel (the FP64 contraction GEMM)
-    if not args.no_prof:
-        gms = st["prof_ms"]["gemm"]
-        gfl = st["prof_flops"]["gemm"]
-        nl = st["prof_launches"]["gemm"]
+           "fp64_arm": {"value": fp64_value, "unit": UNIT, "ms_per_step": ref["ms"] / args.steps,
+                        "kernel_time_ms": {k: round(v, 3) for k, v in ref["stats"]["prof_ms"].items()}},
+           "speedup_vs_fp64": value / fp64_value,
+           "pop_error_vs_fp64": {"eq_error_final": err, "max_abs_dP": float(dP.max()),
+                                 "steps_compared": len(t) - 1},
+           "gpu_launches": int(st["kernel_launches"]), "clocks": run["clocks"]}
+    if prof:
+        cat_ms = st["prof_ms"]
+        top = max(cat_ms, key=cat_ms.get)
+        total = sum(cat_ms.values())
+        gms, gfl, nl = cat_ms["gemm"], st["prof_flops"]["gemm"], st["prof_launches"]["gemm"]
         ach = gfl / (gms * 1e-3) / 1e12 if gms > 0 else None
-        total_prof = sum(st["prof_ms"].values())
-        out["roofline"] = {"kernel": "zgemm_kernel (FP64 complex contraction GEMMs)", "bound": "alu",
-                           "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                           "frac": ach / FP64_NOMINAL_TFLOPS if ach else None, "traffic": None,
-                           "peak_source": "B300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
+        if args.precision == "fp64":
+            peak, bound, src = FP64_NOMINAL_TFLOPS, "alu", "B300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)"
+        else:
+            pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {"bf16_tflops": 1800.0}
+            peak = pk["bf16_tflops"] * TF32_OF_BF16
+            bound, src = "tensor", "measured bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25"
+        if args.precision != "fp64":
+            gms, gfl, nl = cat_ms["tc_gemm"], st["prof_flops"]["tc_gemm"], st["prof_launches"]["tc_gemm"]
+            ach = gfl / (gms * 1e-3) / 1e12 if gms > 0 else None
+        out["roofline"] = {"kernel": "zgemm_kernel (FP64)" if args.precision == "fp64" else "tc_cgemm_kernel (tcgen05 kind::tf32)",
+                           "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                           "frac": ach / peak if ach else None, "traffic": None, "peak_source": src,
                            "launches": nl, "avg_launch_us": 1e3 * gms / max(nl, 1),
-                           "share_of_step": gms / max(total_prof, 1e-9)}
-        out["kernel_time_ms"] = {k: round(v, 3) for k, v in st["prof_ms"].items()}
+                           "share_of_step": gms / max(total, 1e-9),
+                           "note": "algorithmic flops = 8 per complex multiply-add of the logical product"}
+        out["kernel_time_ms"] = {k: round(v, 3) for k, v in cat_ms.items()}
+        out["dominant_category"] = top
     out["krylov"] = {"mean_dim": st["krylov_dim_sum"] / max(st["krylov_solves"], 1),
                      "max_dim": st["krylov_dim_max"], "host_syncs": st["host_syncs"]}
-    eng.close()
     return out, p
 
 
@@ -200,11 +243,12 @@ def run_e2e(args, p):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     eng = pkg.Engine(n_realisations=1)
+    eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
     d, bd, w = eng.chain_info(0)
     for _ in range(args.steps):
-        eng.step(args.dt, 1, tol=args.tol)
+        eng.step(args.dt, 1, precision=PREC[args.precision], tol=args.tol)
         pops, E, nrm = eng.observables(0)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
@@ -229,7 +273,7 @@ def oracle_rate(p, args, n_steps=1):
     N = len(p.chain())
     t0 = time.perf_counter()
     for _ in range(n_steps):
-        tdvp_ps_step(st, args.dt, tol=args.tol)
+        tdvp_ps_step(st, args.dt, tol=args.tol, rank_rtol=args.rank_rtol)
     dt = time.perf_counter() - t0
     return (2 * N - 1) * n_steps / dt, threads, dt
 

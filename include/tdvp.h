@@ -66,8 +66,12 @@ typedef struct {
 #define TDVP_ERR_NAN                  -6  /* a non-finite norm was met */
 #define TDVP_ERR_STATE                -7  /* call out of order (e.g. step before init) */
 
-/* Arithmetic of the contractions (H_eff.A, zero-site H0.D, environments). */
+/* Arithmetic of the Lanczos matvecs H_eff.A (Eq. tdvp2_C) and H0.D (Eq. tdvp2_D).  The
+ * environments, the Lanczos orthogonalisation, the tridiagonal exponential and the gauge-shift
+ * QR are FP64 in every mode. */
 #define TDVP_PREC_FP64   0   /* complex double on the FP64 pipe */
+#define TDVP_PREC_TF32   1   /* tcgen05 kind::tf32, 4 real products per complex product, FP32 accumulation */
+#define TDVP_PREC_TF32X3 2   /* as TF32 with hi/lo split operands, hi*hi + hi*lo + lo*hi (FP32-level products) */
 
 /* Krylov dimension control. */
 #define TDVP_KRYLOV_ADAPTIVE 0   /* grow k until the a-posteriori estimate meets the tolerance */
@@ -130,9 +134,14 @@ int tdvp_move_center(tdvp_ctx* ctx, int r, int site);
 int tdvp_center_to_zero(tdvp_ctx* ctx, int r);
 
 /* y = H[i] x for the effective Hamiltonian of Eq. tdvp1_H at site i of
- * realisation r, with the stored environments (valid at the current centre).
- * x, y: host arrays of Dl*d*Dr complex. */
-int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, const double* x, double* y);
+ * realisation r, with the stored environments (valid at the current centre), in the
+ * arithmetic `precision` (TDVP_PREC_*).  x, y: host arrays of Dl*d*Dr complex. */
+int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, int precision, const double* x, double* y);
+
+/* y = H0 x for the zero-site Hamiltonian of Eq. tdvp2_D on the bond (i, i+1):
+ * sum_w h[1:i]_w x h[i+1:N]_w^T with the stored left environment of site i+1 and right
+ * environment of site i.  x, y: host arrays of D*D complex (D = bond dimension). */
+int tdvp_apply_h0(tdvp_ctx* ctx, int r, int i, int precision, const double* x, double* y);
 
 /* Gauge-shift decomposition of Eq. QR on the device, exposed for testing:
  * C (m x n, m >= n, row-major complex, host) = Q R with Q orthonormal columns
@@ -154,7 +163,8 @@ int tdvp_debug_expm(tdvp_ctx* ctx, int r, int i, double z_re, double z_im, doubl
 #define TDVP_CAT_TRIDIAG 3   /* tridiagonal exponential, convergence test, next Krylov vector */
 #define TDVP_CAT_QR      4   /* gauge-shift QR/LQ and its transposes */
 #define TDVP_CAT_OTHER   5
-#define TDVP_NCAT        6
+#define TDVP_CAT_TC      6   /* tcgen05 complex GEMMs of the mixed-precision matvecs */
+#define TDVP_NCAT        7
 
 typedef struct {
   long long steps;             /* completed time steps (per realisation) */
@@ -207,6 +217,18 @@ void tdvp_reset_stats(tdvp_ctx* ctx);
  * GPU (other streams, other host threads) race and give wrong results; serialise them.
  * Returns TDVP_ERR_DEVICE_TIMEOUT if a bounded device-side wait gave up. */
 int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* cuda_stream);
+
+/* Options of a context (take effect from the next call):
+ *   TDVP_OPT_RANK_RTOL: relative rank threshold of the gauge-shift QR (default 1e-13); a column
+ *     whose residual after two Gram-Schmidt passes is <= value * ||C||_F is replaced by the
+ *     completion vector.  From a product start most bonds are rank deficient and this threshold
+ *     decides which directions are completed; raising it (e.g. to 1e-6) makes those decisions
+ *     insensitive to arithmetic noise of the mixed-precision matvecs.
+ *   TDVP_OPT_KRYLOV_CHECK_ALL: 1 = test Lanczos convergence at every k, 0 (default) = from the
+ *     last Krylov dimension of the same site minus 2 on. */
+#define TDVP_OPT_RANK_RTOL         1
+#define TDVP_OPT_KRYLOV_CHECK_ALL  2
+int tdvp_set_option(tdvp_ctx* ctx, int option, double value);
 
 const char* tdvp_last_error(const tdvp_ctx* ctx);
 void tdvp_destroy(tdvp_ctx* ctx);

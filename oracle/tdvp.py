@@ -48,7 +48,7 @@ class TDVPState:
         return cls(W=W, mps=mps, Lenv=Lenv, Renv=Renv, kinds=kinds)
 
 
-def tdvp_ps_step(st: TDVPState, dt_fs: float, tol=1e-12, kmax=60):
+def tdvp_ps_step(st: TDVPState, dt_fs: float, tol=1e-12, kmax=60, rank_rtol=1e-13):
     """Advance by dt with the symmetric second-order split of Eq. ps_trotter.
 
     Left-to-right half sweep with tau/2 (Eq. tdvp2_C forward, Eq. QR, Eq. tdvp2_D
@@ -56,6 +56,7 @@ def tdvp_ps_step(st: TDVPState, dt_fs: float, tol=1e-12, kmax=60):
     (one exponential, reading of the middle factor of Eq. ps_trotter), then the
     mirror right-to-left half sweep with LQ, ending with the forward step of site 1.
     H is in cm^-1 and dt in fs, so the exponent is -i * (2 pi c) * dt * H.
+    ``rank_rtol`` is the relative rank threshold of the gauge-shift QR (see qr_rr).
     """
     tau = dt_fs * PHASE_PER_CM_FS
     A, W, L, R = st.mps, st.W, st.Lenv, st.Renv
@@ -69,7 +70,7 @@ def tdvp_ps_step(st: TDVPState, dt_fs: float, tol=1e-12, kmax=60):
     for i in range(N - 1):
         fwd(i, tau / 2)
         Dl, d, Dr = A[i].shape
-        Q, Rm = qr_rr(A[i].reshape(Dl * d, Dr))
+        Q, Rm = qr_rr(A[i].reshape(Dl * d, Dr), rank_rtol)
         A[i] = Q.reshape(Dl, d, Dr)
         L[i + 1] = env_left(L[i], A[i], W[i])
         Rm = lanczos_expm(lambda x: h0_apply(L[i + 1], R[i], x), Rm, 1j * tau / 2, tol, kmax, stats=kd)
@@ -77,7 +78,7 @@ def tdvp_ps_step(st: TDVPState, dt_fs: float, tol=1e-12, kmax=60):
     fwd(N - 1, tau)
     for i in range(N - 1, 0, -1):
         Dl, d, Dr = A[i].shape
-        Dm, Qr = lq_rr(A[i].reshape(Dl, d * Dr))
+        Dm, Qr = lq_rr(A[i].reshape(Dl, d * Dr), rank_rtol)
         A[i] = Qr.reshape(Dl, d, Dr)
         R[i - 1] = env_right(R[i], A[i], W[i])
         Dm = lanczos_expm(lambda x: h0_apply(L[i], R[i - 1], x), Dm, 1j * tau / 2, tol, kmax, stats=kd)

@@ -4,9 +4,9 @@ The time evolution runs in ``libtdvp.so`` (hand-written CUDA for sm_103a behind 
 ``include/tdvp.h``); this package only loads the library and marshals arguments.  There is no
 CPU path: if the library is missing, ``Engine`` raises.
 """
-from ._lib import (Engine, TDVPError, load_library, library_path, lq_noalloc, PREC_FP64,
-                   KRYLOV_ADAPTIVE, EXPORTED_SYMBOLS)
+from ._lib import (Engine, TDVPError, load_library, library_path, lq_noalloc, PREC_FP64, PREC_TF32,
+                   PREC_TF32X3, KRYLOV_ADAPTIVE, OPT_RANK_RTOL, OPT_KRYLOV_CHECK_ALL, EXPORTED_SYMBOLS)
 from .build import build
 
-__all__ = ["Engine", "TDVPError", "load_library", "library_path", "lq_noalloc", "build", "PREC_FP64",
-           "KRYLOV_ADAPTIVE", "EXPORTED_SYMBOLS"]
+__all__ = ["Engine", "TDVPError", "load_library", "library_path", "lq_noalloc", "build", "PREC_FP64", "PREC_TF32", "PREC_TF32X3",
+           "KRYLOV_ADAPTIVE", "OPT_RANK_RTOL", "OPT_KRYLOV_CHECK_ALL", "EXPORTED_SYMBOLS"]

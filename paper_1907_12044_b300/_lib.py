@@ -9,6 +9,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 PREC_FP64 = 0
+PREC_TF32 = 1
+PREC_TF32X3 = 2
 KRYLOV_ADAPTIVE = 0
 
 ERRORS = {
@@ -22,7 +24,7 @@ EXPORTED_SYMBOLS = [
     "tdvp_observables", "tdvp_chain_info", "tdvp_get_site", "tdvp_move_center",
     "tdvp_center_to_zero", "tdvp_apply_heff", "tdvp_debug_qr", "tdvp_debug_expm", "tdvp_stats",
     "tdvp_reset_stats", "tdvp_last_error", "tdvp_destroy", "tdvp_set_profiling",
-    "tdvp_lq_noalloc",
+    "tdvp_lq_noalloc", "tdvp_apply_h0", "tdvp_set_option",
 ]
 
 
@@ -40,8 +42,10 @@ class FHParamsC(C.Structure):
                 ("include_zpe", C.c_int)]
 
 
-NCAT = 6
-CATEGORIES = ["gemm", "wapply", "lanczos_vec", "tridiag", "qr", "other"]
+NCAT = 7
+CATEGORIES = ["gemm", "wapply", "lanczos_vec", "tridiag", "qr", "other", "tc_gemm"]
+OPT_RANK_RTOL = 1
+OPT_KRYLOV_CHECK_ALL = 2
 
 
 class StatsC(C.Structure):
@@ -82,11 +86,13 @@ def load_library():
     lib.tdvp_get_site.argtypes = [P, C.c_int, C.c_int, dp]
     lib.tdvp_move_center.argtypes = [P, C.c_int, C.c_int]
     lib.tdvp_center_to_zero.argtypes = [P, C.c_int]
-    lib.tdvp_apply_heff.argtypes = [P, C.c_int, C.c_int, dp, dp]
+    lib.tdvp_apply_heff.argtypes = [P, C.c_int, C.c_int, C.c_int, dp, dp]
+    lib.tdvp_apply_h0.argtypes = [P, C.c_int, C.c_int, C.c_int, dp, dp]
     lib.tdvp_debug_qr.argtypes = [P, C.c_int, C.c_int, dp, dp, dp]
     lib.tdvp_debug_expm.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, ip]
     lib.tdvp_stats.argtypes = [P, C.POINTER(StatsC)]
     lib.tdvp_set_profiling.argtypes = [P, C.c_int]
+    lib.tdvp_set_option.argtypes = [P, C.c_int, C.c_double]
     lib.tdvp_lq_noalloc.argtypes = [C.c_int, C.c_int, P, P, P, P]
     lib.tdvp_reset_stats.argtypes = [P]
     lib.tdvp_reset_stats.restype = None
@@ -204,10 +210,18 @@ class Engine:
     def center_to_zero(self, r):
         self._check(self.lib.tdvp_center_to_zero(self._h, r))
 
-    def apply_heff(self, r, i, x):
+    def apply_heff(self, r, i, x, precision=PREC_FP64):
         x = np.ascontiguousarray(x, dtype=np.complex128)
         y = np.zeros_like(x)
-        self._check(self.lib.tdvp_apply_heff(self._h, r, i, _dptr(x.view(np.float64)), _dptr(y.view(np.float64))))
+        self._check(self.lib.tdvp_apply_heff(self._h, r, i, int(precision), _dptr(x.view(np.float64)),
+                                             _dptr(y.view(np.float64))))
+        return y
+
+    def apply_h0(self, r, i, x, precision=PREC_FP64):
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        y = np.zeros_like(x)
+        self._check(self.lib.tdvp_apply_h0(self._h, r, i, int(precision), _dptr(x.view(np.float64)),
+                                           _dptr(y.view(np.float64))))
         return y
 
     def debug_qr(self, Cm):
@@ -235,6 +249,9 @@ class Engine:
             v = getattr(s, k)
             out[k] = {c: v[i] for i, c in enumerate(CATEGORIES)} if k.startswith("prof_") else v
         return out
+
+    def set_option(self, option, value):
+        self._check(self.lib.tdvp_set_option(self._h, int(option), float(value)))
 
     def set_profiling(self, on=True):
         self._check(self.lib.tdvp_set_profiling(self._h, 1 if on else 0))

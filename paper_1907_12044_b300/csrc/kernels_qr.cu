@@ -30,7 +30,13 @@ constexpr int QT = TDVP_QR_THREADS;       // 256 threads = 8 warps
 constexpr int NW = QT / 32;
 constexpr int QR_NMAX = 256;              // largest n (bond dimension) handled
 constexpr int PB = 8;                     // panel height
-constexpr long long SPIN_LIMIT = 1LL << 24;
+constexpr unsigned long long WAIT_NS = 1000000000ull;   // a barrier wait gives up after 1 s
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct QrJob {
   zc* X;
@@ -53,8 +59,10 @@ __device__ QrJob qr_job(int dir, int site, const SiteDev* sdr, const WorkDev& W,
   return J;
 }
 
-// Bounded barrier over the B blocks of one realisation.  Returns false if this or an earlier
-// wait gave up (the caller then returns).
+// Bounded two-level barrier over the B blocks of one realisation: blocks arrive on one of
+// ceil(B/16) group counters, the last of each group on the root counter, and the last root
+// arrival advances the generation word everybody polls.  Counter words: bar[0] = root,
+// bar[1] = generation, bar[2 + g] = group g.  Returns false if this or an earlier wait gave up.
 __device__ bool group_sync(const WorkDev& W, int nblocks) {
   __shared__ int ok;
   __syncthreads();
@@ -63,20 +71,34 @@ __device__ bool group_sync(const WorkDev& W, int nblocks) {
     volatile int* err = W.err;
     int good = (*err == 0);
     if (good && nblocks > 1) {
+      const int b = blockIdx.x % nblocks;
+      const int ngroups = (nblocks + 15) / 16;
+      const int grp = b / 16;
+      const unsigned gsize = (unsigned)min(16, nblocks - grp * 16);
       const unsigned g = *gen;
       __threadfence();
-      const unsigned arrived = atomicAdd(W.bar, 1u) + 1u;
-      if (arrived == (unsigned)nblocks) {
-        atomicExch(W.bar, 0u);
-        __threadfence();
-        atomicAdd(W.bar + 1, 1u);
-      } else {
-        long long spins = 0;
-        while (*gen == g) {
-          if (*err != 0) { good = 0; break; }
-          if (++spins > SPIN_LIMIT) { atomicExch(W.err, -5); good = 0; break; }
-          __nanosleep(32);
+      bool last = true;
+      if (ngroups > 1) {
+        const unsigned a = atomicAdd(W.bar + 2 + grp, 1u) + 1u;
+        last = (a == gsize);
+        if (last) {
+          atomicExch(W.bar + 2 + grp, 0u);
+          __threadfence();
         }
+      }
+      if (last) {
+        const unsigned need = ngroups > 1 ? (unsigned)ngroups : (unsigned)nblocks;
+        const unsigned a = atomicAdd(W.bar, 1u) + 1u;
+        if (a == need) {
+          atomicExch(W.bar, 0u);
+          __threadfence();
+          atomicAdd(W.bar + 1, 1u);
+        }
+      }
+      const unsigned long long t0 = gtimer();
+      while (*gen == g) {
+        if (*err != 0) { good = 0; break; }
+        if (gtimer() - t0 > WAIT_NS) { atomicExch(W.err, -5); good = 0; break; }
       }
       __threadfence();
     }
@@ -87,10 +109,23 @@ __device__ bool group_sync(const WorkDev& W, int nblocks) {
 }
 
 // sum_c conj(b[c]) a[c] over the whole row by one warp (rows may be written by other blocks).
+// Four independent accumulators keep eight L2 loads per lane in flight.
 __device__ __forceinline__ zc warp_dot(const zc* a, const zc* b, int m) {
   const int lane = threadIdx.x % 32;
-  zc s = zmake(0, 0);
-  for (int c = lane; c < m; c += 32) s = zcfma(__ldcg(b + c), __ldcg(a + c), s);
+  zc s0 = zmake(0, 0), s1 = s0, s2 = s0, s3 = s0;
+  int c = lane;
+  for (; c + 96 < m; c += 128) {
+    const zc b0 = __ldcg(b + c), a0 = __ldcg(a + c);
+    const zc b1 = __ldcg(b + c + 32), a1 = __ldcg(a + c + 32);
+    const zc b2 = __ldcg(b + c + 64), a2 = __ldcg(a + c + 64);
+    const zc b3 = __ldcg(b + c + 96), a3 = __ldcg(a + c + 96);
+    s0 = zcfma(b0, a0, s0);
+    s1 = zcfma(b1, a1, s1);
+    s2 = zcfma(b2, a2, s2);
+    s3 = zcfma(b3, a3, s3);
+  }
+  for (; c < m; c += 32) s0 = zcfma(__ldcg(b + c), __ldcg(a + c), s0);
+  zc s = zadd(zadd(s0, s1), zadd(s2, s3));
   for (int o = 16; o > 0; o >>= 1) {
     s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
     s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
@@ -117,7 +152,18 @@ __device__ void slab_update(zc* X, int m, int row0, int nb, int T, const zc* Hs,
     if (active) {
       r = e / cs;
       c = c0 + e % cs;
-      for (int t = sub; t < T; t += tpe) acc = zfma(Hs[r * ldh + t], X[(long long)t * m + c], acc);
+      zc a1 = zmake(0, 0), a2 = a1, a3 = a1;
+      int t = sub;
+      for (; t + 3 * tpe < T; t += 4 * tpe) {
+        const zc x0 = X[(long long)t * m + c], x1 = X[(long long)(t + tpe) * m + c];
+        const zc x2 = X[(long long)(t + 2 * tpe) * m + c], x3 = X[(long long)(t + 3 * tpe) * m + c];
+        acc = zfma(Hs[r * ldh + t], x0, acc);
+        a1 = zfma(Hs[r * ldh + t + tpe], x1, a1);
+        a2 = zfma(Hs[r * ldh + t + 2 * tpe], x2, a2);
+        a3 = zfma(Hs[r * ldh + t + 3 * tpe], x3, a3);
+      }
+      for (; t < T; t += tpe) acc = zfma(Hs[r * ldh + t], X[(long long)t * m + c], acc);
+      acc = zadd(zadd(acc, a1), zadd(a2, a3));
     }
     for (int o = tpe / 2; o > 0; o >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -155,7 +201,7 @@ struct Scratch {
   zc* H2;     // [PB][n]  second-pass coefficients
   zc* G;      // [PB][PB] Gram matrix
   zc* hv;     // [2n]     coefficients of the row-by-row path
-  zc* Pn;     // [B]      per-block scalars
+  zc* Pn;     // [2B]     per-block scalars
   zc* Pc;     // [2B]     per-block completion candidates
 };
 
@@ -165,6 +211,8 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
   __shared__ zc Hs[PB * QR_NMAX];
   __shared__ zc L1[PB][PB];
   __shared__ zc L2[PB][PB];
+  __shared__ zc Gs[PB][PB];
+  __shared__ double Gd[PB];
   __shared__ double red[NW];
   __shared__ int flag[2];
   const int r = blockIdx.x / B, b = blockIdx.x % B;
@@ -185,7 +233,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
   S.G = S.H2 + PB * n;
   S.hv = S.G + PB * PB;
   S.Pn = S.hv + 2 * n;
-  S.Pc = S.Pn + B;
+  S.Pc = S.Pn + 2 * B;
   double* colsq = W.colsq;
 
   // ||X||_F and the rank threshold
@@ -232,24 +280,31 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
       }
       if (!group_sync(W, B)) return;
       zc (*Lc)[PB] = it ? L2 : L1;
-      if (threadIdx.x == 0) {
+      // Gram matrix into shared memory with one parallel load, then a right-looking Cholesky in
+      // warp 0 with one lane per entry of the trailing triangle (no serial global loads).
+      for (int e = threadIdx.x; e < nb * nb; e += QT) {
+        const int i = e / nb, k = e % nb;
+        Gs[i][k] = (k <= i) ? __ldcg(S.G + i * PB + k) : zmake(0, 0);
+        if (i == k) Gd[i] = Gs[i][k].x;
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {
         int bad = 0;
         for (int jj = 0; jj < nb; ++jj) {
-          const double gjj = __ldcg(S.G + jj * PB + jj).x;
-          double s = gjj;
-          for (int k = 0; k < jj; ++k) s -= zabs2(Lc[jj][k]);
-          if (!(s > 0.0) || (it == 0 && (s <= 1e-10 * gjj || s <= 1e8 * thresh * thresh))) { bad = it + 1; break; }
-          const double d = sqrt(s);
-          Lc[jj][jj] = zmake(d, 0);
-          const double inv = 1.0 / d;
-          for (int i = jj + 1; i < nb; ++i) {
-            zc v = __ldcg(S.G + i * PB + jj);
-            for (int k = 0; k < jj; ++k) v = zfms(Lc[i][k], zconj(Lc[jj][k]), v);
-            Lc[i][jj] = zscale(v, inv);
+          const double s = Gs[jj][jj].x;            // Schur complement pivot
+          if (!(s > 0.0) || (it == 0 && (s <= 1e-10 * Gd[jj] || s <= 1e8 * thresh * thresh))) { bad = it + 1; break; }
+          const double d = sqrt(s), inv = 1.0 / d;
+          for (int i = lane; i < nb; i += 32)
+            Lc[i][jj] = (i < jj) ? zmake(0, 0) : (i == jj ? zmake(d, 0) : zscale(Gs[i][jj], inv));
+          __syncwarp();
+          const int T = nb - jj - 1;
+          for (int e = lane; e < T * T; e += 32) {
+            const int i = jj + 1 + e / T, k = jj + 1 + e % T;
+            if (k <= i) Gs[i][k] = zfms(Lc[i][jj], zconj(Lc[k][jj]), Gs[i][k]);
           }
-          for (int i = 0; i < jj; ++i) Lc[i][jj] = zmake(0, 0);
+          __syncwarp();
         }
-        flag[0] = bad;
+        if (lane == 0) flag[0] = bad;
       }
       __syncthreads();
       if (flag[0] == 2) {              // the rows are already orthonormal to ~1e-6 here
@@ -292,51 +347,36 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
       continue;
     }
     // ---- exact row-by-row path for this panel ----
+    // Per row: (A) first-pass dots; (B) update, residual norm and completion candidates;
+    // full rows: (C) second-pass dots, (D) update and normalise; rank-deficient rows:
+    // (C') completion vector e_p - sum_t conj(Q_t[p]) Q_t and its norm, (D') normalise.
+    // The rank decision is taken on the residual after the first pass (the second pass
+    // changes it by O(eps ||x||), far below the threshold), and a completion vector is at
+    // distance >= 1/2 from the span, so one projection pass leaves it orthogonal to O(eps).
     for (int j = j0; j < j0 + nb; ++j) {
       const int rr = j - j0;
       zc* x = X + (long long)j * m;
-      for (int pass = 0; pass < 2; ++pass) {
-        zc* hb = S.hv + pass * n;
-        for (int t = gw; t < j; t += nwarps) {
-          const zc s = warp_dot(x, X + (long long)t * m, m);
-          if (lane == 0) hb[t] = s;
-        }
-        if (!group_sync(W, B)) return;
-        for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(hb + t);
-        __syncthreads();
-        slab_update(X, m, j, 1, j, Hs, j, c0, c1);
-        if (pass == 0 && !group_sync(W, B)) return;
-      }
-      {
-        double s = 0;
-        for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(x[c]);
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) S.Pn[b] = zmake(s, 0);
+      // (A)
+      for (int t = gw; t < j; t += nwarps) {
+        const zc s = warp_dot(x, X + (long long)t * m, m);
+        if (lane == 0) S.hv[t] = s;
       }
       if (!group_sync(W, B)) return;
-      const double nrm = sqrt(sum_over_blocks(S.Pn, B));
-      const bool full = nrm > thresh;
-      if (b == 0) {
-        for (int t = threadIdx.x; t < n; t += QT) {
-          zc v = zmake(0, 0);
-          if (t < j) {
-            v = zadd(__ldcg(S.hv + t), __ldcg(S.hv + n + t));
-            if (t < j0) v = zadd(v, zadd(__ldcg(S.H1 + rr * n + t), __ldcg(S.H2 + rr * n + t)));
-          } else if (t == j) {
-            v = zmake(full ? nrm : 0.0, 0);
-          }
-          J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
-        }
-      }
-      if (!full) {
-        // completion by the first unit vector at distance >= 1/2 from rows 0..j-1
+      // (B)
+      for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(S.hv + t);
+      __syncthreads();
+      slab_update(X, m, j, 1, j, Hs, j, c0, c1);
+      {
+        double s = 0;
         int first = 0x7fffffff, besti = 0x7fffffff;
         double bestv = -1.0;
         for (int c = c0 + threadIdx.x; c < c1; c += QT) {
+          s += zabs2(x[c]);
           const double dist = 1.0 - colsq[c];
           if (dist >= 0.25 && c < first) first = c;
           if (dist > bestv || (dist == bestv && c < besti)) { bestv = dist; besti = c; }
         }
+        s = block_sum(s, red);
         for (int o = 16; o > 0; o >>= 1) {
           const int f2 = __shfl_xor_sync(0xffffffffu, first, o);
           const double v2 = __shfl_xor_sync(0xffffffffu, bestv, o);
@@ -345,56 +385,90 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
           if (v2 > bestv || (v2 == bestv && i2 < besti)) { bestv = v2; besti = i2; }
         }
         __syncthreads();
-        if (lane == 0) { Hs[2 * (threadIdx.x / 32)] = zmake((double)first, bestv); Hs[2 * (threadIdx.x / 32) + 1] = zmake((double)besti, 0); }
+        if (lane == 0) { Hs[PB * QR_NMAX - 2 * NW + 2 * (threadIdx.x / 32)] = zmake((double)first, bestv);
+                         Hs[PB * QR_NMAX - 2 * NW + 2 * (threadIdx.x / 32) + 1] = zmake((double)besti, 0); }
         __syncthreads();
         if (threadIdx.x == 0) {
-          double f = Hs[0].x, bv = Hs[0].y, bi = Hs[1].x;
+          const zc* cw = Hs + PB * QR_NMAX - 2 * NW;
+          double f = cw[0].x, bv = cw[0].y, bi = cw[1].x;
           for (int w = 1; w < NW; ++w) {
-            f = fmin(f, Hs[2 * w].x);
-            const double v2 = Hs[2 * w].y, i2 = Hs[2 * w + 1].x;
+            f = fmin(f, cw[2 * w].x);
+            const double v2 = cw[2 * w].y, i2 = cw[2 * w + 1].x;
             if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
           }
+          S.Pn[b] = zmake(s, 0);
           S.Pc[2 * b] = zmake(f, 0);
           S.Pc[2 * b + 1] = zmake(bv, bi);
         }
+      }
+      if (!group_sync(W, B)) return;
+      const double s1 = sum_over_blocks(S.Pn, B);
+      const bool full = sqrt(s1) > thresh;
+      double en;
+      if (full) {
+        // (C)
+        for (int t = gw; t < j; t += nwarps) {
+          const zc s = warp_dot(x, X + (long long)t * m, m);
+          if (lane == 0) S.hv[n + t] = s;
+        }
         if (!group_sync(W, B)) return;
-        if (threadIdx.x == 0) {
+        // (D)
+        for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(S.hv + n + t);
+        __syncthreads();
+        slab_update(X, m, j, 1, j, Hs, j, c0, c1);
+        double hh = 0;
+        {
+          double v = 0;
+          for (int t = threadIdx.x; t < j; t += QT) v += zabs2(Hs[t]);
+          hh = block_sum(v, red);
+        }
+        en = sqrt(fmax(s1 - hh, 0.0));
+      } else {
+        // (C') completion from the first unit vector at distance >= 1/2 (else the farthest)
+        if (threadIdx.x < 32) {
           double f = 2147483647.0, bv = -2.0, bi = 2147483647.0;
-          for (int bb = 0; bb < B; ++bb) {
+          for (int bb = lane; bb < B; bb += 32) {
             f = fmin(f, __ldcg(S.Pc + 2 * bb).x);
             const zc q = __ldcg(S.Pc + 2 * bb + 1);
             if (q.x > bv || (q.x == bv && q.y < bi)) { bv = q.x; bi = q.y; }
           }
-          flag[1] = (f < 2147483647.0) ? (int)f : (int)bi;
+          for (int o = 16; o > 0; o >>= 1) {
+            const double f2 = __shfl_xor_sync(0xffffffffu, f, o);
+            const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+            const double i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            f = fmin(f, f2);
+            if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
+          }
+          if (lane == 0) flag[1] = (f < 2147483647.0) ? (int)f : (int)bi;
         }
         __syncthreads();
         const int p = flag[1];
-        if (!group_sync(W, B)) return;            // everyone has read the candidates
-        if (p >= c0 && p < c1)
-          for (int t = threadIdx.x; t < j; t += QT) W.qhp[t] = zconj(X[(long long)t * m + p]);
-        if (!group_sync(W, B)) return;
-        for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(W.qhp + t);
+        for (int t = threadIdx.x; t < j; t += QT) Hs[t] = zconj(__ldcg(X + (long long)t * m + p));
         for (int c = c0 + threadIdx.x; c < c1; c += QT) x[c] = zmake(c == p ? 1.0 : 0.0, 0);
-        __syncthreads();
-        slab_update(X, m, j, 1, j, Hs, j, c0, c1);
-        if (!group_sync(W, B)) return;
-        for (int t = gw; t < j; t += nwarps) {
-          const zc s = warp_dot(x, X + (long long)t * m, m);
-          if (lane == 0) S.hv[t] = s;
-        }
-        if (!group_sync(W, B)) return;
-        for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(S.hv + t);
         __syncthreads();
         slab_update(X, m, j, 1, j, Hs, j, c0, c1);
         {
           double s = 0;
           for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(x[c]);
           s = block_sum(s, red);
-          if (threadIdx.x == 0) S.Pn[b] = zmake(s, 0);
+          if (threadIdx.x == 0) S.Pn[B + b] = zmake(s, 0);
         }
         if (!group_sync(W, B)) return;
+        en = sqrt(sum_over_blocks(S.Pn + B, B));
       }
-      const double en = full ? nrm : sqrt(sum_over_blocks(S.Pn, B));
+      if (b == 0) {
+        for (int t = threadIdx.x; t < n; t += QT) {
+          zc v = zmake(0, 0);
+          if (t < j) {
+            v = __ldcg(S.hv + t);
+            if (full) v = zadd(v, __ldcg(S.hv + n + t));
+            if (t < j0) v = zadd(v, zadd(__ldcg(S.H1 + rr * n + t), __ldcg(S.H2 + rr * n + t)));
+          } else if (t == j) {
+            v = zmake(full ? en : 0.0, 0);
+          }
+          J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
+        }
+      }
       const double inv = en > 0 ? 1.0 / en : 0.0;
       for (int c = c0 + threadIdx.x; c < c1; c += QT) {
         const zc v = zscale(x[c], inv);

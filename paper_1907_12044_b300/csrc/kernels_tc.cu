@@ -1,0 +1,452 @@
+// Mixed-precision contractions of the Lanczos matvecs on the 5th-generation tensor cores.
+//
+// H[i] C (Eq. tdvp2_C) and the zero-site H0 D (Eq. tdvp2_D) are complex GEMMs.  Each runs as real
+// TF32 products on tcgen05 with FP32 accumulation in tensor memory:
+//   Dr += Ar Br - Ai Bi,   Di += Ai Br + Ar Bi        (4 real products, the A-negate bit gives -Ai)
+// and, in the compensated mode, every operand is split a = a_hi + a_lo (a_hi = TF32 rounding of a)
+// and the three terms hi*hi + hi*lo + lo*hi are accumulated (FP32-level products).
+//
+// Operands are produced by the pack kernels below directly in the tensor-core tile layout: a
+// matrix with R rows (R = 128 for the A operand, 64 for B) and K columns is cut into R x 32 tiles,
+// each stored contiguously in K-major "no swizzle" core-matrix order (8 rows x 16 bytes per core
+// matrix; core matrices adjacent in K are 128 bytes apart, 8-row groups 1024 bytes apart), planes
+// re_hi, im_hi, re_lo, im_lo one after another.  Padding rows/columns are zero.  A whole tile is
+// therefore one contiguous block that a 1-D bulk TMA copy moves into shared memory.
+//
+// GEMM kernel: one CTA per 128 x 64 output tile, 128 threads.  Thread 0 issues the bulk copies
+// (two-stage ring, mbarrier with transaction bytes) and the MMAs (tcgen05.mma, commit to an
+// mbarrier); all four warps then read the accumulators (tcgen05.ld) and write the epilogue.
+// Every wait is bounded: on timeout the CTA records an error, drains its copies and MMAs with
+// bounded waits, frees its tensor memory and returns.
+#include "tdvp_internal.cuh"
+#include <cstdint>
+
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 32;
+constexpr int A_TILE = BM * BK * 4;     // 16 KB per plane
+constexpr int B_TILE = BN * BK * 4;     //  8 KB per plane
+constexpr int NPL = 4;                  // planes: re_hi, im_hi, re_lo, im_lo
+constexpr int STAGE_BYTES = NPL * (A_TILE + B_TILE);   // 96 KB
+constexpr int STAGES = 2;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TMEM_COLS = 128;     // Dr: 0..63, Di: 64..127
+constexpr unsigned long long WAIT_NS = 1000000000ull;   // every wait gives up after 1 s
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait bounded in wall time; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > WAIT_NS) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle, LBO = 128 B (next core matrix in K),
+// SBO = 1024 B (next 8-row group); bits 46-48 = 0b001.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((128 >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// instruction descriptor: kind::tf32, D = F32, A = B = TF32, K-major, M = 128, N = 64
+__device__ __forceinline__ uint32_t idesc_tf32(bool negA) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// byte offset of element (row, k) in a packed operand with RT-row tiles and nkt K-tiles
+__device__ __forceinline__ long long pk_off(int RT, int nkt, int row, int k, int plane) {
+  const int rt = row / RT, r = row % RT, kt = k / BK, kk = k % BK;
+  const long long tile = ((long long)(rt * nkt + kt) * NPL + plane) * (RT * BK * 4);
+  return tile + (r / 8) * 1024 + (kk / 4) * 128 + (r % 8) * 16 + (kk % 4) * 4;
+}
+
+// store a complex value into the packed planes (hi/lo split when split != 0)
+__device__ __forceinline__ void pk_store(char* base, int RT, int nkt, int row, int k, double re, double im, int split) {
+  const float rh = tf32_round((float)re), ih = tf32_round((float)im);
+  *reinterpret_cast<float*>(base + pk_off(RT, nkt, row, k, 0)) = rh;
+  *reinterpret_cast<float*>(base + pk_off(RT, nkt, row, k, 1)) = ih;
+  if (split) {
+    *reinterpret_cast<float*>(base + pk_off(RT, nkt, row, k, 2)) = (float)(re - (double)rh);
+    *reinterpret_cast<float*>(base + pk_off(RT, nkt, row, k, 3)) = (float)(im - (double)ih);
+  }
+}
+
+__device__ __forceinline__ int cdivd(int a, int b) { return (a + b - 1) / b; }
+
+struct TcDesc {
+  const char* A;     // packed, 128-row tiles
+  const char* B;     // packed, 64-row tiles
+  int M, N, K;       // logical sizes
+  int mode;          // 0: planar FP32 (Cr, Ci), 1: complex FP64 (C64), 2: packed A of the next GEMM
+  float* Cr;
+  float* Ci;
+  zc* C64;
+  int ldc;
+  char* P;           // mode 2 target
+  int pDb, pnkt;     // mode 2: row m = w*Db + l' -> (l', w*Db + n)
+};
+
+// operands of the four tensor-core GEMMs, derived on the device from the site tables
+__device__ bool tc_desc(int op, int site, const SiteDev* sdr, const WorkDev& W, TcDesc& g) {
+  const SiteDev& s = sdr[site];
+  switch (op) {
+    case TC_MV1:   // T1[(w a')][(s b)] = sum_a L[w][a'][a] x[a][(s b)]
+      g.A = W.tc_l; g.B = W.tc_x;
+      g.M = s.Wl * s.Dl; g.N = s.d * s.Dr; g.K = s.Dl;
+      g.mode = 0; g.Cr = W.tc_t1; g.Ci = W.tc_t1 + W.tc_t1_plane; g.ldc = s.d * s.Dr;
+      return true;
+    case TC_MV3:   // w[(a' s')][b'] = sum_{w',b} T2[(a' s')][(w' b)] R[w'][b'][b]
+      g.A = W.tc_t2; g.B = W.tc_r;
+      g.M = s.Dl * s.d; g.N = s.Dr; g.K = s.Wr * s.Dr;
+      g.mode = 1; g.C64 = W.w; g.ldc = s.Dr;
+      return true;
+    case TC_Z1: {  // bond (site, site+1): T[(w l')][r] = sum_l Lb[w][l'][l] D[l][r]  -> packed A of Z3
+      const int Db = s.Dr, Wb = s.Wr;
+      g.A = W.tc_l; g.B = W.tc_x;
+      g.M = Wb * Db; g.N = Db; g.K = Db;
+      g.mode = 2; g.P = W.tc_t2; g.pDb = Db; g.pnkt = cdivd(Wb * Db, BK);
+      return true;
+    }
+    case TC_Z3: {  // w[l'][r'] = sum_{w,r} T[l'][(w r)] Rb[w][r'][r]
+      const int Db = s.Dr, Wb = s.Wr;
+      g.A = W.tc_t2; g.B = W.tc_r;
+      g.M = Db; g.N = Db; g.K = Wb * Db;
+      g.mode = 1; g.C64 = W.w; g.ldc = Db;
+      return true;
+    }
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
+                int split) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ TcDesc g;
+  __shared__ uint64_t full_bar[STAGES];
+  __shared__ uint64_t done_bar[STAGES];
+  __shared__ uint64_t drain_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int live, abort_flag, last_stage;
+  __shared__ uint32_t last_parity;
+  const int r = blockIdx.z;
+  const WorkDev& W = wk[r];
+  if (threadIdx.x == 0) {
+    const SiteDev* sdr = sd + (long long)r * N_sites;
+    live = tc_desc(op, site, sdr, W, g) && !W.ks->done && (int)blockIdx.y * BM < g.M && (int)blockIdx.x * BN < g.N;
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (!live) return;
+  const int warp = threadIdx.x / 32;
+  if (warp == 0) tmem_alloc(&tmem_base, TMEM_COLS);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&done_bar[s], 1); }
+    mbar_init(&drain_bar, 1);
+    mbar_fence_init();
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = tmem_base;
+  const int nkt = cdivd(g.K, BK);
+  const int mt = blockIdx.y, nt = blockIdx.x;
+  const int npl = split ? 4 : 2;
+  const uint32_t stage_tx = (uint32_t)npl * (A_TILE + B_TILE);
+  if (threadIdx.x == 0) {
+    last_stage = 0;
+    last_parity = 0;
+    auto issue = [&](int kt) {
+      const int s = kt % STAGES;
+      unsigned char* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], stage_tx);
+      for (int p = 0; p < npl; ++p) {
+        bulk_load(st + p * A_TILE, g.A + ((long long)(mt * nkt + kt) * NPL + p) * A_TILE, A_TILE, &full_bar[s]);
+        bulk_load(st + NPL * A_TILE + p * B_TILE, g.B + ((long long)(nt * nkt + kt) * NPL + p) * B_TILE, B_TILE,
+                  &full_bar[s]);
+      }
+    };
+    const uint32_t id_pos = idesc_tf32(false), id_neg = idesc_tf32(true);
+    const uint32_t dr = tmem, di = tmem + BN;
+    int issued = 0;
+    for (; issued < STAGES && issued < nkt; ++issued) issue(issued);
+    bool started = false;
+    for (int kt = 0; kt < nkt && !abort_flag; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t par = (uint32_t)((kt / STAGES) & 1);
+      if (!mbar_wait(&full_bar[s], par)) { abort_flag = 1; break; }
+      tc_after();
+      const uint32_t abase = su32(smem + s * STAGE_BYTES);
+      const uint32_t bbase = abase + NPL * A_TILE;
+#pragma unroll
+      for (int ks = 0; ks < BK / 8; ++ks) {
+        const uint32_t ko = ks * 256;   // 8 TF32 = 2 core matrices of 128 B
+        const uint64_t arh = sdesc(abase + 0 * A_TILE + ko), aih = sdesc(abase + 1 * A_TILE + ko);
+        const uint64_t brh = sdesc(bbase + 0 * B_TILE + ko), bih = sdesc(bbase + 1 * B_TILE + ko);
+        const uint32_t acc = started ? 1u : 0u;
+        mma_tf32(dr, arh, brh, id_pos, acc);
+        mma_tf32(dr, aih, bih, id_neg, 1u);
+        mma_tf32(di, aih, brh, id_pos, acc);
+        mma_tf32(di, arh, bih, id_pos, 1u);
+        if (split) {
+          const uint64_t arl = sdesc(abase + 2 * A_TILE + ko), ail = sdesc(abase + 3 * A_TILE + ko);
+          const uint64_t brl = sdesc(bbase + 2 * B_TILE + ko), bil = sdesc(bbase + 3 * B_TILE + ko);
+          mma_tf32(dr, arh, brl, id_pos, 1u);
+          mma_tf32(dr, arl, brh, id_pos, 1u);
+          mma_tf32(dr, aih, bil, id_neg, 1u);
+          mma_tf32(dr, ail, bih, id_neg, 1u);
+          mma_tf32(di, aih, brl, id_pos, 1u);
+          mma_tf32(di, ail, brh, id_pos, 1u);
+          mma_tf32(di, arh, bil, id_pos, 1u);
+          mma_tf32(di, arl, bih, id_pos, 1u);
+        }
+        started = true;
+      }
+      mma_commit(&done_bar[s]);
+      last_stage = s;
+      last_parity = par;
+      if (issued < nkt) {
+        // stage s is refilled once the MMAs that read it have completed
+        if (!mbar_wait(&done_bar[s], par)) { abort_flag = 1; break; }
+        issue(issued);
+        ++issued;
+      }
+    }
+    if (abort_flag) {
+      // drain (bounded): the newest copy of every stage, then every MMA issued so far
+      for (int s = 0; s < STAGES; ++s) {
+        int last = -1;
+        for (int kt = 0; kt < issued; ++kt) if (kt % STAGES == s) last = kt;
+        if (last >= 0) mbar_wait(&full_bar[s], (uint32_t)((last / STAGES) & 1));
+      }
+      mma_commit(&drain_bar);
+      mbar_wait(&drain_bar, 0);
+      atomicExch(W.err, -5);
+    }
+  }
+  __syncthreads();
+  // accumulators complete once the last commit's barrier flips
+  bool ok = true;
+  if (!abort_flag) ok = mbar_wait(&done_bar[last_stage], last_parity);
+  tc_after();
+  if (ok && !abort_flag) {
+    const int row = mt * BM + warp * 32 + (threadIdx.x % 32);
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int cb = 0; cb < BN; cb += 16) {
+      float vr[16], vi[16];
+      tmem_ld16(lane_addr + cb, vr);
+      tmem_ld16(lane_addr + BN + cb, vi);
+      if (row < g.M) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int col = nt * BN + cb + q;
+          if (col >= g.N) break;
+          if (g.mode == 0) {
+            g.Cr[(long long)row * g.ldc + col] = vr[q];
+            g.Ci[(long long)row * g.ldc + col] = vi[q];
+          } else if (g.mode == 1) {
+            g.C64[(long long)row * g.ldc + col] = zmake((double)vr[q], (double)vi[q]);
+          } else {
+            const int w = row / g.pDb, lp = row % g.pDb;
+            pk_store(g.P, BM, g.pnkt, lp, w * g.pDb + col, (double)vr[q], (double)vi[q], split);
+          }
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(W.err, -5);
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, TMEM_COLS);
+}
+
+// ---- pack kernels (all write only the valid region; the targets are zeroed beforehand) ----
+
+// Lenv[site] stacked as the A operand: row = w*Dl + a', k = a
+__global__ void pack_env_l_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
+                                  int N_sites, int split) {
+  const int r = blockIdx.y;
+  const SiteDev& s = sd[(long long)r * N_sites + site];
+  const WorkDev& W = wk[r];
+  const int M = s.Wl * s.Dl, K = s.Dl, nkt = cdivd(K, BK);
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)M * K) return;
+  const int row = (int)(e / K), k = (int)(e % K);
+  const zc v = s.Lenv[e];          // [w][a'][a] row-major = [(w a')][a]
+  pk_store(W.tc_l, BM, nkt, row, k, v.x, v.y, split);
+}
+
+// Renv[site] as the B operand: row = b', k = w*Dr + b
+__global__ void pack_env_r_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
+                                  int N_sites, int split) {
+  const int r = blockIdx.y;
+  const SiteDev& s = sd[(long long)r * N_sites + site];
+  const WorkDev& W = wk[r];
+  const int Dr = s.Dr, K = s.Wr * Dr, nkt = cdivd(K, BK);
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)s.Wr * Dr * Dr) return;
+  const int w = (int)(e / ((long long)Dr * Dr)), rem = (int)(e % ((long long)Dr * Dr));
+  const int bp = rem / Dr, b = rem % Dr;
+  const zc v = s.Renv[e];          // [w][b'][b]
+  pk_store(W.tc_r, BN, nkt, bp, w * Dr + b, v.x, v.y, split);
+}
+
+// x as the B operand.  kind 0 (site): row = (s b), k = a;  kind 1 (bond D[l][r]): row = r, k = l
+__global__ void pack_x_kernel(int kind, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
+                              int N_sites, int split) {
+  const int r = blockIdx.y;
+  const SiteDev& s = sd[(long long)r * N_sites + site];
+  const WorkDev& W = wk[r];
+  if (W.ks->done) return;
+  const int Kd = kind == 0 ? s.Dl : s.Dr;
+  const int Nn = kind == 0 ? s.d * s.Dr : s.Dr;
+  const int nkt = cdivd(Kd, BK);
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)Kd * Nn) return;
+  const int k = (int)(e / Nn), n = (int)(e % Nn);
+  const zc v = W.x[e];
+  pk_store(W.tc_x, BN, nkt, n, k, v.x, v.y, split);
+}
+
+// Sparse MPO middle stage from the planar FP32 T1 into the packed A operand of the third GEMM:
+// T2[(a' s')][(w' b)] = sum_e val * T1[(w a')][(s b)]  over the CSR row (w', s').
+__global__ void wapply_tc_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
+                                 int N_sites, int split) {
+  const int r = blockIdx.z;
+  const SiteDev& s = sd[(long long)r * N_sites + site];
+  const WorkDev& W = wk[r];
+  if (W.ks->done) return;
+  const int row = blockIdx.y;           // (w', s')
+  const int d = s.d, Dl = s.Dl, Dr = s.Dr;
+  if (row >= s.Wr * d) return;
+  const int xy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xy >= Dl * Dr) return;
+  const int ap = xy / Dr, b = xy % Dr;
+  const int wp = row / d, sp = row % d;
+  const float* T1r = W.tc_t1;
+  const float* T1i = W.tc_t1 + W.tc_t1_plane;
+  const long long ld = (long long)d * Dr;
+  double ar = 0, ai = 0;
+  for (int e = s.fw.ptr[row]; e < s.fw.ptr[row + 1]; ++e) {
+    const long long off = ((long long)s.fw.ci[e] * Dl + ap) * ld + (long long)s.fw.si[e] * Dr + b;
+    ar += s.fw.val[e] * (double)T1r[off];
+    ai += s.fw.val[e] * (double)T1i[off];
+  }
+  const int nkt = cdivd(s.Wr * Dr, BK);
+  pk_store(W.tc_t2, BM, nkt, ap * d + sp, wp * Dr + b, ar, ai, split);
+}
+
+inline int cdivh(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+long long tc_pack_bytes(int rows_tile, long long rows, long long K) {
+  return (long long)cdivh(rows, rows_tile) * cdivh(K, BK) * NPL * rows_tile * BK * 4;
+}
+
+cudaError_t tc_setup() {
+  return cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGES * STAGE_BYTES);
+}
+
+cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
+                           int maxN, int split, cudaStream_t st) {
+  dim3 grid(cdivh(maxN, BN), cdivh(maxM, BM), R);
+  tc_cgemm_kernel<<<grid, TC_THREADS, STAGES * STAGE_BYTES, st>>>(op, site, sd, wk, N_sites, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                            long long max_elems, int split, cudaStream_t st) {
+  dim3 grid(cdivh(max_elems, 256), R);
+  if (which == 0) pack_env_l_kernel<<<grid, 256, 0, st>>>(site, sd, wk, N_sites, split);
+  else pack_env_r_kernel<<<grid, 256, 0, st>>>(site, sd, wk, N_sites, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                          long long max_elems, int split, cudaStream_t st) {
+  dim3 grid(cdivh(max_elems, 256), R);
+  pack_x_kernel<<<grid, 256, 0, st>>>(kind, site, sd, wk, N_sites, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wapply_tc(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int max_xy,
+                             int n_rows, int split, cudaStream_t st) {
+  dim3 grid(cdivh(max_xy, 256), n_rows, R);
+  wapply_tc_kernel<<<grid, 256, 0, st>>>(site, sd, wk, N_sites, split);
+  return cudaGetLastError();
+}

@@ -14,7 +14,7 @@
 namespace {
 
 constexpr double kPhasePerCmFs = 2.0 * 3.14159265358979323846 * 2.99792458e-5;   // 2 pi c
-constexpr double kRankRtol = 1e-13;
+constexpr double kRankRtolDefault = 1e-13;
 
 struct RealHost {
   bool mpo = false, mps = false;
@@ -49,8 +49,11 @@ struct tdvp_ctx {
   std::vector<int> khist;     // last Krylov dim per (site, kind)
   std::vector<long long> ws_cap;   // elements of T1 (= T2) per realisation
   int qr_cap = 0;
+  double rank_rtol = kRankRtolDefault;
   int check_every = 0;        // 1: test Lanczos convergence at every k (else from the last k - 2 on)
   // per-launch timing
+  int l_site = -1, r_site = -1;     // site whose environment is packed in tc_l / tc_r
+  int l_split = -1, r_split = -1;
   int prof = 0;
   std::vector<cudaEvent_t> ev;   // pairs
   std::vector<int> ev_cat;
@@ -209,6 +212,7 @@ int tdvp_create(tdvp_ctx** out, int device, void* cuda_stream, int n_realisation
   ctx->h_work.assign(ctx->R, WorkDev{});
   ctx->ws_cap.assign(ctx->R, 0);
   ctx->qr_cap = qr_max_coresident_blocks(device);
+  if (tc_setup() != cudaSuccess) { tdvp_destroy(ctx); return TDVP_ERR_CUDA; }
   if (ctx->qr_cap < ctx->R) { tdvp_destroy(ctx); return TDVP_ERR_INVALID_ARG; }
   *out = ctx;
   return TDVP_OK;
@@ -542,10 +546,111 @@ int matvec_bond(tdvp_ctx* ctx, const Views& v, int i) {
   return g_op(ctx, v, OP_Z3, i, m.Dr, m.Dr, 1);
 }
 
+// ---- mixed-precision matvecs on the tensor cores ----
+long long used_bytes(tdvp_ctx* ctx, const Views& v, int rows_tile, int which, int site) {
+  long long b = 0;
+  for (int r = v.r0; r < v.r0 + v.R; ++r) {
+    const auto& bd = ctx->rh[r].bd;
+    const long long Dl = bd[site], Dr = bd[site + 1], d = ctx->d[site];
+    const long long Wl = ctx->Wb[site], Wr = ctx->Wb[site + 1];
+    long long x = 0;
+    switch (which) {
+      case 0: x = tc_pack_bytes(128, Wl * Dl, Dl); break;                 // L of this site
+      case 1: x = tc_pack_bytes(64, Dr, Wr * Dr); break;                  // R of this site
+      case 2: x = tc_pack_bytes(64, d * Dr, Dl); break;                   // x of the site solve
+      case 3: x = tc_pack_bytes(64, Dr, Dr); break;                       // x of the bond solve
+      case 4: x = tc_pack_bytes(128, Dl * d, Wr * Dr); break;             // T2 of the site solve
+      case 5: x = tc_pack_bytes(128, Dr, Wr * Dr); break;                 // T of the bond solve
+    }
+    b = std::max(b, x);
+  }
+  (void)rows_tile;
+  return b;
+}
+
+int memset_tc(tdvp_ctx* ctx, const Views& v, int field, long long bytes) {
+  for (int r = v.r0; r < v.r0 + v.R; ++r) {
+    const WorkDev& W = ctx->h_work[r];
+    void* p = field == 0 ? (void*)W.tc_l : field == 1 ? (void*)W.tc_r : field == 2 ? (void*)W.tc_x : (void*)W.tc_t2;
+    CK(cudaMemsetAsync(p, 0, (size_t)bytes, ctx->st));
+  }
+  return TDVP_OK;
+}
+
+int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int split) {
+  if (ctx->l_site != lsite || ctx->l_split != split) {
+    int rc = memset_tc(ctx, v, 0, used_bytes(ctx, v, 128, 0, lsite));
+    if (rc) return rc;
+    const Dims m = maxdims(ctx, lsite, v);
+    LAUNCH(launch_pack_env(0, lsite, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[lsite] * m.Dl * m.Dl, split, ctx->st));
+    ctx->l_site = lsite;
+    ctx->l_split = split;
+  }
+  if (ctx->r_site != rsite || ctx->r_split != split) {
+    int rc = memset_tc(ctx, v, 1, used_bytes(ctx, v, 64, 1, rsite));
+    if (rc) return rc;
+    const Dims m = maxdims(ctx, rsite, v);
+    LAUNCH(launch_pack_env(1, rsite, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[rsite + 1] * m.Dr * m.Dr, split, ctx->st));
+    ctx->r_site = rsite;
+    ctx->r_split = split;
+  }
+  return TDVP_OK;
+}
+
+// clear the per-solve tensor-core operands (their geometry changes from solve to solve)
+int prepare_tc_solve(tdvp_ctx* ctx, const Views& v, int kind, int site, int split) {
+  int rc;
+  if (kind == 0) {
+    if ((rc = ensure_env_packs(ctx, v, site, site, split))) return rc;
+    if ((rc = memset_tc(ctx, v, 2, used_bytes(ctx, v, 64, 2, site)))) return rc;
+    return memset_tc(ctx, v, 3, used_bytes(ctx, v, 128, 4, site));
+  }
+  if ((rc = ensure_env_packs(ctx, v, site + 1, site, split))) return rc;
+  if ((rc = memset_tc(ctx, v, 2, used_bytes(ctx, v, 64, 3, site)))) return rc;
+  return memset_tc(ctx, v, 3, used_bytes(ctx, v, 128, 5, site));
+}
+
+int matvec_site_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
+  const Dims m = maxdims(ctx, i, v);
+  const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
+  LAUNCH(launch_pack_x(0, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dl * d * m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_tc(i, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wr * d, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV3, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, split, ctx->st));
+  if (ctx->prof) {
+    double f = 0;
+    for (int r = v.r0; r < v.r0 + v.R; ++r) {
+      const auto& bd = ctx->rh[r].bd;
+      const double Dl = bd[i], Dr = bd[i + 1];
+      f += 8.0 * (Wl * Dl * d * Dr * Dl + Dl * d * Dr * Wr * Dr);
+    }
+    ctx->stats.prof_flops[TDVP_CAT_TC] += f;
+  }
+  return TDVP_OK;
+}
+
+int matvec_bond_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
+  const Dims m = maxdims(ctx, i, v);
+  const int Wb = ctx->Wb[i + 1];
+  LAUNCH(launch_pack_x(1, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dr * m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z1, i, v.sd, v.wk, v.R, ctx->N, Wb * m.Dr, m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, m.Dr, split, ctx->st));
+  if (ctx->prof) {
+    double f = 0;
+    for (int r = v.r0; r < v.r0 + v.R; ++r) {
+      const double Db = ctx->rh[r].bd[i + 1];
+      f += 8.0 * 2.0 * Wb * Db * Db * Db;
+    }
+    ctx->stats.prof_flops[TDVP_CAT_TC] += f;
+  }
+  return TDVP_OK;
+}
+
 int env_left(tdvp_ctx* ctx, const Views& v, int i) {
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
+  if (ctx->l_site == i + 1) ctx->l_site = -1;
   if ((rc = g_op(ctx, v, OP_EL1, i, m.Dl, d * m.Dr, Wl))) return rc;
   LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply(0, i, 0, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wr * d, ctx->st));
   return g_op(ctx, v, OP_EL3, i, m.Dr, m.Dr, Wr);
@@ -555,6 +660,7 @@ int env_right(tdvp_ctx* ctx, const Views& v, int i) {
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
+  if (ctx->r_site == i - 1) ctx->r_site = -1;
   if ((rc = g_op(ctx, v, OP_ER1, i, m.Dl * d, m.Dr, Wr))) return rc;
   LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply(1, i, 0, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wl * d, ctx->st));
   return g_op(ctx, v, OP_ER3, i, m.Dl, m.Dl, Wl);
@@ -573,10 +679,10 @@ int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
   const int d = ctx->d[i];
   if (dir == 0) {
     LAUNCHC(TDVP_CAT_QR, launch_transpose_site(1, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, ctx->st));
-    LAUNCHC(TDVP_CAT_QR, launch_row_qr(0, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, m.Dl * d), kRankRtol, 0, 0, ctx->st));
+    LAUNCHC(TDVP_CAT_QR, launch_row_qr(0, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, m.Dl * d), ctx->rank_rtol, 0, 0, ctx->st));
     LAUNCHC(TDVP_CAT_QR, launch_transpose_site(0, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, ctx->st));
   } else {
-    LAUNCHC(TDVP_CAT_QR, launch_row_qr(1, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, d * m.Dr), kRankRtol, 0, 0, ctx->st));
+    LAUNCHC(TDVP_CAT_QR, launch_row_qr(1, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, d * m.Dr), ctx->rank_rtol, 0, 0, ctx->st));
   }
   return TDVP_OK;
 }
@@ -590,7 +696,7 @@ int nblk_for(long long n) {
 // H = H[site] (kind 0) or the zero-site H0 of bond (site, site+1) (kind 1); the result goes to
 // `dst` (1 = site tensor, 2 = bond, 3 = w).  Returns TDVP_OK or an error; sets *notconv.
 int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
-         int* notconv) {
+         int* notconv, int prec = TDVP_PREC_FP64) {
   const Dims m = maxdims(ctx, site, v);
   const long long n = kind == 0 ? (long long)m.Dl * ctx->d[site] * m.Dr : (long long)m.Dr * m.Dr;
   LzArgs a;
@@ -601,13 +707,24 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
   const int guess = kh > 0 ? kh : 6;
   a.jcheck = ctx->check_every ? 1 : std::max(1, guess - 2);
   CK(cudaMemsetAsync(v.flags, 0, sizeof(int) * v.R, ctx->st));
+  const int split = prec == TDVP_PREC_TF32X3 ? 1 : 0;
+  if (prec != TDVP_PREC_FP64) {
+    int rc0 = prepare_tc_solve(ctx, v, kind, site, split);
+    if (rc0) return rc0;
+  }
   LAUNCHC(TDVP_CAT_LZVEC, launch_lz_start(a, ctx->st));
   int j = 0, batch = guess, rc;
   bool all_done = false;
   while (j < ctx->kmax && !all_done) {
     for (int q = 0; q < batch && j < ctx->kmax; ++q, ++j) {
-      if (kind == 0) { if ((rc = matvec_site(ctx, v, site, OP_MV1))) return rc; }
-      else if ((rc = matvec_bond(ctx, v, site))) return rc;
+      if (prec != TDVP_PREC_FP64) {
+        if (kind == 0) { if ((rc = matvec_site_tc(ctx, v, site, split))) return rc; }
+        else if ((rc = matvec_bond_tc(ctx, v, site, split))) return rc;
+      } else if (kind == 0) {
+        if ((rc = matvec_site(ctx, v, site, OP_MV1))) return rc;
+      } else if ((rc = matvec_bond(ctx, v, site))) {
+        return rc;
+      }
       LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));
       LAUNCHC(TDVP_CAT_TRIDIAG, launch_lz_iter_post(a, j, ctx->st));
       ctx->stats.matvecs += v.R;
@@ -700,7 +817,24 @@ int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
   if ((rc = dalloc(ctx, H.mps_allocs, &W.colsq, mmax))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.obs, ctx->n_el + 4))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.ks, 1))) return rc;
-  if ((rc = dalloc(ctx, H.mps_allocs, &W.bar, 2))) return rc;
+  {
+    long long bl = 1, br = 1, bx = 1, bt2 = 1, bt1 = 1;
+    for (int i = 0; i < N; ++i) {
+      const long long Dl = bd[i], Dr = bd[i + 1], d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
+      bl = std::max(bl, tc_pack_bytes(128, Wl * Dl, Dl));
+      br = std::max(br, tc_pack_bytes(64, Dr, Wr * Dr));
+      bx = std::max(bx, std::max(tc_pack_bytes(64, d * Dr, Dl), tc_pack_bytes(64, Dr, Dr)));
+      bt2 = std::max(bt2, std::max(tc_pack_bytes(128, Dl * d, Wr * Dr), tc_pack_bytes(128, Dr, Wr * Dr)));
+      bt1 = std::max(bt1, Wl * Dl * d * Dr);
+    }
+    if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_l, (size_t)bl))) return rc;
+    if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_r, (size_t)br))) return rc;
+    if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_x, (size_t)bx))) return rc;
+    if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_t2, (size_t)bt2))) return rc;
+    if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_t1, (size_t)(2 * bt1)))) return rc;
+    W.tc_t1_plane = bt1;
+  }
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.bar, 2 + 16))) return rc;   // root, generation, group counters
   W.err = ctx->d_err + r;
   // boundary environments are the scalar 1
   const zc one = zmake(1.0, 0.0);
@@ -761,6 +895,7 @@ int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site) {
                        ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
   }
+  ctx->l_site = ctx->r_site = -1;
   if ((rc = build_right_envs(ctx, one_view(ctx, r)))) return rc;
   CK(cudaStreamSynchronize(ctx->st));
   ctx->rh[r].mps = true;
@@ -806,6 +941,7 @@ int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const doub
     LAUNCH(launch_lz_start(a, ctx->st));
     LAUNCH(launch_copy_vec(1, 0, v.sd, v.wk, 1, N, m.Dl * ctx->d[0] * m.Dr, ctx->st));
   }
+  ctx->l_site = ctx->r_site = -1;
   if ((rc = build_right_envs(ctx, v))) return rc;
   CK(cudaStreamSynchronize(ctx->st));
   ctx->rh[r].mps = true;
@@ -815,7 +951,8 @@ int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const doub
 int tdvp_ps_step(tdvp_ctx* ctx, double dt_fs, int n_steps, int precision, int krylov_mode, double krylov_tol) {
   if (!ctx) return TDVP_ERR_INVALID_ARG;
   if (n_steps < 0 || !(krylov_tol >= 0) || !std::isfinite(dt_fs)) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: bad args");
-  if (precision != TDVP_PREC_FP64) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported precision");
+  if (precision != TDVP_PREC_FP64 && precision != TDVP_PREC_TF32 && precision != TDVP_PREC_TF32X3)
+    return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported precision");
   if (krylov_mode != TDVP_KRYLOV_ADAPTIVE) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported krylov mode");
   if (!all_ready(ctx)) return fail(ctx, TDVP_ERR_STATE, "ps_step: every realisation needs build_mpo and init");
   CK(cudaSetDevice(ctx->dev));
@@ -823,26 +960,28 @@ int tdvp_ps_step(tdvp_ctx* ctx, double dt_fs, int n_steps, int precision, int kr
   const int N = ctx->N;
   const double tau = dt_fs * kPhasePerCmFs;
   int rc, nc = 0;
+  const int P = precision;
   for (int step = 0; step < n_steps; ++step) {
+    ctx->l_site = ctx->r_site = -1;
     if (N == 1) {
-      if ((rc = expm(ctx, v, 0, 0, 1, 1, -tau, krylov_tol, &nc))) return rc;
+      if ((rc = expm(ctx, v, 0, 0, 1, 1, -tau, krylov_tol, &nc, P))) return rc;
     } else {
       for (int i = 0; i < N - 1; ++i) {
-        if ((rc = expm(ctx, v, 0, i, i == 0 ? 1 : 0, 1, -0.5 * tau, krylov_tol, &nc))) return rc;
+        if ((rc = expm(ctx, v, 0, i, i == 0 ? 1 : 0, 1, -0.5 * tau, krylov_tol, &nc, P))) return rc;
         if ((rc = gauge_qr(ctx, v, i, 0))) return rc;
         if ((rc = env_left(ctx, v, i))) return rc;
-        if ((rc = expm(ctx, v, 1, i, 2, 2, 0.5 * tau, krylov_tol, &nc))) return rc;
+        if ((rc = expm(ctx, v, 1, i, 2, 2, 0.5 * tau, krylov_tol, &nc, P))) return rc;
         const Dims m = maxdims(ctx, i + 1, v);
         if ((rc = g_op(ctx, v, OP_ABS_L, i, m.Dl, ctx->d[i + 1] * m.Dr, 1))) return rc;
       }
-      if ((rc = expm(ctx, v, 0, N - 1, 0, 1, -tau, krylov_tol, &nc))) return rc;
+      if ((rc = expm(ctx, v, 0, N - 1, 0, 1, -tau, krylov_tol, &nc, P))) return rc;
       for (int i = N - 1; i >= 1; --i) {
         if ((rc = gauge_qr(ctx, v, i, 1))) return rc;
         if ((rc = env_right(ctx, v, i))) return rc;
-        if ((rc = expm(ctx, v, 1, i - 1, 2, 2, 0.5 * tau, krylov_tol, &nc))) return rc;
+        if ((rc = expm(ctx, v, 1, i - 1, 2, 2, 0.5 * tau, krylov_tol, &nc, P))) return rc;
         const Dims m = maxdims(ctx, i - 1, v);
         if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
-        if ((rc = expm(ctx, v, 0, i - 1, 0, 1, -0.5 * tau, krylov_tol, &nc))) return rc;
+        if ((rc = expm(ctx, v, 0, i - 1, 0, 1, -0.5 * tau, krylov_tol, &nc, P))) return rc;
       }
     }
     ctx->stats.steps++;
@@ -941,9 +1080,10 @@ int tdvp_center_to_zero(tdvp_ctx* ctx, int r) {
   return check_device_errors(ctx);
 }
 
-int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, const double* x, double* y) {
+int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, int precision, const double* x, double* y) {
   if (!ctx || r < 0 || r >= ctx->R || !x || !y) return TDVP_ERR_INVALID_ARG;
   if (!ctx->rh[r].mps || i < 0 || i >= ctx->N) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_heff: bad site");
+  if (precision < TDVP_PREC_FP64 || precision > TDVP_PREC_TF32X3) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_heff: precision");
   CK(cudaSetDevice(ctx->dev));
   const Views v = one_view(ctx, r);
   const SiteDev& S = ctx->h_sites[(size_t)r * ctx->N + i];
@@ -951,10 +1091,39 @@ int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, const double* x, double* y) {
   CK(cudaMemcpyAsync(ctx->h_work[r].x, x, n * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
   LAUNCH(launch_reset_ks(v.wk, 1, ctx->st));
   int rc;
-  if ((rc = matvec_site(ctx, v, i, OP_MV1))) return rc;
+  if (precision == TDVP_PREC_FP64) {
+    if ((rc = matvec_site(ctx, v, i, OP_MV1))) return rc;
+  } else {
+    ctx->l_site = ctx->r_site = -1;
+    if ((rc = prepare_tc_solve(ctx, v, 0, i, precision == TDVP_PREC_TF32X3))) return rc;
+    if ((rc = matvec_site_tc(ctx, v, i, precision == TDVP_PREC_TF32X3))) return rc;
+  }
   CK(cudaMemcpyAsync(y, ctx->h_work[r].w, n * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
-  return TDVP_OK;
+  return check_device_errors(ctx);
+}
+
+int tdvp_apply_h0(tdvp_ctx* ctx, int r, int i, int precision, const double* x, double* y) {
+  if (!ctx || r < 0 || r >= ctx->R || !x || !y) return TDVP_ERR_INVALID_ARG;
+  if (!ctx->rh[r].mps || i < 0 || i >= ctx->N - 1) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_h0: bad bond");
+  if (precision < TDVP_PREC_FP64 || precision > TDVP_PREC_TF32X3) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_h0: precision");
+  CK(cudaSetDevice(ctx->dev));
+  const Views v = one_view(ctx, r);
+  const int Db = ctx->rh[r].bd[i + 1];
+  const size_t n = (size_t)Db * Db;
+  CK(cudaMemcpyAsync(ctx->h_work[r].x, x, n * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
+  LAUNCH(launch_reset_ks(v.wk, 1, ctx->st));
+  int rc;
+  if (precision == TDVP_PREC_FP64) {
+    if ((rc = matvec_bond(ctx, v, i))) return rc;
+  } else {
+    ctx->l_site = ctx->r_site = -1;
+    if ((rc = prepare_tc_solve(ctx, v, 1, i, precision == TDVP_PREC_TF32X3))) return rc;
+    if ((rc = matvec_bond_tc(ctx, v, i, precision == TDVP_PREC_TF32X3))) return rc;
+  }
+  CK(cudaMemcpyAsync(y, ctx->h_work[r].w, n * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return check_device_errors(ctx);
 }
 
 int tdvp_debug_qr(tdvp_ctx* ctx, int m, int n, const double* C, double* Q, double* Rout) {
@@ -976,7 +1145,7 @@ int tdvp_debug_qr(tdvp_ctx* ctx, int m, int n, const double* C, double* Q, doubl
     for (int b = 0; b < n; ++b) X[(size_t)b * m + a] = zmake(C[2 * ((size_t)a * n + b)], C[2 * ((size_t)a * n + b) + 1]);
   const Views v = one_view(ctx, 0);
   CK(cudaMemcpyAsync(ctx->h_work[0].scratch, X.data(), X.size() * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
-  LAUNCH(launch_row_qr(2, 0, v.sd, v.wk, 1, ctx->N, qr_blocks(ctx, 1, m), kRankRtol, n, m, ctx->st));
+  LAUNCH(launch_row_qr(2, 0, v.sd, v.wk, 1, ctx->N, qr_blocks(ctx, 1, m), ctx->rank_rtol, n, m, ctx->st));
   std::vector<zc> R((size_t)n * n);
   CK(cudaMemcpyAsync(X.data(), ctx->h_work[0].scratch, X.size() * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(R.data(), ctx->h_work[0].bond, R.size() * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
@@ -1018,6 +1187,20 @@ int tdvp_stats(tdvp_ctx* ctx, tdvp_stats_t* out) {
 
 void tdvp_reset_stats(tdvp_ctx* ctx) {
   if (ctx) ctx->stats = tdvp_stats_t{};
+}
+
+int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
+  if (!ctx) return TDVP_ERR_INVALID_ARG;
+  switch (option) {
+    case TDVP_OPT_RANK_RTOL:
+      if (!(value > 0.0 && value < 1.0)) return fail(ctx, TDVP_ERR_INVALID_ARG, "rank rtol must be in (0, 1)");
+      ctx->rank_rtol = value;
+      return TDVP_OK;
+    case TDVP_OPT_KRYLOV_CHECK_ALL:
+      ctx->check_every = value != 0.0 ? 1 : 0;
+      return TDVP_OK;
+  }
+  return fail(ctx, TDVP_ERR_INVALID_ARG, "unknown option");
 }
 
 int tdvp_set_profiling(tdvp_ctx* ctx, int on) {

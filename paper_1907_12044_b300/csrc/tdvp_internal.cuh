@@ -104,6 +104,13 @@ struct WorkDev {
   double* colsq;// QR column norms [d*Dmax]
   double* obs;  // observables: [n_el] <n>, then <Psi|Psi>, energy numerator
   KState* ks;
+  // tensor-core operands (packed tiles, see kernels_tc.cu)
+  char* tc_l;   // A operand: left environment stacked [(w l')][l]
+  char* tc_r;   // B operand: right environment [r'][(w r)]
+  char* tc_x;   // B operand: the Lanczos vector
+  char* tc_t2;  // A operand of the third stage
+  float* tc_t1; // first-stage output, planar FP32 (re plane, then im plane)
+  long long tc_t1_plane;
   unsigned* bar;// [0]=count, [1]=generation of the QR group barrier
   int* err;     // device-side error flag of this realisation
 };
@@ -124,6 +131,9 @@ enum GemmOp {
   OP_TR3,       // E' = A^H T1
   OP_HX1,       // T1[w] = L_w A  with x = site tensor (energy: H_eff C)
 };
+
+// Tensor-core GEMMs of the mixed-precision matvecs.
+enum TcOp { TC_MV1 = 0, TC_MV3 = 1, TC_Z1 = 2, TC_Z3 = 3 };
 
 struct GemmDesc {
   const zc* A;
@@ -184,3 +194,15 @@ cudaError_t launch_obs_energy(int slot, const SiteDev* sd, const WorkDev* wk, in
 cudaError_t launch_copy_vec(int what, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
                             int maxn, cudaStream_t st);
 cudaError_t launch_reset_ks(const WorkDev* wk, int R, cudaStream_t st);
+
+// Tensor-core path (kernels_tc.cu)
+long long tc_pack_bytes(int rows_tile, long long rows, long long K);
+cudaError_t tc_setup();
+cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
+                           int maxN, int split, cudaStream_t st);
+cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                            long long max_elems, int split, cudaStream_t st);
+cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                          long long max_elems, int split, cudaStream_t st);
+cudaError_t launch_wapply_tc(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int max_xy,
+                             int n_rows, int split, cudaStream_t st);

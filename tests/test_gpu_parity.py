@@ -229,3 +229,19 @@ def test_errors_are_reported_not_crashing():
     with pytest.raises(pkg.TDVPError) as e:
         eng.step(10.0, precision=99)
     assert e.value.code == -1
+
+
+def test_rank_threshold_option_matches_oracle():
+    """The gauge-shift rank threshold is an option; both sides take the same decisions at 1e-6."""
+    p = wl.tiny_chain()
+    eng = pkg.Engine()
+    eng.set_option(pkg.OPT_RANK_RTOL, 1e-6)
+    eng.build_mpo(0, p)
+    eng.init_mps(0, 16, p.exciton_site)
+    st = TDVPState.start(p, D=16)
+    for _ in range(10):
+        eng.step(10.0)
+        tdvp_ps_step(st, 10.0, rank_rtol=1e-6)
+        assert rel_pop_err(eng.observables(0)[0], populations(st, p)) <= POP_TOL
+    with pytest.raises(pkg.TDVPError):
+        eng.set_option(pkg.OPT_RANK_RTOL, 2.0)
