@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-prof", action="store_true", help="time without per-launch events")
+    ap.add_argument("--batched", type=int, default=32,
+                    help="also time R disorder realisations with ragged bond dims in the same launches (0: skip)")
     return ap.parse_args()
 
 
@@ -234,6 +236,42 @@ def run_ours(args, rank, world):
     return out, p
 
 
+def run_batched(args, R):
+    """R static-disorder realisations of the FMO-sized chain with bond dims drawn from
+    {32,48,64,96,128}, advanced together; total site updates per second."""
+    import torch
+    import workloads as wl
+    import paper_1907_12044_b300 as pkg
+    base = wl.fmo_sized()
+    Ds = wl.ragged_bond_dims(R)
+    eng = pkg.Engine(n_realisations=R)
+    eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
+    for r in range(R):
+        q = wl.disorder_realisation(base, r)
+        eng.build_mpo(r, q)
+        eng.init_mps(r, Ds[r], q.exciton_site)
+    eng.autotune()
+    for _ in range(args.warmup):
+        eng.step(args.dt, 1, precision=PREC[args.precision], tol=args.tol)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    eng.reset_stats()
+    e0.record(stream)
+    eng.step(args.dt, args.steps, precision=PREC[args.precision], tol=args.tol)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = eng.stats()
+    eng.close()
+    N = len(base.chain())
+    return {"realisations": R, "bond_dims": "ragged from {32,48,64,96,128} (seed 12044)",
+            "precision": args.precision, "value": (2 * N - 1) * R * args.steps / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms / args.steps, "gpu_launches": int(st["kernel_launches"]),
+            "qr_blocks": "autotuned"}
+
+
 def run_e2e(args, p):
     """Whole job through the public API from host buffers: parameters and the initial state go
     host->device, every step's populations come back device->host."""
@@ -306,6 +344,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     out, p = run_ours(args, rank, world)
     if rank == 0:
+        if args.batched > 0:
+            out["batched"] = run_batched(args, args.batched)
         if not args.no_e2e:
             out["e2e"] = run_e2e(args, p)
         if not args.no_cpu_baseline and world == 1:

@@ -218,6 +218,12 @@ void tdvp_reset_stats(tdvp_ctx* ctx);
  * Returns TDVP_ERR_DEVICE_TIMEOUT if a bounded device-side wait gave up. */
 int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* cuda_stream);
 
+/* Autotuner: for every distinct gauge-shift QR shape of the chain, time the QR kernel with
+ * several block counts per realisation on random full-rank matrices placed in the QR scratch
+ * (the state is not touched) and keep the fastest for the following steps.  Requires every
+ * realisation to be initialised; synchronises the stream. */
+int tdvp_autotune(tdvp_ctx* ctx);
+
 /* Options of a context (take effect from the next call):
  *   TDVP_OPT_RANK_RTOL: relative rank threshold of the gauge-shift QR (default 1e-13); a column
  *     whose residual after two Gram-Schmidt passes is <= value * ||C||_F is replaced by the

@@ -24,7 +24,7 @@ EXPORTED_SYMBOLS = [
     "tdvp_observables", "tdvp_chain_info", "tdvp_get_site", "tdvp_move_center",
     "tdvp_center_to_zero", "tdvp_apply_heff", "tdvp_debug_qr", "tdvp_debug_expm", "tdvp_stats",
     "tdvp_reset_stats", "tdvp_last_error", "tdvp_destroy", "tdvp_set_profiling",
-    "tdvp_lq_noalloc", "tdvp_apply_h0", "tdvp_set_option",
+    "tdvp_lq_noalloc", "tdvp_apply_h0", "tdvp_set_option", "tdvp_autotune",
 ]
 
 
@@ -93,6 +93,7 @@ def load_library():
     lib.tdvp_stats.argtypes = [P, C.POINTER(StatsC)]
     lib.tdvp_set_profiling.argtypes = [P, C.c_int]
     lib.tdvp_set_option.argtypes = [P, C.c_int, C.c_double]
+    lib.tdvp_autotune.argtypes = [P]
     lib.tdvp_lq_noalloc.argtypes = [C.c_int, C.c_int, P, P, P, P]
     lib.tdvp_reset_stats.argtypes = [P]
     lib.tdvp_reset_stats.restype = None
@@ -249,6 +250,9 @@ class Engine:
             v = getattr(s, k)
             out[k] = {c: v[i] for i, c in enumerate(CATEGORIES)} if k.startswith("prof_") else v
         return out
+
+    def autotune(self):
+        self._check(self.lib.tdvp_autotune(self._h))
 
     def set_option(self, option, value):
         self._check(self.lib.tdvp_set_option(self._h, int(option), float(value)))

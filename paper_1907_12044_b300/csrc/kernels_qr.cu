@@ -53,6 +53,9 @@ __device__ QrJob qr_job(int dir, int site, const SiteDev* sdr, const WorkDev& W,
   } else if (dir == 1) {
     const SiteDev& s = sdr[site];
     J.X = s.A; J.n = s.Dl; J.m = s.d * s.Dr; J.Rout = W.bond; J.rtrans = 0;
+  } else if (dir == 3) {          // right-to-left shape on the scratch buffer (autotuning)
+    const SiteDev& s = sdr[site];
+    J.X = W.scratch; J.n = s.Dl; J.m = s.d * s.Dr; J.Rout = W.bond; J.rtrans = 0;
   } else {
     J.X = W.scratch; J.n = dn; J.m = dm; J.Rout = W.bond; J.rtrans = 1;
   }

@@ -7,6 +7,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <random>
+#include <tuple>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -50,6 +53,7 @@ struct tdvp_ctx {
   std::vector<long long> ws_cap;   // elements of T1 (= T2) per realisation
   int qr_cap = 0;
   double rank_rtol = kRankRtolDefault;
+  std::map<std::tuple<int, int, int>, int> qr_tuned;   // (R, m, n) -> blocks per realisation
   int check_every = 0;        // 1: test Lanczos convergence at every k (else from the last k - 2 on)
   // per-launch timing
   int l_site = -1, r_site = -1;     // site whose environment is packed in tc_l / tc_r
@@ -547,39 +551,35 @@ int matvec_bond(tdvp_ctx* ctx, const Views& v, int i) {
 }
 
 // ---- mixed-precision matvecs on the tensor cores ----
-long long used_bytes(tdvp_ctx* ctx, const Views& v, int rows_tile, int which, int site) {
-  long long b = 0;
-  for (int r = v.r0; r < v.r0 + v.R; ++r) {
-    const auto& bd = ctx->rh[r].bd;
-    const long long Dl = bd[site], Dr = bd[site + 1], d = ctx->d[site];
-    const long long Wl = ctx->Wb[site], Wr = ctx->Wb[site + 1];
-    long long x = 0;
-    switch (which) {
-      case 0: x = tc_pack_bytes(128, Wl * Dl, Dl); break;                 // L of this site
-      case 1: x = tc_pack_bytes(64, Dr, Wr * Dr); break;                  // R of this site
-      case 2: x = tc_pack_bytes(64, d * Dr, Dl); break;                   // x of the site solve
-      case 3: x = tc_pack_bytes(64, Dr, Dr); break;                       // x of the bond solve
-      case 4: x = tc_pack_bytes(128, Dl * d, Wr * Dr); break;             // T2 of the site solve
-      case 5: x = tc_pack_bytes(128, Dr, Wr * Dr); break;                 // T of the bond solve
-    }
-    b = std::max(b, x);
+// bytes of one packed tensor-core operand of realisation r (which: 0 L, 1 R, 2 x of a site
+// solve, 3 x of a bond solve, 4 T2 of a site solve, 5 T of a bond solve)
+long long used_bytes(tdvp_ctx* ctx, int r, int which, int site) {
+  const auto& bd = ctx->rh[r].bd;
+  const long long Dl = bd[site], Dr = bd[site + 1], d = ctx->d[site];
+  const long long Wl = ctx->Wb[site], Wr = ctx->Wb[site + 1];
+  switch (which) {
+    case 0: return tc_pack_bytes(128, Wl * Dl, Dl);
+    case 1: return tc_pack_bytes(64, Dr, Wr * Dr);
+    case 2: return tc_pack_bytes(64, d * Dr, Dl);
+    case 3: return tc_pack_bytes(64, Dr, Dr);
+    case 4: return tc_pack_bytes(128, Dl * d, Wr * Dr);
+    default: return tc_pack_bytes(128, Dr, Wr * Dr);
   }
-  (void)rows_tile;
-  return b;
 }
 
-int memset_tc(tdvp_ctx* ctx, const Views& v, int field, long long bytes) {
+// zero the used part of one tensor-core operand buffer in every realisation of the view
+int memset_tc(tdvp_ctx* ctx, const Views& v, int field, int which, int site) {
   for (int r = v.r0; r < v.r0 + v.R; ++r) {
     const WorkDev& W = ctx->h_work[r];
     void* p = field == 0 ? (void*)W.tc_l : field == 1 ? (void*)W.tc_r : field == 2 ? (void*)W.tc_x : (void*)W.tc_t2;
-    CK(cudaMemsetAsync(p, 0, (size_t)bytes, ctx->st));
+    CK(cudaMemsetAsync(p, 0, (size_t)used_bytes(ctx, r, which, site), ctx->st));
   }
   return TDVP_OK;
 }
 
 int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int split) {
   if (ctx->l_site != lsite || ctx->l_split != split) {
-    int rc = memset_tc(ctx, v, 0, used_bytes(ctx, v, 128, 0, lsite));
+    int rc = memset_tc(ctx, v, 0, 0, lsite);
     if (rc) return rc;
     const Dims m = maxdims(ctx, lsite, v);
     LAUNCH(launch_pack_env(0, lsite, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[lsite] * m.Dl * m.Dl, split, ctx->st));
@@ -587,7 +587,7 @@ int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int sp
     ctx->l_split = split;
   }
   if (ctx->r_site != rsite || ctx->r_split != split) {
-    int rc = memset_tc(ctx, v, 1, used_bytes(ctx, v, 64, 1, rsite));
+    int rc = memset_tc(ctx, v, 1, 1, rsite);
     if (rc) return rc;
     const Dims m = maxdims(ctx, rsite, v);
     LAUNCH(launch_pack_env(1, rsite, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[rsite + 1] * m.Dr * m.Dr, split, ctx->st));
@@ -602,12 +602,12 @@ int prepare_tc_solve(tdvp_ctx* ctx, const Views& v, int kind, int site, int spli
   int rc;
   if (kind == 0) {
     if ((rc = ensure_env_packs(ctx, v, site, site, split))) return rc;
-    if ((rc = memset_tc(ctx, v, 2, used_bytes(ctx, v, 64, 2, site)))) return rc;
-    return memset_tc(ctx, v, 3, used_bytes(ctx, v, 128, 4, site));
+    if ((rc = memset_tc(ctx, v, 2, 2, site))) return rc;
+    return memset_tc(ctx, v, 3, 4, site);
   }
   if ((rc = ensure_env_packs(ctx, v, site + 1, site, split))) return rc;
-  if ((rc = memset_tc(ctx, v, 2, used_bytes(ctx, v, 64, 3, site)))) return rc;
-  return memset_tc(ctx, v, 3, used_bytes(ctx, v, 128, 5, site));
+  if ((rc = memset_tc(ctx, v, 2, 3, site))) return rc;
+  return memset_tc(ctx, v, 3, 5, site);
 }
 
 int matvec_site_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
@@ -666,7 +666,9 @@ int env_right(tdvp_ctx* ctx, const Views& v, int i) {
   return g_op(ctx, v, OP_ER3, i, m.Dl, m.Dl, Wl);
 }
 
-int qr_blocks(tdvp_ctx* ctx, int R, int m) {
+int qr_blocks(tdvp_ctx* ctx, int R, int m, int n = 0) {
+  auto it = ctx->qr_tuned.find(std::make_tuple(R, m, n));
+  if (it != ctx->qr_tuned.end()) return it->second;
   int B = cdivi(m, 8);
   B = std::max(1, std::min(B, 148));
   B = std::min(B, std::max(1, ctx->qr_cap / std::max(1, R)));
@@ -679,10 +681,10 @@ int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
   const int d = ctx->d[i];
   if (dir == 0) {
     LAUNCHC(TDVP_CAT_QR, launch_transpose_site(1, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, ctx->st));
-    LAUNCHC(TDVP_CAT_QR, launch_row_qr(0, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, m.Dl * d), ctx->rank_rtol, 0, 0, ctx->st));
+    LAUNCHC(TDVP_CAT_QR, launch_row_qr(0, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, m.Dl * d, m.Dr), ctx->rank_rtol, 0, 0, ctx->st));
     LAUNCHC(TDVP_CAT_QR, launch_transpose_site(0, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, ctx->st));
   } else {
-    LAUNCHC(TDVP_CAT_QR, launch_row_qr(1, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, d * m.Dr), ctx->rank_rtol, 0, 0, ctx->st));
+    LAUNCHC(TDVP_CAT_QR, launch_row_qr(1, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, d * m.Dr, m.Dl), ctx->rank_rtol, 0, 0, ctx->st));
   }
   return TDVP_OK;
 }
@@ -1145,7 +1147,7 @@ int tdvp_debug_qr(tdvp_ctx* ctx, int m, int n, const double* C, double* Q, doubl
     for (int b = 0; b < n; ++b) X[(size_t)b * m + a] = zmake(C[2 * ((size_t)a * n + b)], C[2 * ((size_t)a * n + b) + 1]);
   const Views v = one_view(ctx, 0);
   CK(cudaMemcpyAsync(ctx->h_work[0].scratch, X.data(), X.size() * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
-  LAUNCH(launch_row_qr(2, 0, v.sd, v.wk, 1, ctx->N, qr_blocks(ctx, 1, m), ctx->rank_rtol, n, m, ctx->st));
+  LAUNCH(launch_row_qr(2, 0, v.sd, v.wk, 1, ctx->N, qr_blocks(ctx, 1, m, n), ctx->rank_rtol, n, m, ctx->st));
   std::vector<zc> R((size_t)n * n);
   CK(cudaMemcpyAsync(X.data(), ctx->h_work[0].scratch, X.size() * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(R.data(), ctx->h_work[0].bond, R.size() * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
@@ -1187,6 +1189,60 @@ int tdvp_stats(tdvp_ctx* ctx, tdvp_stats_t* out) {
 
 void tdvp_reset_stats(tdvp_ctx* ctx) {
   if (ctx) ctx->stats = tdvp_stats_t{};
+}
+
+int tdvp_autotune(tdvp_ctx* ctx) {
+  if (!ctx) return TDVP_ERR_INVALID_ARG;
+  if (!all_ready(ctx)) return fail(ctx, TDVP_ERR_STATE, "autotune: every realisation needs build_mpo and init");
+  CK(cudaSetDevice(ctx->dev));
+  const Views v = all_views(ctx);
+  std::mt19937_64 rng(12044);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // every QR shape of the sweep, timed with each realisation's own site dims on random
+  // full-rank matrices in its QR scratch (the state is not touched)
+  for (int i = 0; i < ctx->N; ++i) {
+    for (int dir : {0, 3}) {
+      if ((dir == 0 && i == ctx->N - 1) || (dir == 3 && i == 0)) continue;
+      const Dims mx = maxdims(ctx, i, v);
+      const int mm = dir == 0 ? mx.Dl * ctx->d[i] : ctx->d[i] * mx.Dr;
+      const int nn = dir == 0 ? mx.Dr : mx.Dl;
+      const auto key = std::make_tuple(ctx->R, mm, nn);
+      if (ctx->qr_tuned.count(key) || nn > 256) continue;
+      std::vector<std::vector<zc>> X(ctx->R);
+      for (int r = 0; r < ctx->R; ++r) {
+        const auto& bd = ctx->rh[r].bd;
+        X[r].resize((size_t)bd[i] * ctx->d[i] * bd[i + 1]);
+        for (auto& z : X[r]) z = zmake(nd(rng), nd(rng));
+      }
+      int bestB = qr_blocks(ctx, ctx->R, mm, nn);
+      float best = 1e30f;
+      const int cands[] = {1, 2, 4, 8, 16, 24, 32, 48, 64, 80, 96, 128, 148};
+      for (int B : cands) {
+        if (B > mm || (long long)B * ctx->R > ctx->qr_cap) continue;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          for (int r = 0; r < ctx->R; ++r)
+            CK(cudaMemcpyAsync(ctx->h_work[r].scratch, X[r].data(), X[r].size() * sizeof(zc), cudaMemcpyHostToDevice,
+                               ctx->st));
+          CK(cudaEventRecord(e0, ctx->st));
+          CK(launch_row_qr(dir, i, v.sd, v.wk, v.R, ctx->N, B, 1e-13, 0, 0, ctx->st));
+          CK(cudaEventRecord(e1, ctx->st));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          tmin = std::min(tmin, ms);
+        }
+        if (tmin < best) { best = tmin; bestB = B; }
+      }
+      ctx->qr_tuned[key] = bestB;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return check_device_errors(ctx);
 }
 
 int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
