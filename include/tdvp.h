@@ -75,6 +75,9 @@ typedef struct {
 
 /* Krylov dimension control. */
 #define TDVP_KRYLOV_ADAPTIVE 0   /* grow k until the a-posteriori estimate meets the tolerance */
+#define TDVP_KRYLOV_LEARNED  1   /* the learned controller predicts k after the first Lanczos step;
+                                    convergence is tested from that k on, and the adaptive test
+                                    (the same estimate and tolerance) decides when to stop */
 
 /* Create a context on CUDA device `device` working on `cuda_stream`, holding
  * `n_realisations` independent trajectories (>= 1) that share one chain layout,
@@ -176,6 +179,7 @@ typedef struct {
   long long host_syncs;        /* stream synchronisations made inside tdvp_ps_step */
   long long kernel_launches;   /* kernels enqueued by this context */
   long long not_converged;     /* solves that stopped at kmax above tolerance */
+  long long tri_evals;         /* tridiagonal exponentials evaluated (convergence tests), all realisations */
   /* filled only while profiling is on: per category, summed CUDA-event time of each launch
    * (recorded on the context stream right before and after it), launch count, and the
    * algorithmic real flops of the contraction GEMMs (8 per complex multiply-add). */
@@ -217,6 +221,23 @@ void tdvp_reset_stats(tdvp_ctx* ctx);
  * GPU (other streams, other host threads) race and give wrong results; serialise them.
  * Returns TDVP_ERR_DEVICE_TIMEOUT if a bounded device-side wait gave up. */
 int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* cuda_stream);
+
+/* Learned Krylov controller (not in the paper): a two-layer MLP, 8 features -> 64 -> 64 -> 1, ReLU,
+ * FP32, MLP_NPARAM = 4801 floats laid out W1[8][64], b1[64], W2[64][64], b2[64], W3[64], b3.
+ * Features of a local exponential, known after its first Lanczos step: log10(1 + |tau| ||H v||),
+ * kind (site 0 / bond 1), previous k of the same site and kind / 32, site / (N-1),
+ * log2(vector length) / 20, log10|tau| / 4, -log10(tol) / 12, log10(1 + |tau| |alpha_0|).
+ * Its prediction only moves the first convergence test; the stopping rule is unchanged. */
+int tdvp_controller_set_weights(tdvp_ctx* ctx, const float* w, int n);   /* n = 4801, host array */
+int tdvp_controller_get_weights(tdvp_ctx* ctx, float* w, int n);
+/* Log every finished exponential (features, k) into a device buffer of `capacity` rows; 0 stops. */
+int tdvp_controller_logging(tdvp_ctx* ctx, long long capacity);
+/* Copy up to max_rows log rows (9 floats each) to the host; rows receives the logged count. */
+int tdvp_controller_log(tdvp_ctx* ctx, float* out, long long max_rows, long long* rows);
+/* Adam (beta 0.9/0.999) on the mean-squared error of k over the log, in mini-batches, on the GPU. */
+int tdvp_controller_train(tdvp_ctx* ctx, int epochs, int batch, float lr, float* final_loss);
+/* Loss and gradient of the current weights on B rows X[B][8], targets t[B] (host), for checking. */
+int tdvp_controller_loss_grad(tdvp_ctx* ctx, const float* X, const float* t, int B, float* loss, float* grad);
 
 /* Autotuner: for every distinct gauge-shift QR shape of the chain, time the QR kernel with
  * several block counts per realisation on random full-rank matrices placed in the QR scratch

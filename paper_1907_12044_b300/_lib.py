@@ -12,6 +12,8 @@ PREC_FP64 = 0
 PREC_TF32 = 1
 PREC_TF32X3 = 2
 KRYLOV_ADAPTIVE = 0
+KRYLOV_LEARNED = 1
+MLP_NPARAM = 4801
 
 ERRORS = {
     -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
@@ -25,6 +27,8 @@ EXPORTED_SYMBOLS = [
     "tdvp_center_to_zero", "tdvp_apply_heff", "tdvp_debug_qr", "tdvp_debug_expm", "tdvp_stats",
     "tdvp_reset_stats", "tdvp_last_error", "tdvp_destroy", "tdvp_set_profiling",
     "tdvp_lq_noalloc", "tdvp_apply_h0", "tdvp_set_option", "tdvp_autotune",
+    "tdvp_controller_set_weights", "tdvp_controller_get_weights", "tdvp_controller_logging",
+    "tdvp_controller_log", "tdvp_controller_train", "tdvp_controller_loss_grad",
 ]
 
 
@@ -53,6 +57,7 @@ class StatsC(C.Structure):
                 ("krylov_solves", C.c_longlong), ("krylov_dim_sum", C.c_longlong),
                 ("krylov_dim_max", C.c_int), ("host_syncs", C.c_longlong),
                 ("kernel_launches", C.c_longlong), ("not_converged", C.c_longlong),
+                ("tri_evals", C.c_longlong),
                 ("prof_ms", C.c_double * NCAT), ("prof_launches", C.c_longlong * NCAT),
                 ("prof_flops", C.c_double * NCAT)]
 
@@ -94,6 +99,13 @@ def load_library():
     lib.tdvp_set_profiling.argtypes = [P, C.c_int]
     lib.tdvp_set_option.argtypes = [P, C.c_int, C.c_double]
     lib.tdvp_autotune.argtypes = [P]
+    fp = C.POINTER(C.c_float)
+    lib.tdvp_controller_set_weights.argtypes = [P, fp, C.c_int]
+    lib.tdvp_controller_get_weights.argtypes = [P, fp, C.c_int]
+    lib.tdvp_controller_logging.argtypes = [P, C.c_longlong]
+    lib.tdvp_controller_log.argtypes = [P, fp, C.c_longlong, C.POINTER(C.c_longlong)]
+    lib.tdvp_controller_train.argtypes = [P, C.c_int, C.c_int, C.c_float, fp]
+    lib.tdvp_controller_loss_grad.argtypes = [P, fp, fp, C.c_int, fp, fp]
     lib.tdvp_lq_noalloc.argtypes = [C.c_int, C.c_int, P, P, P, P]
     lib.tdvp_reset_stats.argtypes = [P]
     lib.tdvp_reset_stats.restype = None
@@ -111,6 +123,10 @@ def _dptr(a):
 
 def _iptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
 
 
 class Engine:
@@ -250,6 +266,41 @@ class Engine:
             v = getattr(s, k)
             out[k] = {c: v[i] for i, c in enumerate(CATEGORIES)} if k.startswith("prof_") else v
         return out
+
+    # -- learned Krylov controller ------------------------------------------------------------
+    def controller_set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._check(self.lib.tdvp_controller_set_weights(self._h, _fptr(w), w.size))
+
+    def controller_get_weights(self):
+        w = np.zeros(MLP_NPARAM, np.float32)
+        self._check(self.lib.tdvp_controller_get_weights(self._h, _fptr(w), w.size))
+        return w
+
+    def controller_logging(self, capacity):
+        self._check(self.lib.tdvp_controller_logging(self._h, int(capacity)))
+
+    def controller_log(self, max_rows=1 << 22):
+        n = C.c_longlong()
+        self._check(self.lib.tdvp_controller_log(self._h, None, 0, C.byref(n)))
+        k = min(n.value, max_rows)
+        out = np.zeros((k, 9), np.float32)
+        if k:
+            self._check(self.lib.tdvp_controller_log(self._h, _fptr(out), k, C.byref(n)))
+        return out
+
+    def controller_train(self, epochs=20, batch=1024, lr=1e-3):
+        loss = C.c_float()
+        self._check(self.lib.tdvp_controller_train(self._h, int(epochs), int(batch), float(lr), C.byref(loss)))
+        return loss.value
+
+    def controller_loss_grad(self, X, t):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = C.c_float()
+        g = np.zeros(MLP_NPARAM, np.float32)
+        self._check(self.lib.tdvp_controller_loss_grad(self._h, _fptr(X), _fptr(t), X.shape[0], C.byref(loss), _fptr(g)))
+        return loss.value, g
 
     def autotune(self):
         self._check(self.lib.tdvp_autotune(self._h))

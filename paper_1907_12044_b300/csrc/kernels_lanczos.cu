@@ -375,10 +375,34 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
     return;
   }
   const bool last = (k >= ks->kcap) || beta == 0.0;
-  if (k < a.jcheck && !last) {
+  if (j == 0) {
+    // controller features, known after the first Lanczos step
+    if (threadIdx.x == 0) {
+      const double th = fabs(a.theta), a0 = ks->alpha[0];
+      const double hn = sqrt(a0 * a0 + beta * beta);
+      ks->feat[0] = (float)log10(1.0 + th * hn);
+      ks->feat[1] = (float)a.kind;
+      ks->feat[2] = (float)W.kprev[2 * a.site + a.kind] / 32.f;
+      ks->feat[3] = (float)a.site / (float)(a.N_sites > 1 ? a.N_sites - 1 : 1);
+      ks->feat[4] = (float)(log2((double)g.n) / 20.0);
+      ks->feat[5] = (float)(log10(th + 1e-30) / 4.0);
+      ks->feat[6] = (float)(-log10(a.tol + 1e-300) / 12.0);
+      ks->feat[7] = (float)log10(1.0 + th * fabs(a0));
+      ks->kpred = 0;
+    }
+    __syncthreads();
+    if (a.mlp) {
+      const float y = mlp_infer(ks->feat, a.mlp, reinterpret_cast<float*>(sh));
+      if (threadIdx.x == 0) ks->kpred = (int)fminf(fmaxf(floorf(y), 1.f), 126.f);
+      __syncthreads();
+    }
+  }
+  const int jcheck = a.mlp ? max(1, ks->kpred) : a.jcheck;
+  if (k < jcheck && !last) {
     if (threadIdx.x == 0) { ks->beta[j] = beta; ks->inv_beta = 1.0 / beta; }
     return;
   }
+  if (threadIdx.x == 0) (*W.tri_count)++;
   const bool ok = tridiag_expi(ks->alpha, ks->beta, k, a.theta, c, sh);
   if (!ok) {
     if (threadIdx.x == 0) { ks->status = -1; ks->done = 1; ks->k = 0; flags[r] = -1; }
@@ -394,6 +418,14 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
       ks->notconv = (!conv && beta > 0.0) ? 1 : 0;
       ks->done = 1;
       flags[r] = k | (ks->notconv << 16);
+      W.kprev[2 * a.site + a.kind] = k;
+      if (a.log) {
+        const unsigned slot = atomicAdd(a.log_count, 1u);
+        if ((long long)slot < a.log_cap) {
+          for (int q = 0; q < MLP_NIN; ++q) a.log[(long long)slot * (MLP_NIN + 1) + q] = ks->feat[q];
+          a.log[(long long)slot * (MLP_NIN + 1) + MLP_NIN] = (float)k;
+        }
+      }
     }
   } else if (threadIdx.x == 0) {
     ks->err = err;

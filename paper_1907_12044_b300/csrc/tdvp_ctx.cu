@@ -56,9 +56,20 @@ struct tdvp_ctx {
   std::map<std::tuple<int, int, int>, int> qr_tuned;   // (R, m, n) -> blocks per realisation
   int check_every = 0;        // 1: test Lanczos convergence at every k (else from the last k - 2 on)
   // per-launch timing
+  // learned Krylov controller
+  float* d_mlp = nullptr;           // weights (MLP_NPARAM)
+  float* d_mlp_m = nullptr;         // Adam moments
+  float* d_mlp_v = nullptr;
+  int mlp_ready = 0;
+  int mlp_step = 0;
+  float* d_log = nullptr;           // solve log [cap][MLP_NIN + 1]
+  unsigned* d_log_count = nullptr;
+  long long log_cap = 0;
+  int logging = 0;
   int l_site = -1, r_site = -1;     // site whose environment is packed in tc_l / tc_r
   int l_split = -1, r_split = -1;
   int prof = 0;
+  int krylov_mode = TDVP_KRYLOV_ADAPTIVE;
   std::vector<cudaEvent_t> ev;   // pairs
   std::vector<int> ev_cat;
   size_t ev_used = 0;
@@ -234,6 +245,11 @@ void tdvp_destroy(tdvp_ctx* ctx) {
   cudaFreeHost(ctx->h_flags);
   cudaFreeHost(ctx->h_err);
   cudaFreeHost(ctx->h_obs);
+  cudaFree(ctx->d_mlp);
+  cudaFree(ctx->d_mlp_m);
+  cudaFree(ctx->d_mlp_v);
+  cudaFree(ctx->d_log);
+  cudaFree(ctx->d_log_count);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
 }
@@ -705,6 +721,10 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
   a.sd = v.sd; a.wk = v.wk; a.R = v.R; a.N_sites = ctx->N; a.site = site; a.kind = kind;
   a.src = src; a.dst = dst; a.theta = theta; a.tol = tol; a.kmax = ctx->kmax;
   a.nblk = nblk_for(n); a.flags = v.flags;
+  a.mlp = (ctx->krylov_mode == TDVP_KRYLOV_LEARNED && ctx->mlp_ready) ? ctx->d_mlp : nullptr;
+  a.log = ctx->logging ? ctx->d_log : nullptr;
+  a.log_count = ctx->d_log_count;
+  a.log_cap = ctx->log_cap;
   int& kh = ctx->khist[2 * site + kind];
   const int guess = kh > 0 ? kh : 6;
   a.jcheck = ctx->check_every ? 1 : std::max(1, guess - 2);
@@ -766,6 +786,17 @@ int check_device_errors(tdvp_ctx* ctx) {
                   code == -5 ? "device barrier timed out"
                              : (code == -6 ? "gauge-shift QR met a non-positive Gram pivot" : "device kernel rejected its sizes"));
     }
+  return TDVP_OK;
+}
+
+int collect_tri_counts(tdvp_ctx* ctx) {
+  for (int r = 0; r < ctx->R; ++r) {
+    int cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, ctx->h_work[r].tri_count, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemsetAsync(ctx->h_work[r].tri_count, 0, sizeof(int), ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->stats.tri_evals += cnt;
+  }
   return TDVP_OK;
 }
 
@@ -837,6 +868,8 @@ int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
     W.tc_t1_plane = bt1;
   }
   if ((rc = dalloc(ctx, H.mps_allocs, &W.bar, 2 + 16))) return rc;   // root, generation, group counters
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.kprev, 2 * N))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.tri_count, 1))) return rc;
   W.err = ctx->d_err + r;
   // boundary environments are the scalar 1
   const zc one = zmake(1.0, 0.0);
@@ -955,7 +988,11 @@ int tdvp_ps_step(tdvp_ctx* ctx, double dt_fs, int n_steps, int precision, int kr
   if (n_steps < 0 || !(krylov_tol >= 0) || !std::isfinite(dt_fs)) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: bad args");
   if (precision != TDVP_PREC_FP64 && precision != TDVP_PREC_TF32 && precision != TDVP_PREC_TF32X3)
     return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported precision");
-  if (krylov_mode != TDVP_KRYLOV_ADAPTIVE) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported krylov mode");
+  if (krylov_mode != TDVP_KRYLOV_ADAPTIVE && krylov_mode != TDVP_KRYLOV_LEARNED)
+    return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported krylov mode");
+  if (krylov_mode == TDVP_KRYLOV_LEARNED && !ctx->mlp_ready)
+    return fail(ctx, TDVP_ERR_STATE, "ps_step: the learned controller has no weights");
+  ctx->krylov_mode = krylov_mode;
   if (!all_ready(ctx)) return fail(ctx, TDVP_ERR_STATE, "ps_step: every realisation needs build_mpo and init");
   CK(cudaSetDevice(ctx->dev));
   const Views v = all_views(ctx);
@@ -990,6 +1027,7 @@ int tdvp_ps_step(tdvp_ctx* ctx, double dt_fs, int n_steps, int precision, int kr
     ctx->stats.site_updates += (long long)(2 * N - 1) * ctx->R;
   }
   if ((rc = check_device_errors(ctx))) return rc;
+  if ((rc = collect_tri_counts(ctx))) return rc;
   if (ctx->prof && (rc = prof_collect(ctx))) return rc;
   if (nc) return fail(ctx, TDVP_ERR_KRYLOV_NOT_CONVERGED, "some Lanczos solve stopped at kmax above the tolerance");
   return TDVP_OK;
@@ -1189,6 +1227,139 @@ int tdvp_stats(tdvp_ctx* ctx, tdvp_stats_t* out) {
 
 void tdvp_reset_stats(tdvp_ctx* ctx) {
   if (ctx) ctx->stats = tdvp_stats_t{};
+}
+
+int tdvp_controller_set_weights(tdvp_ctx* ctx, const float* w, int n) {
+  if (!ctx || !w) return TDVP_ERR_INVALID_ARG;
+  if (n != MLP_NPARAM) return fail(ctx, TDVP_ERR_INVALID_ARG, "controller: wrong number of weights");
+  CK(cudaSetDevice(ctx->dev));
+  if (!ctx->d_mlp) {
+    CK(cudaMalloc(&ctx->d_mlp, sizeof(float) * MLP_NPARAM));
+    CK(cudaMalloc(&ctx->d_mlp_m, sizeof(float) * MLP_NPARAM));
+    CK(cudaMalloc(&ctx->d_mlp_v, sizeof(float) * MLP_NPARAM));
+  }
+  CK(cudaMemcpyAsync(ctx->d_mlp, w, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemsetAsync(ctx->d_mlp_m, 0, sizeof(float) * MLP_NPARAM, ctx->st));
+  CK(cudaMemsetAsync(ctx->d_mlp_v, 0, sizeof(float) * MLP_NPARAM, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->mlp_ready = 1;
+  ctx->mlp_step = 0;
+  return TDVP_OK;
+}
+
+int tdvp_controller_get_weights(tdvp_ctx* ctx, float* w, int n) {
+  if (!ctx || !w) return TDVP_ERR_INVALID_ARG;
+  if (n != MLP_NPARAM || !ctx->mlp_ready) return fail(ctx, TDVP_ERR_INVALID_ARG, "controller: no weights");
+  CK(cudaMemcpyAsync(w, ctx->d_mlp, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return TDVP_OK;
+}
+
+int tdvp_controller_logging(tdvp_ctx* ctx, long long capacity) {
+  if (!ctx || capacity < 0) return TDVP_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->dev));
+  if (capacity == 0) { ctx->logging = 0; return TDVP_OK; }
+  if (capacity != ctx->log_cap) {
+    cudaFree(ctx->d_log);
+    ctx->d_log = nullptr;
+    CK(cudaMalloc(&ctx->d_log, sizeof(float) * (MLP_NIN + 1) * capacity));
+    if (!ctx->d_log_count) CK(cudaMalloc(&ctx->d_log_count, sizeof(unsigned)));
+    ctx->log_cap = capacity;
+  }
+  CK(cudaMemsetAsync(ctx->d_log_count, 0, sizeof(unsigned), ctx->st));
+  ctx->logging = 1;
+  return TDVP_OK;
+}
+
+long long log_size(tdvp_ctx* ctx) {
+  unsigned cnt = 0;
+  if (!ctx->d_log_count) return 0;
+  if (cudaMemcpyAsync(&cnt, ctx->d_log_count, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->st) != cudaSuccess)
+    return -1;
+  return std::min<long long>(cnt, ctx->log_cap);
+}
+
+int tdvp_controller_log(tdvp_ctx* ctx, float* out, long long max_rows, long long* rows) {
+  if (!ctx || !rows) return TDVP_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->dev));
+  const long long n = log_size(ctx);
+  if (n < 0) return fail(ctx, TDVP_ERR_CUDA, "controller: reading the log size failed");
+  *rows = n;
+  if (out && max_rows > 0 && n > 0) {
+    CK(cudaMemcpyAsync(out, ctx->d_log, sizeof(float) * (MLP_NIN + 1) * std::min(n, max_rows), cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return TDVP_OK;
+}
+
+// mean-squared-error loss and gradient of the controller on B rows of `data` (device or host)
+int controller_grad(tdvp_ctx* ctx, const float* d_data, long long idx0, int B, float* d_grad, float* loss) {
+  float* partial = nullptr;
+  CK(cudaMalloc(&partial, sizeof(float) * mlp_partial_floats(B)));
+  cudaError_t e = launch_mlp_grad(d_data, idx0, B, ctx->d_mlp, partial, d_grad, ctx->st);
+  if (e == cudaSuccess && loss) {
+    e = cudaMemcpyAsync(loss, d_grad + MLP_NPARAM, sizeof(float), cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  }
+  cudaFree(partial);
+  if (e != cudaSuccess) return fail(ctx, TDVP_ERR_CUDA, std::string("controller gradient: ") + cudaGetErrorString(e));
+  return TDVP_OK;
+}
+
+int tdvp_controller_loss_grad(tdvp_ctx* ctx, const float* X, const float* t, int B, float* loss, float* grad) {
+  if (!ctx || !X || !t || B < 1 || !grad || !loss) return TDVP_ERR_INVALID_ARG;
+  if (!ctx->mlp_ready) return fail(ctx, TDVP_ERR_STATE, "controller: set weights first");
+  CK(cudaSetDevice(ctx->dev));
+  std::vector<float> rows((size_t)B * (MLP_NIN + 1));
+  for (int b = 0; b < B; ++b) {
+    for (int q = 0; q < MLP_NIN; ++q) rows[(size_t)b * (MLP_NIN + 1) + q] = X[(size_t)b * MLP_NIN + q];
+    rows[(size_t)b * (MLP_NIN + 1) + MLP_NIN] = t[b];
+  }
+  float *d_rows = nullptr, *d_grad = nullptr;
+  CK(cudaMalloc(&d_rows, sizeof(float) * rows.size()));
+  CK(cudaMalloc(&d_grad, sizeof(float) * (MLP_NPARAM + 1)));
+  int rc = TDVP_OK;
+  if (cudaMemcpyAsync(d_rows, rows.data(), sizeof(float) * rows.size(), cudaMemcpyHostToDevice, ctx->st) != cudaSuccess)
+    rc = fail(ctx, TDVP_ERR_CUDA, "controller: upload failed");
+  if (!rc) rc = controller_grad(ctx, d_rows, 0, B, d_grad, loss);
+  if (!rc && (cudaMemcpyAsync(grad, d_grad, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+              cudaStreamSynchronize(ctx->st) != cudaSuccess))
+    rc = fail(ctx, TDVP_ERR_CUDA, "controller: download failed");
+  cudaFree(d_rows);
+  cudaFree(d_grad);
+  return rc;
+}
+
+int tdvp_controller_train(tdvp_ctx* ctx, int epochs, int batch, float lr, float* final_loss) {
+  if (!ctx || epochs < 1 || batch < 1 || !(lr > 0)) return TDVP_ERR_INVALID_ARG;
+  if (!ctx->mlp_ready) return fail(ctx, TDVP_ERR_STATE, "controller: set (initial) weights first");
+  CK(cudaSetDevice(ctx->dev));
+  const long long n = log_size(ctx);
+  if (n < 1) return fail(ctx, TDVP_ERR_STATE, "controller: the solve log is empty");
+  float* d_grad = nullptr;
+  CK(cudaMalloc(&d_grad, sizeof(float) * (MLP_NPARAM + 1)));
+  float loss = 0.f, acc = 0.f;
+  int rc = TDVP_OK;
+  for (int ep = 0; ep < epochs && !rc; ++ep) {
+    acc = 0.f;
+    int nb = 0;
+    for (long long i0 = 0; i0 < n && !rc; i0 += batch) {
+      const int B = (int)std::min<long long>(batch, n - i0);
+      rc = controller_grad(ctx, ctx->d_log, i0, B, d_grad, &loss);
+      if (rc) break;
+      ++ctx->mlp_step;
+      if (launch_mlp_adam(ctx->d_mlp, d_grad, ctx->d_mlp_m, ctx->d_mlp_v, lr, ctx->mlp_step, ctx->st) != cudaSuccess)
+        rc = fail(ctx, TDVP_ERR_CUDA, "controller: Adam update failed");
+      acc += loss;
+      ++nb;
+    }
+    acc /= std::max(1, nb);
+  }
+  cudaFree(d_grad);
+  if (final_loss) *final_loss = acc;
+  return rc;
 }
 
 int tdvp_autotune(tdvp_ctx* ctx) {

@@ -17,6 +17,11 @@ typedef double2 zc;
 #define TDVP_MAX_VEC_BLOCKS 160   // chunks per vector (bounds the partial-sum table)
 #define TDVP_QR_THREADS 256
 
+// Learned Krylov controller (kernels_mlp.cu): 8 features -> 64 -> 64 -> 1
+#define MLP_NIN 8
+#define MLP_NH 64
+#define MLP_NPARAM (MLP_NIN * MLP_NH + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1)
+
 __host__ __device__ __forceinline__ zc zmake(double re, double im) { return make_double2(re, im); }
 __host__ __device__ __forceinline__ zc zadd(zc a, zc b) { return make_double2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ zc zsub(zc a, zc b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -84,7 +89,9 @@ struct KState {
   int n;                       // vector length of the solve
   int notconv;                 // stopped at kcap above tolerance
   int status;                  // 0 ok, TDVP_ERR_NAN ...
-  int pad[2];
+  int kpred;                   // Krylov dimension predicted by the learned controller (0: none)
+  int pad;
+  float feat[MLP_NIN];         // controller features of the solve in flight
 };
 
 // Per-realisation work buffers.
@@ -111,6 +118,8 @@ struct WorkDev {
   char* tc_t2;  // A operand of the third stage
   float* tc_t1; // first-stage output, planar FP32 (re plane, then im plane)
   long long tc_t1_plane;
+  int* kprev;   // [2*N] last Krylov dimension per (site, kind)
+  int* tri_count; // tridiagonal exponentials evaluated (convergence tests)
   unsigned* bar;// [0]=count, [1]=generation of the QR group barrier
   int* err;     // device-side error flag of this realisation
 };
@@ -171,7 +180,44 @@ struct LzArgs {
   int jcheck;       // convergence is tested only once k >= jcheck
   int nblk;         // chunks per vector (max over realisations)
   int* flags;       // [R] device: Krylov dimension once a solve is done, -1 on failure
+  const float* mlp; // learned controller weights (null: tests start at jcheck)
+  float* log;       // solve log rows [8 features, k] (null: no logging)
+  unsigned* log_count;
+  long long log_cap;
 };
+
+// Controller inference by the first MLP_NH threads of a block; y is returned to every thread.
+// `sm` holds at least 2*MLP_NH + MLP_NIN floats of shared memory.
+__device__ __forceinline__ float mlp_infer(const float* feat, const float* w, float* sm) {
+  float* x = sm;
+  float* h1 = sm + MLP_NIN;
+  float* h2 = h1 + MLP_NH;
+  const int j = threadIdx.x;
+  if (j < MLP_NIN) x[j] = feat[j];
+  __syncthreads();
+  if (j < MLP_NH) {
+    float z = w[MLP_NIN * MLP_NH + j];
+    for (int i = 0; i < MLP_NIN; ++i) z = fmaf(x[i], w[i * MLP_NH + j], z);
+    h1[j] = fmaxf(z, 0.f);
+  }
+  __syncthreads();
+  const int ow2 = MLP_NIN * MLP_NH + MLP_NH, ob2 = ow2 + MLP_NH * MLP_NH, ow3 = ob2 + MLP_NH;
+  if (j < MLP_NH) {
+    float z = w[ob2 + j];
+    for (int i = 0; i < MLP_NH; ++i) z = fmaf(h1[i], w[ow2 + i * MLP_NH + j], z);
+    h2[j] = fmaxf(z, 0.f) * w[ow3 + j];
+  }
+  __syncthreads();
+  if (j == 0) {
+    float y = w[ow3 + MLP_NH];
+    for (int i = 0; i < MLP_NH; ++i) y += h2[i];
+    x[0] = y;
+  }
+  __syncthreads();
+  const float y = x[0];
+  __syncthreads();
+  return y;
+}
 cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st);
 cudaError_t launch_lz_iter_pre(const LzArgs& a, int j, cudaStream_t st);   // orthogonalisation
 cudaError_t launch_lz_iter_post(const LzArgs& a, int j, cudaStream_t st);  // tridiagonal exp, next vector
@@ -206,3 +252,9 @@ cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* 
                           long long max_elems, int split, cudaStream_t st);
 cudaError_t launch_wapply_tc(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int max_xy,
                              int n_rows, int split, cudaStream_t st);
+
+// Controller training (kernels_mlp.cu)
+int mlp_partial_floats(int B);
+cudaError_t launch_mlp_grad(const float* data, long long idx0, int B, const float* w, float* partial, float* grad,
+                            cudaStream_t st);
+cudaError_t launch_mlp_adam(float* w, const float* g, float* m, float* v, float lr, int t, cudaStream_t st);
