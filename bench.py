@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-prof", action="store_true", help="time without per-launch events")
+    ap.add_argument("--no-learned", action="store_true", help="mixed arm without the learned Krylov controller")
+    ap.add_argument("--only-timed-arm", action="store_true",
+                    help="skip the FP64 reference arm (for profiling captures; no population error then)")
     ap.add_argument("--batched", type=int, default=32,
                     help="also time R disorder realisations with ragged bond dims in the same launches (0: skip)")
     return ap.parse_args()
@@ -129,18 +132,37 @@ PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2}
 TF32_OF_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rate ratio
 
 
-def timed_run(args, p, precision, rank, world, dev, stream, flush, prof):
-    """W warm-up steps, then K timed steps (L2 flushed before each); returns timing and populations."""
+def train_controller(eng, seed=0):
+    """Train the learned Krylov controller on the solve log of the warm-up steps (GPU)."""
+    from paper_1907_12044_b300.controller import init_weights
+    eng.controller_set_weights(init_weights(seed))
+    return eng.controller_train(epochs=150, batch=256, lr=3e-3)
+
+
+def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned=False):
+    """W warm-up steps, then K timed steps (L2 flushed before each); returns timing and populations.
+
+    The plain method tests Lanczos convergence at every k.  With ``learned`` the warm-up steps
+    log their solves, the controller is trained on them and the timed steps use it."""
     import torch
     import paper_1907_12044_b300 as pkg
     eng = pkg.Engine(n_realisations=1, stream=stream.cuda_stream)
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
+    eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
     pops = [eng.observables(0)[0]]
+    if learned:
+        eng.controller_logging(1 << 20)
     for _ in range(args.warmup):
         eng.step(args.dt, 1, precision=PREC[precision], tol=args.tol)
         pops.append(eng.observables(0)[0])
+    ctl = None
+    if learned:
+        nlog = eng.stats()["krylov_solves"]
+        eng.controller_logging(0)
+        ctl = {"train_loss": train_controller(eng), "samples": int(nlog)}
+    mode = pkg.KRYLOV_LEARNED if learned else pkg.KRYLOV_ADAPTIVE
     torch.cuda.synchronize()
     eng.reset_stats()
     if prof:
@@ -155,7 +177,7 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            eng.step(args.dt, 1, precision=PREC[precision], tol=args.tol)
+            eng.step(args.dt, 1, precision=PREC[precision], krylov_mode=mode, tol=args.tol)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -171,7 +193,7 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    return {"ms": ms, "stats": st, "pops": np.array(pops), "clocks": clk.summary()}
+    return {"ms": ms, "stats": st, "pops": np.array(pops), "clocks": clk.summary(), "controller": ctl}
 
 
 def run_ours(args, rank, world):
@@ -183,8 +205,12 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     prof = not args.no_prof
-    ref = timed_run(args, p, "fp64", rank, world, dev, stream, flush, prof)
-    run = ref if args.precision == "fp64" else timed_run(args, p, args.precision, rank, world, dev, stream, flush, prof)
+    run = None if args.precision == "fp64" else timed_run(args, p, args.precision, rank, world, dev, stream, flush, prof,
+                                                          learned=not args.no_learned)
+    ref = run if args.only_timed_arm and run is not None else timed_run(args, p, "fp64", rank, world, dev, stream,
+                                                                        flush, prof)
+    if run is None:
+        run = ref
     updates = (2 * N - 1) * args.steps * world
     value = updates / (run["ms"] / 1e3)
     fp64_value = updates / (ref["ms"] / 1e3)
@@ -203,7 +229,11 @@ def run_ours(args, rank, world):
                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                           l2="flushed between timed steps (256 MiB write)"),
            "fp64_arm": {"value": fp64_value, "unit": UNIT, "ms_per_step": ref["ms"] / args.steps,
+                        "krylov": "adaptive, convergence tested at every k",
+                        "tri_evals_per_step": ref["stats"]["tri_evals"] / args.steps,
                         "kernel_time_ms": {k: round(v, 3) for k, v in ref["stats"]["prof_ms"].items()}},
+           "learned_controller": run["controller"],
+           "tri_evals_per_step": run["stats"]["tri_evals"] / args.steps,
            "speedup_vs_fp64": value / fp64_value,
            "pop_error_vs_fp64": {"eq_error_final": err, "max_abs_dP": float(dP.max()),
                                  "steps_compared": len(t) - 1},
@@ -251,15 +281,23 @@ def run_batched(args, R):
         eng.build_mpo(r, q)
         eng.init_mps(r, Ds[r], q.exciton_site)
     eng.autotune()
+    eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
+    if not args.no_learned:
+        eng.controller_logging(1 << 22)
     for _ in range(args.warmup):
         eng.step(args.dt, 1, precision=PREC[args.precision], tol=args.tol)
+    mode = pkg.KRYLOV_ADAPTIVE
+    if not args.no_learned:
+        eng.controller_logging(0)
+        train_controller(eng)
+        mode = pkg.KRYLOV_LEARNED
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     eng.reset_stats()
     e0.record(stream)
-    eng.step(args.dt, args.steps, precision=PREC[args.precision], tol=args.tol)
+    eng.step(args.dt, args.steps, precision=PREC[args.precision], krylov_mode=mode, tol=args.tol)
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
@@ -269,7 +307,7 @@ def run_batched(args, R):
     return {"realisations": R, "bond_dims": "ragged from {32,48,64,96,128} (seed 12044)",
             "precision": args.precision, "value": (2 * N - 1) * R * args.steps / (ms / 1e3),
             "unit": UNIT, "ms_per_step": ms / args.steps, "gpu_launches": int(st["kernel_launches"]),
-            "qr_blocks": "autotuned"}
+            "qr_blocks": "autotuned", "krylov": "learned controller" if not args.no_learned else "adaptive"}
 
 
 def run_e2e(args, p):
