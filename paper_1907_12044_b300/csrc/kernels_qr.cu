@@ -62,44 +62,24 @@ __device__ QrJob qr_job(int dir, int site, const SiteDev* sdr, const WorkDev& W,
   return J;
 }
 
-// Bounded two-level barrier over the B blocks of one realisation: blocks arrive on one of
-// ceil(B/16) group counters, the last of each group on the root counter, and the last root
-// arrival advances the generation word everybody polls.  Counter words: bar[0] = root,
-// bar[1] = generation, bar[2 + g] = group g.  Returns false if this or an earlier wait gave up.
+// Bounded barrier over the B blocks of one realisation.  One atomic per block on one word: every
+// block adds 1 except block 0, which adds 2^31 - (B-1), so the word's top bit flips exactly once
+// per barrier; a block waits until the top bit differs from the value it read at its arrival.
+// The wait gives up after 1 s (TDVP_ERR_DEVICE_TIMEOUT).  Returns false if this or an earlier
+// wait gave up.
 __device__ bool group_sync(const WorkDev& W, int nblocks) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = W.bar + 1;
     volatile int* err = W.err;
     int good = (*err == 0);
     if (good && nblocks > 1) {
-      const int b = blockIdx.x % nblocks;
-      const int ngroups = (nblocks + 15) / 16;
-      const int grp = b / 16;
-      const unsigned gsize = (unsigned)min(16, nblocks - grp * 16);
-      const unsigned g = *gen;
+      const unsigned inc = (blockIdx.x % nblocks == 0) ? (0x80000000u - (unsigned)(nblocks - 1)) : 1u;
+      volatile unsigned* word = W.bar;
       __threadfence();
-      bool last = true;
-      if (ngroups > 1) {
-        const unsigned a = atomicAdd(W.bar + 2 + grp, 1u) + 1u;
-        last = (a == gsize);
-        if (last) {
-          atomicExch(W.bar + 2 + grp, 0u);
-          __threadfence();
-        }
-      }
-      if (last) {
-        const unsigned need = ngroups > 1 ? (unsigned)ngroups : (unsigned)nblocks;
-        const unsigned a = atomicAdd(W.bar, 1u) + 1u;
-        if (a == need) {
-          atomicExch(W.bar, 0u);
-          __threadfence();
-          atomicAdd(W.bar + 1, 1u);
-        }
-      }
+      const unsigned old = atomicAdd(W.bar, inc);
       const unsigned long long t0 = gtimer();
-      while (*gen == g) {
+      while (((old ^ *word) & 0x80000000u) == 0u) {
         if (*err != 0) { good = 0; break; }
         if (gtimer() - t0 > WAIT_NS) { atomicExch(W.err, -5); good = 0; break; }
       }
@@ -134,6 +114,37 @@ __device__ __forceinline__ zc warp_dot(const zc* a, const zc* b, int m) {
     s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
   }
   return s;
+}
+
+// Row dot products sum_c conj(X_t[c]) x[c] for t < j into out[t].  With fewer products than
+// blocks each block takes whole products with all its warps splitting the row (one L2 round
+// trip per lane, shared-memory combine); otherwise one warp per product.
+__device__ void row_dots(const zc* X, int m, const zc* x, int j, zc* out, int b, int B, int gw, int nwarps, zc* sbuf) {
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  if (j <= B) {
+    for (int t = b; t < j; t += B) {
+      const zc* q = X + (long long)t * m;
+      zc s = zmake(0, 0);
+      for (int c = threadIdx.x; c < m; c += QT) s = zcfma(__ldcg(q + c), __ldcg(x + c), s);
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      __syncthreads();
+      if (lane == 0) sbuf[wid] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        zc tot = sbuf[0];
+        for (int w = 1; w < NW; ++w) tot = zadd(tot, sbuf[w]);
+        out[t] = tot;
+      }
+    }
+  } else {
+    for (int t = gw; t < j; t += nwarps) {
+      const zc s = warp_dot(x, X + (long long)t * m, m);
+      if (lane == 0) out[t] = s;
+    }
+  }
 }
 
 // X[row0 + r][c] -= sum_{t<T} Hs[r*ldh + t] * X[t][c] for r < nb and c in the slab [c0, c1).
@@ -216,6 +227,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
   __shared__ zc L2[PB][PB];
   __shared__ zc Gs[PB][PB];
   __shared__ double Gd[PB];
+  __shared__ zc sdot[NW];
   __shared__ double red[NW];
   __shared__ int flag[2];
   const int r = blockIdx.x / B, b = blockIdx.x % B;
@@ -360,10 +372,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
       const int rr = j - j0;
       zc* x = X + (long long)j * m;
       // (A)
-      for (int t = gw; t < j; t += nwarps) {
-        const zc s = warp_dot(x, X + (long long)t * m, m);
-        if (lane == 0) S.hv[t] = s;
-      }
+      row_dots(X, m, x, j, S.hv, b, B, gw, nwarps, sdot);
       if (!group_sync(W, B)) return;
       // (B)
       for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(S.hv + t);
@@ -410,10 +419,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
       double en;
       if (full) {
         // (C)
-        for (int t = gw; t < j; t += nwarps) {
-          const zc s = warp_dot(x, X + (long long)t * m, m);
-          if (lane == 0) S.hv[n + t] = s;
-        }
+        row_dots(X, m, x, j, S.hv + n, b, B, gw, nwarps, sdot);
         if (!group_sync(W, B)) return;
         // (D)
         for (int t = threadIdx.x; t < j; t += QT) Hs[t] = __ldcg(S.hv + n + t);
