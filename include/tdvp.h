@@ -239,9 +239,10 @@ int tdvp_controller_train(tdvp_ctx* ctx, int epochs, int batch, float lr, float*
 /* Loss and gradient of the current weights on B rows X[B][8], targets t[B] (host), for checking. */
 int tdvp_controller_loss_grad(tdvp_ctx* ctx, const float* X, const float* t, int B, float* loss, float* grad);
 
-/* Autotuner: for every distinct gauge-shift QR shape of the chain, time the QR kernel with
- * several block counts per realisation on random full-rank matrices placed in the QR scratch
- * (the state is not touched) and keep the fastest for the following steps.  Requires every
+/* Autotuner: for every distinct gauge-shift QR shape of the chain, time the cooperative-grid QR
+ * kernel with several block counts per realisation and the cluster QR kernel with several
+ * cluster sizes, each on a random full-rank plus a random rank-deficient matrix placed in the QR
+ * scratch (the state is not touched), and keep the fastest for the following steps.  Requires every
  * realisation to be initialised; synchronises the stream. */
 int tdvp_autotune(tdvp_ctx* ctx);
 
@@ -252,9 +253,15 @@ int tdvp_autotune(tdvp_ctx* ctx);
  *     decides which directions are completed; raising it (e.g. to 1e-6) makes those decisions
  *     insensitive to arithmetic noise of the mixed-precision matvecs.
  *   TDVP_OPT_KRYLOV_CHECK_ALL: 1 = test Lanczos convergence at every k, 0 (default) = from the
- *     last Krylov dimension of the same site minus 2 on. */
+ *     last Krylov dimension of the same site minus 2 on.
+ *   TDVP_OPT_QR_KERNEL: which kernel runs the gauge-shift QR.  -1 (default): the autotuned
+ *     choice, else the cluster kernel with the largest cluster the shape fits; 0: the
+ *     cooperative-grid kernel (blocked Gram-Schmidt with Cholesky-QR panels); 1, 2, 4, 8, 16: the
+ *     cluster kernel with that many CTAs per realisation (a shape that does not fit its shared
+ *     memory fails with TDVP_ERR_INVALID_ARG).  All compute the same decomposition. */
 #define TDVP_OPT_RANK_RTOL         1
 #define TDVP_OPT_KRYLOV_CHECK_ALL  2
+#define TDVP_OPT_QR_KERNEL         3
 int tdvp_set_option(tdvp_ctx* ctx, int option, double value);
 
 const char* tdvp_last_error(const tdvp_ctx* ctx);

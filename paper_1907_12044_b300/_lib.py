@@ -50,6 +50,7 @@ NCAT = 7
 CATEGORIES = ["gemm", "wapply", "lanczos_vec", "tridiag", "qr", "other", "tc_gemm"]
 OPT_RANK_RTOL = 1
 OPT_KRYLOV_CHECK_ALL = 2
+OPT_QR_KERNEL = 3
 
 
 class StatsC(C.Structure):

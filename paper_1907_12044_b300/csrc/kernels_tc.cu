@@ -13,11 +13,15 @@
 // re_hi, im_hi, re_lo, im_lo one after another.  Padding rows/columns are zero.  A whole tile is
 // therefore one contiguous block that a 1-D bulk TMA copy moves into shared memory.
 //
-// GEMM kernel: one CTA per 128 x 64 output tile, 128 threads.  Thread 0 issues the bulk copies
-// (two-stage ring, mbarrier with transaction bytes) and the MMAs (tcgen05.mma, commit to an
-// mbarrier); all four warps then read the accumulators (tcgen05.ld) and write the epilogue.
+// GEMM kernel: 128 threads per CTA and S CTAs per 128 x 64 output tile, each over its own range
+// of K tiles (split-K; S = 1 when the output alone fills the GPU).  Thread 0 issues the bulk
+// copies (two-stage ring, mbarrier with transaction bytes) and the MMAs (tcgen05.mma, commit to
+// an mbarrier); all four warps then move the accumulators (tcgen05.ld) into shared memory, which
+// the copies no longer use.  The S CTAs of a tile form one thread-block cluster: after a cluster
+// barrier CTA q sums rows [q*128/S, (q+1)*128/S) of all S partial tiles, read through distributed
+// shared memory in the fixed order 0..S-1 (deterministic), and writes them with coalesced stores.
 // Every wait is bounded: on timeout the CTA records an error, drains its copies and MMAs with
-// bounded waits, frees its tensor memory and returns.
+// bounded waits, still takes part in the cluster barriers, frees its tensor memory and returns.
 #include "tdvp_internal.cuh"
 #include <cstdint>
 
@@ -91,6 +95,25 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float ld_cluster_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
@@ -191,9 +214,13 @@ __device__ bool tc_desc(int op, int site, const SiteDev* sdr, const WorkDev& W, 
   return false;
 }
 
+constexpr int PART_LD = BN + 1;       // partial tile row stride in floats (conflict-free columns)
+constexpr int MAX_SPLIT = 8;
+static_assert(2 * BM * PART_LD * 4 <= STAGE_BYTES, "partial tile must fit in the first stage");
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
-                int split) {
+                int split, int S) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ TcDesc g;
   __shared__ uint64_t full_bar[STAGES];
@@ -202,7 +229,8 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
   __shared__ uint32_t tmem_base;
   __shared__ int live, abort_flag, last_stage;
   __shared__ uint32_t last_parity;
-  const int r = blockIdx.z;
+  const int r = blockIdx.z / S;
+  const int sidx = S > 1 ? (int)cluster_rank() : 0;
   const WorkDev& W = wk[r];
   if (threadIdx.x == 0) {
     const SiteDev* sdr = sd + (long long)r * N_sites;
@@ -210,6 +238,7 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
     abort_flag = 0;
   }
   __syncthreads();
+  // the S CTAs of a cluster share realisation and output tile, so all of them leave here or none
   if (!live) return;
   const int warp = threadIdx.x / 32;
   if (warp == 0) tmem_alloc(&tmem_base, TMEM_COLS);
@@ -222,21 +251,24 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
   __syncthreads();
   tc_after();
   const uint32_t tmem = tmem_base;
-  const int nkt = cdivd(g.K, BK);
+  const int nkt_all = cdivd(g.K, BK);
+  const int kt0 = (int)((long long)nkt_all * sidx / S);
+  const int nkt = (int)((long long)nkt_all * (sidx + 1) / S) - kt0;
   const int mt = blockIdx.y, nt = blockIdx.x;
   const int npl = split ? 4 : 2;
   const uint32_t stage_tx = (uint32_t)npl * (A_TILE + B_TILE);
   if (threadIdx.x == 0) {
-    last_stage = 0;
+    last_stage = -1;
     last_parity = 0;
     auto issue = [&](int kt) {
       const int s = kt % STAGES;
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full_bar[s], stage_tx);
       for (int p = 0; p < npl; ++p) {
-        bulk_load(st + p * A_TILE, g.A + ((long long)(mt * nkt + kt) * NPL + p) * A_TILE, A_TILE, &full_bar[s]);
-        bulk_load(st + NPL * A_TILE + p * B_TILE, g.B + ((long long)(nt * nkt + kt) * NPL + p) * B_TILE, B_TILE,
+        bulk_load(st + p * A_TILE, g.A + ((long long)(mt * nkt_all + kt0 + kt) * NPL + p) * A_TILE, A_TILE,
                   &full_bar[s]);
+        bulk_load(st + NPL * A_TILE + p * B_TILE, g.B + ((long long)(nt * nkt_all + kt0 + kt) * NPL + p) * B_TILE,
+                  B_TILE, &full_bar[s]);
       }
     };
     const uint32_t id_pos = idesc_tf32(false), id_neg = idesc_tf32(true);
@@ -298,39 +330,79 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
     }
   }
   __syncthreads();
-  // accumulators complete once the last commit's barrier flips
-  bool ok = true;
-  if (!abort_flag) ok = mbar_wait(&done_bar[last_stage], last_parity);
+  // accumulators complete once the last commit's barrier flips (no K tiles: the partial is zero)
+  bool ok = !abort_flag;
+  if (ok && last_stage >= 0) ok = mbar_wait(&done_bar[last_stage], last_parity);
   tc_after();
-  if (ok && !abort_flag) {
-    const int row = mt * BM + warp * 32 + (threadIdx.x % 32);
+  if (!ok && threadIdx.x == 0) atomicExch(W.err, -5);
+  // ---- accumulators -> shared memory partial tile part[plane][row][col] ----
+  float* part = reinterpret_cast<float*>(smem);
+  {
+    const int row = warp * 32 + (threadIdx.x % 32);
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const bool have = ok && last_stage >= 0;
     for (int cb = 0; cb < BN; cb += 16) {
       float vr[16], vi[16];
-      tmem_ld16(lane_addr + cb, vr);
-      tmem_ld16(lane_addr + BN + cb, vi);
-      if (row < g.M) {
+      if (have) {
+        tmem_ld16(lane_addr + cb, vr);
+        tmem_ld16(lane_addr + BN + cb, vi);
+      } else {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int col = nt * BN + cb + q;
-          if (col >= g.N) break;
-          if (g.mode == 0) {
-            g.Cr[(long long)row * g.ldc + col] = vr[q];
-            g.Ci[(long long)row * g.ldc + col] = vi[q];
-          } else if (g.mode == 1) {
-            g.C64[(long long)row * g.ldc + col] = zmake((double)vr[q], (double)vi[q]);
-          } else {
-            const int w = row / g.pDb, lp = row % g.pDb;
-            pk_store(g.P, BM, g.pnkt, lp, w * g.pDb + col, (double)vr[q], (double)vi[q], split);
-          }
+        for (int q = 0; q < 16; ++q) { vr[q] = 0.f; vi[q] = 0.f; }
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        part[row * PART_LD + cb + q] = vr[q];
+        part[BM * PART_LD + row * PART_LD + cb + q] = vi[q];
+      }
+    }
+  }
+  tc_before();
+  if (S > 1) cluster_sync_all(); else __syncthreads();
+  // ---- sum of the S partials over this CTA's rows, coalesced epilogue ----
+  {
+    const int rows = BM / S, row0 = sidx * rows;
+    const uint32_t pbase = su32(part);
+    uint32_t rbase[MAX_SPLIT];
+#pragma unroll
+    for (int q = 0; q < MAX_SPLIT; ++q) rbase[q] = (S > 1 && q < S) ? mapa(pbase, (uint32_t)q) : 0u;
+    for (int e = threadIdx.x; e < rows * BN; e += TC_THREADS) {
+      const int lr = row0 + e / BN, col = e % BN;
+      const uint32_t off = (uint32_t)(lr * PART_LD + col) * 4u, offi = off + (uint32_t)(BM * PART_LD) * 4u;
+      float vr, vi;
+      if (S == 1) {
+        vr = part[lr * PART_LD + col];
+        vi = part[BM * PART_LD + lr * PART_LD + col];
+      } else {
+        float ar[MAX_SPLIT], ai[MAX_SPLIT];
+#pragma unroll
+        for (int q = 0; q < MAX_SPLIT; ++q) {
+          ar[q] = q < S ? ld_cluster_f32(rbase[q] + off) : 0.f;
+          ai[q] = q < S ? ld_cluster_f32(rbase[q] + offi) : 0.f;
+        }
+        vr = ar[0];
+        vi = ai[0];
+#pragma unroll
+        for (int q = 1; q < MAX_SPLIT; ++q)
+          if (q < S) { vr += ar[q]; vi += ai[q]; }
+      }
+      const int row = mt * BM + lr, gcol = nt * BN + col;
+      if (ok && row < g.M && gcol < g.N) {
+        if (g.mode == 0) {
+          g.Cr[(long long)row * g.ldc + gcol] = vr;
+          g.Ci[(long long)row * g.ldc + gcol] = vi;
+        } else if (g.mode == 1) {
+          g.C64[(long long)row * g.ldc + gcol] = zmake((double)vr, (double)vi);
+        } else {
+          const int w = row / g.pDb, lp = row % g.pDb;
+          pk_store(g.P, BM, g.pnkt, lp, w * g.pDb + gcol, (double)vr, (double)vi, split);
         }
       }
     }
-  } else if (threadIdx.x == 0) {
-    atomicExch(W.err, -5);
   }
-  tc_before();
-  __syncthreads();
+  // no CTA leaves (or frees its tensor memory) while another may still read its shared memory
+  if (S > 1) cluster_sync_all(); else __syncthreads();
+  tc_after();
   if (warp == 0) tmem_free(tmem, TMEM_COLS);
 }
 
@@ -422,11 +494,32 @@ cudaError_t tc_setup() {
   return cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGES * STAGE_BYTES);
 }
 
+// K splits per output tile: the largest power of two <= 8 that keeps at least two K tiles per
+// CTA and the whole grid within one CTA per SM of the 148
+int tc_splits(int tiles, int R, int maxK) {
+  const int nkt = cdivh(maxK, BK);
+  int S = 1;
+  while (2 * S <= MAX_SPLIT && (long long)2 * S * tiles * R <= 148 && nkt >= 4 * S) S *= 2;
+  return S;
+}
+
 cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
-                           int maxN, int split, cudaStream_t st) {
-  dim3 grid(cdivh(maxN, BN), cdivh(maxM, BM), R);
-  tc_cgemm_kernel<<<grid, TC_THREADS, STAGES * STAGE_BYTES, st>>>(op, site, sd, wk, N_sites, split);
-  return cudaGetLastError();
+                           int maxN, int maxK, int split, cudaStream_t st) {
+  const int tn = cdivh(maxN, BN), tm = cdivh(maxM, BM);
+  const int S = tc_splits(tn * tm, R, maxK);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = S;
+  cfg.gridDim = dim3(tn, tm, R * S);
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = STAGES * STAGE_BYTES;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = S > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel, op, site, sd, wk, N_sites, split, S);
 }
 
 cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,

@@ -53,7 +53,10 @@ struct tdvp_ctx {
   std::vector<long long> ws_cap;   // elements of T1 (= T2) per realisation
   int qr_cap = 0;
   double rank_rtol = kRankRtolDefault;
-  std::map<std::tuple<int, int, int>, int> qr_tuned;   // (R, m, n) -> blocks per realisation
+  // (R, m, n) -> QR kernel: B > 0 grid kernel with B blocks per realisation, -C cluster kernel
+  std::map<std::tuple<int, int, int>, int> qr_tuned;
+  int qr_force = -1;          // TDVP_OPT_QR_KERNEL
+  bool cqr_ok[17] = {};       // cluster size launchable with the largest shared-memory slab
   int check_every = 0;        // 1: test Lanczos convergence at every k (else from the last k - 2 on)
   // per-launch timing
   // learned Krylov controller
@@ -228,6 +231,8 @@ int tdvp_create(tdvp_ctx** out, int device, void* cuda_stream, int n_realisation
   ctx->ws_cap.assign(ctx->R, 0);
   ctx->qr_cap = qr_max_coresident_blocks(device);
   if (tc_setup() != cudaSuccess) { tdvp_destroy(ctx); return TDVP_ERR_CUDA; }
+  if (cqr_setup(device) != cudaSuccess) { tdvp_destroy(ctx); return TDVP_ERR_CUDA; }
+  for (int C : {1, 2, 4, 8, 16}) ctx->cqr_ok[C] = cqr_max_clusters(C, TDVP_CQR_SMEM_MAX) >= 1;
   if (ctx->qr_cap < ctx->R) { tdvp_destroy(ctx); return TDVP_ERR_INVALID_ARG; }
   *out = ctx;
   return TDVP_OK;
@@ -630,9 +635,9 @@ int matvec_site_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   LAUNCH(launch_pack_x(0, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dl * d * m.Dr, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, m.Dl, split, ctx->st));
   LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_tc(i, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wr * d, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV3, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV3, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, Wr * m.Dr, split, ctx->st));
   if (ctx->prof) {
     double f = 0;
     for (int r = v.r0; r < v.r0 + v.R; ++r) {
@@ -649,8 +654,8 @@ int matvec_bond_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
   const Dims m = maxdims(ctx, i, v);
   const int Wb = ctx->Wb[i + 1];
   LAUNCH(launch_pack_x(1, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dr * m.Dr, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z1, i, v.sd, v.wk, v.R, ctx->N, Wb * m.Dr, m.Dr, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z1, i, v.sd, v.wk, v.R, ctx->N, Wb * m.Dr, m.Dr, m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, m.Dr, Wb * m.Dr, split, ctx->st));
   if (ctx->prof) {
     double f = 0;
     for (int r = v.r0; r < v.r0 + v.R; ++r) {
@@ -682,27 +687,63 @@ int env_right(tdvp_ctx* ctx, const Views& v, int i) {
   return g_op(ctx, v, OP_ER3, i, m.Dl, m.Dl, Wl);
 }
 
-int qr_blocks(tdvp_ctx* ctx, int R, int m, int n = 0) {
-  auto it = ctx->qr_tuned.find(std::make_tuple(R, m, n));
-  if (it != ctx->qr_tuned.end()) return it->second;
+int qr_grid_default(tdvp_ctx* ctx, int R, int m) {
   int B = cdivi(m, 8);
   B = std::max(1, std::min(B, 148));
-  B = std::min(B, std::max(1, ctx->qr_cap / std::max(1, R)));
-  return B;
+  return std::min(B, std::max(1, ctx->qr_cap / std::max(1, R)));
+}
+
+bool cqr_fits(tdvp_ctx* ctx, int C, int m, int n) {
+  return C >= 1 && C <= 16 && ctx->cqr_ok[C] && C <= m && cqr_smem_bytes(n, m, C) <= TDVP_CQR_SMEM_MAX;
+}
+
+// QR kernel for an (n x m) shape over R realisations: B > 0 grid kernel, -C cluster kernel
+int qr_mode(tdvp_ctx* ctx, int R, int m, int n) {
+  if (ctx->qr_force == 0) return qr_grid_default(ctx, R, m);
+  if (ctx->qr_force > 0) return -ctx->qr_force;
+  auto it = ctx->qr_tuned.find(std::make_tuple(R, m, n));
+  if (it != ctx->qr_tuned.end()) return it->second;
+  if (n <= 256)
+    for (int C : {16, 8, 4, 2, 1})
+      if (cqr_fits(ctx, C, m, n)) return -C;
+  return qr_grid_default(ctx, R, m);
+}
+
+// One QR launch.  dir: 0 left-to-right on A[site], 1 right-to-left on A[site], 2 debug matrix,
+// 3 / 4 autotune shapes on scratch (right-to-left / left-to-right).  (m, n) bound every
+// realisation's shape.
+int run_qr(tdvp_ctx* ctx, const Views& v, int dir, int i, int m, int n, int mode, double rtol, int dn, int dm) {
+  if (mode < 0) {
+    const int C = -mode;
+    if (!cqr_fits(ctx, C, m, n)) return fail(ctx, TDVP_ERR_INVALID_ARG, "QR: shape does not fit the cluster kernel");
+    CK(launch_cluster_qr(dir, i, v.sd, v.wk, v.R, ctx->N, C, cqr_smem_bytes(n, m, C), rtol, dn, dm, ctx->st));
+    ctx->stats.kernel_launches++;
+    return TDVP_OK;
+  }
+  const int gdir = dir == 4 ? 0 : dir;      // the grid kernel's left-to-right shape lives in scratch
+  if (dir == 0) CK(launch_transpose_site(1, i, v.sd, v.wk, v.R, ctx->N, m, n, ctx->st));
+  CK(launch_row_qr(gdir, i, v.sd, v.wk, v.R, ctx->N, mode, rtol, dn, dm, ctx->st));
+  if (dir == 0) CK(launch_transpose_site(0, i, v.sd, v.wk, v.R, ctx->N, m, n, ctx->st));
+  ctx->stats.kernel_launches += dir == 0 ? 3 : 1;
+  return TDVP_OK;
+}
+
+// run_qr inside one profiling interval of category `cat`
+int run_qr_timed(tdvp_ctx* ctx, int cat, const Views& v, int dir, int i, int m, int n, int mode, double rtol,
+                 int dn, int dm) {
+  if (ctx->prof) { int pr = prof_begin(ctx, cat); if (pr) return pr; }
+  const int rc = run_qr(ctx, v, dir, i, m, n, mode, rtol, dn, dm);
+  if (rc) return rc;
+  if (ctx->prof) { int pr = prof_end(ctx); if (pr) return pr; }
+  return TDVP_OK;
 }
 
 // dir 0: C_i = L_i D (left-to-right), dir 1: C_i = D R_i (right-to-left); D lands in `bond`
 int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i];
-  if (dir == 0) {
-    LAUNCHC(TDVP_CAT_QR, launch_transpose_site(1, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, ctx->st));
-    LAUNCHC(TDVP_CAT_QR, launch_row_qr(0, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, m.Dl * d, m.Dr), ctx->rank_rtol, 0, 0, ctx->st));
-    LAUNCHC(TDVP_CAT_QR, launch_transpose_site(0, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, ctx->st));
-  } else {
-    LAUNCHC(TDVP_CAT_QR, launch_row_qr(1, i, v.sd, v.wk, v.R, ctx->N, qr_blocks(ctx, v.R, d * m.Dr, m.Dl), ctx->rank_rtol, 0, 0, ctx->st));
-  }
-  return TDVP_OK;
+  const int mm = dir == 0 ? m.Dl * d : d * m.Dr, nn = dir == 0 ? m.Dr : m.Dl;
+  return run_qr_timed(ctx, TDVP_CAT_QR, v, dir, i, mm, nn, qr_mode(ctx, v.R, mm, nn), ctx->rank_rtol, 0, 0);
 }
 
 int nblk_for(long long n) {
@@ -1185,7 +1226,10 @@ int tdvp_debug_qr(tdvp_ctx* ctx, int m, int n, const double* C, double* Q, doubl
     for (int b = 0; b < n; ++b) X[(size_t)b * m + a] = zmake(C[2 * ((size_t)a * n + b)], C[2 * ((size_t)a * n + b) + 1]);
   const Views v = one_view(ctx, 0);
   CK(cudaMemcpyAsync(ctx->h_work[0].scratch, X.data(), X.size() * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
-  LAUNCH(launch_row_qr(2, 0, v.sd, v.wk, 1, ctx->N, qr_blocks(ctx, 1, m, n), ctx->rank_rtol, n, m, ctx->st));
+  {
+    const int rc = run_qr_timed(ctx, TDVP_CAT_OTHER, v, 2, 0, m, n, qr_mode(ctx, 1, m, n), ctx->rank_rtol, n, m);
+    if (rc) return rc;
+  }
   std::vector<zc> R((size_t)n * n);
   CK(cudaMemcpyAsync(X.data(), ctx->h_work[0].scratch, X.size() * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(R.data(), ctx->h_work[0].bond, R.size() * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
@@ -1372,8 +1416,9 @@ int tdvp_autotune(tdvp_ctx* ctx) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  // every QR shape of the sweep, timed with each realisation's own site dims on random
-  // full-rank matrices in its QR scratch (the state is not touched)
+  // every QR shape of the sweep, timed with each realisation's own site dims in its QR scratch
+  // (the state is not touched) on a random full-rank and a random rank-deficient matrix (rank
+  // n/8): the sweep meets both, and the kernels' row-by-row paths differ in cost
   for (int i = 0; i < ctx->N; ++i) {
     for (int dir : {0, 3}) {
       if ((dir == 0 && i == ctx->N - 1) || (dir == 3 && i == 0)) continue;
@@ -1382,33 +1427,70 @@ int tdvp_autotune(tdvp_ctx* ctx) {
       const int nn = dir == 0 ? mx.Dr : mx.Dl;
       const auto key = std::make_tuple(ctx->R, mm, nn);
       if (ctx->qr_tuned.count(key) || nn > 256) continue;
-      std::vector<std::vector<zc>> X(ctx->R);
+      // M[kind][r]: n_r x m_r row-major; kind 0 full rank, kind 1 rank max(1, n_r / 8)
+      std::vector<std::vector<zc>> M[2];
+      std::vector<int> nr(ctx->R), mr(ctx->R);
       for (int r = 0; r < ctx->R; ++r) {
         const auto& bd = ctx->rh[r].bd;
-        X[r].resize((size_t)bd[i] * ctx->d[i] * bd[i + 1]);
-        for (auto& z : X[r]) z = zmake(nd(rng), nd(rng));
+        nr[r] = dir == 0 ? bd[i + 1] : bd[i];
+        mr[r] = dir == 0 ? bd[i] * ctx->d[i] : ctx->d[i] * bd[i + 1];
+        const int n = nr[r], m = mr[r], rk = std::max(1, n / 8);
+        M[0].emplace_back((size_t)n * m);
+        for (auto& z : M[0].back()) z = zmake(nd(rng), nd(rng));
+        std::vector<zc> P((size_t)n * rk), Qm((size_t)rk * m);
+        for (auto& z : P) z = zmake(nd(rng), nd(rng));
+        for (auto& z : Qm) z = zmake(nd(rng), nd(rng));
+        M[1].emplace_back((size_t)n * m);
+        for (int a = 0; a < n; ++a)
+          for (int c = 0; c < m; ++c) {
+            zc s = zmake(0, 0);
+            for (int t = 0; t < rk; ++t) s = zfma(P[(size_t)a * rk + t], Qm[(size_t)t * m + c], s);
+            M[1].back()[(size_t)a * m + c] = s;
+          }
       }
-      int bestB = qr_blocks(ctx, ctx->R, mm, nn);
+      std::vector<int> cands;
+      for (int B : {1, 2, 4, 8, 16, 24, 32, 48, 64, 80, 96, 128, 148})
+        if (B <= mm && (long long)B * ctx->R <= ctx->qr_cap) cands.push_back(B);
+      for (int C : {1, 2, 4, 8, 16})
+        if (cqr_fits(ctx, C, mm, nn)) cands.push_back(-C);
+      int best_mode = qr_mode(ctx, ctx->R, mm, nn);
       float best = 1e30f;
-      const int cands[] = {1, 2, 4, 8, 16, 24, 32, 48, 64, 80, 96, 128, 148};
-      for (int B : cands) {
-        if (B > mm || (long long)B * ctx->R > ctx->qr_cap) continue;
-        float tmin = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {
-          for (int r = 0; r < ctx->R; ++r)
-            CK(cudaMemcpyAsync(ctx->h_work[r].scratch, X[r].data(), X[r].size() * sizeof(zc), cudaMemcpyHostToDevice,
-                               ctx->st));
-          CK(cudaEventRecord(e0, ctx->st));
-          CK(launch_row_qr(dir, i, v.sd, v.wk, v.R, ctx->N, B, 1e-13, 0, 0, ctx->st));
-          CK(cudaEventRecord(e1, ctx->st));
-          CK(cudaEventSynchronize(e1));
-          float ms = 0;
-          CK(cudaEventElapsedTime(&ms, e0, e1));
-          tmin = std::min(tmin, ms);
+      std::vector<zc> buf;
+      for (int mode : cands) {
+        // the cluster kernel reads the left-to-right shape through its transposed view
+        const bool trans = mode < 0 && dir == 0;
+        const int tdir = dir == 0 ? 4 : 3;
+        float total = 0;
+        for (int kind = 0; kind < 2; ++kind) {
+          float tmin = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            for (int r = 0; r < ctx->R; ++r) {
+              const int n = nr[r], m = mr[r];
+              const std::vector<zc>& src = M[kind][r];
+              const zc* h = src.data();
+              if (trans) {
+                buf.resize(src.size());
+                for (int a = 0; a < n; ++a)
+                  for (int c = 0; c < m; ++c) buf[(size_t)c * n + a] = src[(size_t)a * m + c];
+                h = buf.data();
+              }
+              CK(cudaMemcpyAsync(ctx->h_work[r].scratch, h, src.size() * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
+              if (trans) CK(cudaStreamSynchronize(ctx->st));    // buf is reused by the next realisation
+            }
+            CK(cudaEventRecord(e0, ctx->st));
+            const int rc = run_qr(ctx, v, tdir, i, mm, nn, mode, 1e-13, 0, 0);
+            if (rc) return rc;
+            CK(cudaEventRecord(e1, ctx->st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tmin = std::min(tmin, ms);
+          }
+          total += tmin;
         }
-        if (tmin < best) { best = tmin; bestB = B; }
+        if (total < best) { best = total; best_mode = mode; }
       }
-      ctx->qr_tuned[key] = bestB;
+      ctx->qr_tuned[key] = best_mode;
     }
   }
   cudaEventDestroy(e0);
@@ -1426,6 +1508,14 @@ int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
     case TDVP_OPT_KRYLOV_CHECK_ALL:
       ctx->check_every = value != 0.0 ? 1 : 0;
       return TDVP_OK;
+    case TDVP_OPT_QR_KERNEL: {
+      const int c = (int)value;
+      if ((double)c != value || !(c == -1 || c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || c == 16))
+        return fail(ctx, TDVP_ERR_INVALID_ARG, "QR kernel option must be -1, 0, 1, 2, 4, 8 or 16");
+      if (c > 0 && !ctx->cqr_ok[c]) return fail(ctx, TDVP_ERR_INVALID_ARG, "cluster size not launchable on this device");
+      ctx->qr_force = c;
+      return TDVP_OK;
+    }
   }
   return fail(ctx, TDVP_ERR_INVALID_ARG, "unknown option");
 }

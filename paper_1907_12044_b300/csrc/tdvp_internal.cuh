@@ -230,6 +230,18 @@ cudaError_t launch_row_qr(int dir, int site, const SiteDev* sd, const WorkDev* w
                           int blocks_per_r, double rtol, int dbg_n, int dbg_m, cudaStream_t st);
 int qr_max_coresident_blocks(int device);
 
+// The same decomposition by one thread-block cluster of C CTAs per realisation with the matrix in
+// shared memory (kernels_cqr.cu).  dir 0 works on A[site] through its transposed view (no
+// transpose pass), dir 1 on A[site] in place, dir 2 on the debug matrix in scratch, dir 3 and 4
+// on scratch with the right-to-left / left-to-right shape of the site (autotuning).  `smem` must
+// be at least cqr_smem_bytes of the largest realisation's shape and at most TDVP_CQR_SMEM_MAX.
+#define TDVP_CQR_SMEM_MAX (220 * 1024)
+long long cqr_smem_bytes(int n, int m, int C);
+cudaError_t cqr_setup(int device);
+int cqr_max_clusters(int C, long long smem);
+cudaError_t launch_cluster_qr(int dir, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int C,
+                              long long smem, double rtol, int dbg_n, int dbg_m, cudaStream_t st);
+
 // Observables helpers.
 cudaError_t launch_set_identity_bond2(const WorkDev* wk, int R, int n, cudaStream_t st);
 cudaError_t launch_obs_local(int site, int slot, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
@@ -244,8 +256,11 @@ cudaError_t launch_reset_ks(const WorkDev* wk, int R, cudaStream_t st);
 // Tensor-core path (kernels_tc.cu)
 long long tc_pack_bytes(int rows_tile, long long rows, long long K);
 cudaError_t tc_setup();
+// maxM x maxN output over maxK bound every realisation's product; long-K products are split over
+// a thread-block cluster (tc_splits)
+int tc_splits(int tiles, int R, int maxK);
 cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
-                           int maxN, int split, cudaStream_t st);
+                           int maxN, int maxK, int split, cudaStream_t st);
 cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
                             long long max_elems, int split, cudaStream_t st);
 cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,

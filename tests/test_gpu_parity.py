@@ -35,19 +35,52 @@ def c1_random():
 
 # ------------------------------------------------------------------ gauge-shift QR (Eq. QR)
 
+# -1: default choice; 0: cooperative-grid kernel; C > 0: cluster kernel with C CTAs
+QR_KERNELS = [-1, 0, 1, 2, 4, 8, 16]
+
+
+def cluster_fits(C, m, n):
+    """Whether an n x m QR fits the cluster kernel's shared memory with C CTAs (220 KiB each)."""
+    ld = (-(-m // C)) | 1
+    return C <= m and 16 * (n * ld + 2 * (n + 4) + 3 * n) + 8 * ld <= 220 * 1024
+
+
+def debug_qr_or_rejected(eng, kernel, C):
+    """debug_qr, or None after checking that a forced cluster size too small for C is rejected."""
+    m, n = C.shape
+    if kernel > 0 and not cluster_fits(kernel, m, n):
+        with pytest.raises(pkg.TDVPError):
+            eng.debug_qr(C)
+        return None
+    return eng.debug_qr(C)
+
+
+@pytest.fixture
+def qr_kernel(c1_random, request):
+    _, eng = c1_random
+    eng.set_option(pkg.OPT_QR_KERNEL, request.param)
+    yield request.param
+    eng.set_option(pkg.OPT_QR_KERNEL, -1)
+
+
+@pytest.mark.parametrize("qr_kernel", QR_KERNELS, indirect=True)
 @pytest.mark.parametrize("m,n", [(640, 64), (100, 37), (33, 33), (40, 12), (257, 5), (64, 1)])
-def test_qr_full_rank_matches_oracle(c1_random, m, n):
+def test_qr_full_rank_matches_oracle(c1_random, qr_kernel, m, n):
     _, eng = c1_random
     rng = np.random.default_rng(m * 1000 + n)
     C = rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n))
-    Q, R = eng.debug_qr(C)
+    out = debug_qr_or_rejected(eng, qr_kernel, C)
+    if out is None:
+        return
+    Q, R = out
     Qo, Ro = qr_rr(C)
     assert np.abs(Q - Qo).max() < 1e-12
     assert np.abs(R - Ro).max() < 1e-12 * np.abs(Ro).max()
     assert np.abs(Q.conj().T @ Q - np.eye(n)).max() < 1e-13
 
 
-def test_qr_rank_deficient_matches_oracle(c1_random):
+@pytest.mark.parametrize("qr_kernel", QR_KERNELS, indirect=True)
+def test_qr_rank_deficient_matches_oracle(c1_random, qr_kernel):
     _, eng = c1_random
     rng = np.random.default_rng(5)
     cases = []
@@ -60,8 +93,18 @@ def test_qr_rank_deficient_matches_oracle(c1_random):
     E[2, 1] = 1.0
     E[7, 3] = 1j
     cases.append(E)
+    # rank 8 of 64 at the size of a bath-mode site, and a matrix whose dependent columns sit
+    # inside the column range of one CTA of a cluster
+    cases.append((rng.normal(size=(640, 8)) + 1j * rng.normal(size=(640, 8))) @ rng.normal(size=(8, 64)))
+    F = rng.normal(size=(96, 24)) + 1j * rng.normal(size=(96, 24))
+    F[:, 5] = F[:, 2] * (0.5 - 1j)
+    F[:, 17] = F[:, 3] + F[:, 9]
+    cases.append(F)
     for C in cases:
-        Q, R = eng.debug_qr(C)
+        out = debug_qr_or_rejected(eng, qr_kernel, C)
+        if out is None:
+            continue
+        Q, R = out
         Qo, Ro = qr_rr(C)
         assert np.abs(Q - Qo).max() < 1e-12
         assert np.abs(R - Ro).max() < 1e-11 * max(1.0, np.abs(Ro).max())
@@ -229,6 +272,24 @@ def test_errors_are_reported_not_crashing():
     with pytest.raises(pkg.TDVPError) as e:
         eng.step(10.0, precision=99)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("kernel", [0, 2])
+def test_truncated_sweep_with_each_qr_kernel_matches_oracle(kernel):
+    """Whole steps with the grid QR kernel (with its transpose passes) and with a 2-CTA cluster."""
+    p = wl.tiny_chain()
+    eng = pkg.Engine()
+    eng.set_option(pkg.OPT_QR_KERNEL, kernel)
+    eng.build_mpo(0, p)
+    eng.init_mps(0, 8, p.exciton_site)
+    st = TDVPState.start(p, D=8)
+    for _ in range(6):
+        eng.step(10.0)
+        tdvp_ps_step(st, 10.0)
+        assert rel_pop_err(eng.observables(0)[0], populations(st, p)) <= POP_TOL
+    for bad in (3, 32, 0.5, -2):
+        with pytest.raises(pkg.TDVPError):
+            eng.set_option(pkg.OPT_QR_KERNEL, bad)
 
 
 def test_rank_threshold_option_matches_oracle():
