@@ -15,8 +15,11 @@
 // earlier rows (block classical Gram-Schmidt), then orthonormalised inside the panel by two
 // Cholesky-QR passes on its PB x PB Gram matrix.  In exact arithmetic this gives the same Q and
 // R as the row-by-row process.  When the first Gram matrix shows a row whose squared residual is
-// below 1e-10 of its squared norm or below 1e8 rtol^2 ||X||_F^2 (where Cholesky-QR loses accuracy
-// and where the rank decision is taken), the panel is redone row by row with the exact rule.
+// below 1e-10 of its squared norm (where Cholesky-QR loses accuracy) or below 100 rtol^2
+// ||X||_F^2 (near the rank decision), the panel is redone row by row with the exact rule.  Above
+// both bounds the pivot's rounding error, O(n eps) of the row's squared norm, is below 1e-4 of the
+// pivot itself, so the pivot cannot be on the other side of rtol^2 ||X||_F^2 from the exact
+// residual.
 //
 // One realisation is processed by B co-resident blocks (cooperative launch).  Dot products over
 // whole rows are spread over all warps of all blocks; updates are done by the block that owns a
@@ -307,7 +310,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
         int bad = 0;
         for (int jj = 0; jj < nb; ++jj) {
           const double s = Gs[jj][jj].x;            // Schur complement pivot
-          if (!(s > 0.0) || (it == 0 && (s <= 1e-10 * Gd[jj] || s <= 1e8 * thresh * thresh))) { bad = it + 1; break; }
+          if (!(s > 0.0) || (it == 0 && (s <= 1e-10 * Gd[jj] || s <= 100.0 * thresh * thresh))) { bad = it + 1; break; }
           const double d = sqrt(s), inv = 1.0 / d;
           for (int i = lane; i < nb; i += 32)
             Lc[i][jj] = (i < jj) ? zmake(0, 0) : (i == jj ? zmake(d, 0) : zscale(Gs[i][jj], inv));

@@ -274,6 +274,39 @@ def test_errors_are_reported_not_crashing():
     assert e.value.code == -1
 
 
+@pytest.mark.parametrize("qr_kernel", QR_KERNELS, indirect=True)
+def test_qr_graded_spectrum_rank_decisions_match_oracle(c1_random, qr_kernel):
+    """Singular values 10^(-k/4 - 1/8): many rows near the threshold rtol*||C||_F on both sides."""
+    _, eng = c1_random
+    rng = np.random.default_rng(77)
+    m, n = 320, 48
+    U, _ = np.linalg.qr(rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n)))
+    V, _ = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    sig = 10.0 ** (-np.arange(n) / 4.0 - 0.125)
+    C = (U * sig) @ V.conj().T
+    for rtol in (1e-6, 1e-9):
+        eng.set_option(pkg.OPT_RANK_RTOL, rtol)
+        try:
+            out = debug_qr_or_rejected(eng, qr_kernel, C)
+        finally:
+            eng.set_option(pkg.OPT_RANK_RTOL, 1e-13)
+        if out is None:
+            return
+        Q, R = out
+        Qo, Ro = qr_rr(C, rtol)
+        dropped = np.abs(np.diag(Ro)) == 0
+        assert 0 < dropped.sum() < n
+        assert np.array_equal(np.abs(np.diag(R)) == 0, dropped)
+        # R is well conditioned here (the oracle's R moves by ~1e-15 under 1e-15 perturbations of
+        # C); Q is not (it moves by ~4e-10 at rtol 1e-6 and ~2e-7 at 1e-9 under the same
+        # perturbations), so Q is checked through orthonormality and C = Q R up to the dropped
+        # residuals, and against the oracle at 1e3 times that sensitivity
+        assert np.abs(R - Ro).max() < 1e-11
+        assert np.abs(Q.conj().T @ Q - np.eye(n)).max() < 1e-12
+        assert np.linalg.norm(Q @ R - C) <= 2 * rtol * np.linalg.norm(C) * np.sqrt(n)
+        assert np.abs(Q - Qo).max() < (1e-6 if rtol == 1e-6 else 1e-4)
+
+
 @pytest.mark.parametrize("kernel", [0, 2])
 def test_truncated_sweep_with_each_qr_kernel_matches_oracle(kernel):
     """Whole steps with the grid QR kernel (with its transpose passes) and with a 2-CTA cluster."""
