@@ -222,6 +222,167 @@ struct Scratch {
   zc* Pc;     // [2B]     per-block completion candidates
 };
 
+// ---- rank-deficient tail ----
+// Taken after a dropped row j when every later row is dropped too.  With Q_t (t < J0 = j+1)
+// final, rows J0..n-1 are projected twice onto them (block Gram-Schmidt); if every residual is
+// <= thresh/2 then, since the exact process tests each later row against a superset of these
+// Q_t (residuals only shrink) and the rounding differences are O(eps ||x||), every later row is
+// dropped under the exact rule as well.  The completions are then built one per group barrier:
+// rows are kept unnormalised with their squared norms (so no row another block reads is
+// rewritten), every block keeps its own copy of all m column sums sum_t |Q_t[c]|^2 and picks
+// the next unit vector itself.  A completion is e_p minus its projection with the exact
+// first-pass coefficients conj(Q_t[p]); being at distance >= 1/2 from the span (or the farthest
+// unit vector), one pass leaves it orthogonal to O(eps).  Finally rows are normalised and the
+// R coefficients of the dropped rows against the completions are taken from the backed-up rows.
+// Returns 1 when rows J0..n-1 are done, 0 when the tail test failed (rows restored), -1 when a
+// group barrier gave up.
+constexpr int TAIL_CQ = (PB * QR_NMAX - QR_NMAX) * 2;   // doubles of the column-sum copy in Hs
+
+__device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J0, int j0, int pend, int b, int B,
+                       int gw, int nwarps, int c0, int c1, double thresh, zc* Hs, double* red, double* ens,
+                       int* flag) {
+  const int n = J.n, m = J.m, Tn = n - J0, lane = threadIdx.x % 32;
+  zc* X = J.X;
+  zc* BK = W.qtail;                                     // [n][m] backup of rows J0..n-1
+  zc* HT1 = BK + (long long)n * m;                      // [n][n]
+  zc* HT2 = HT1 + (long long)n * n;                     // [n][n]
+  double* TPN = reinterpret_cast<double*>(HT2 + (long long)n * n);   // [n][B]
+  for (long long e = threadIdx.x; e < (long long)Tn * (c1 - c0); e += QT) {
+    const int j = J0 + (int)(e / (c1 - c0)), c = c0 + (int)(e % (c1 - c0));
+    BK[(long long)j * m + c] = X[(long long)j * m + c];
+  }
+  // two projection passes of rows J0..n-1 onto rows 0..J0-1
+  for (int pass = 0; pass < 2; ++pass) {
+    zc* HT = pass ? HT2 : HT1;
+    for (int e = gw; e < Tn * J0; e += nwarps) {
+      const int a = e / J0, t = e % J0;
+      const zc s = warp_dot(X + (long long)(J0 + a) * m, X + (long long)t * m, m);
+      if (lane == 0) HT[(long long)a * n + t] = s;
+    }
+    if (!group_sync(W, B)) return -1;
+    for (int a0 = 0; a0 < Tn; a0 += PB) {
+      const int nb = min(PB, Tn - a0);
+      for (int e = threadIdx.x; e < nb * J0; e += QT) Hs[e] = __ldcg(HT + (long long)(a0 + e / J0) * n + e % J0);
+      __syncthreads();
+      slab_update(X, m, J0 + a0, nb, J0, Hs, J0, c0, c1);
+    }
+    if (pass == 1) {
+      for (int a = 0; a < Tn; ++a) {
+        double s = 0;
+        for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(X[(long long)(J0 + a) * m + c]);
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) TPN[(long long)a * B + b] = s;
+      }
+    }
+    if (!group_sync(W, B)) return -1;
+  }
+  // tail test: every residual <= thresh/2 (the same sums in the same order in every block)
+  {
+    int bad = 0;
+    for (int a = threadIdx.x; a < Tn; a += QT) {
+      double s = 0;
+      for (int bb = 0; bb < B; ++bb) s += __ldcg(TPN + (long long)a * B + bb);
+      if (!(sqrt(s) <= 0.5 * thresh)) bad = 1;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad) {
+      for (long long e = threadIdx.x; e < (long long)Tn * (c1 - c0); e += QT) {
+        const int j = J0 + (int)(e / (c1 - c0)), c = c0 + (int)(e % (c1 - c0));
+        X[(long long)j * m + c] = BK[(long long)j * m + c];
+      }
+      return group_sync(W, B) ? 0 : -1;
+    }
+  }
+  // completions, one group barrier each
+  double* cq = reinterpret_cast<double*>(Hs + QR_NMAX);  // all m column sums (this block's copy)
+  for (int c = threadIdx.x; c < m; c += QT) cq[c] = __ldcg(W.colsq + c);
+  __syncthreads();
+  for (int a = 0; a < Tn; ++a) {
+    const int j = J0 + a;
+    // next unit vector: the first column at distance >= 1/2 (1 - cq >= 1/4), else the farthest
+    {
+      int first = 0x7fffffff, besti = 0x7fffffff;
+      double bestv = -2.0;
+      for (int c = threadIdx.x; c < m; c += QT) {
+        const double dist = 1.0 - cq[c];
+        if (dist >= 0.25 && c < first) first = c;
+        if (dist > bestv || (dist == bestv && c < besti)) { bestv = dist; besti = c; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const int f2 = __shfl_xor_sync(0xffffffffu, first, o);
+        const double v2 = __shfl_xor_sync(0xffffffffu, bestv, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, besti, o);
+        first = min(first, f2);
+        if (v2 > bestv || (v2 == bestv && i2 < besti)) { bestv = v2; besti = i2; }
+      }
+      if (lane == 0) { red[threadIdx.x / 32] = bestv; flag[threadIdx.x / 32 + 2] = first; flag[threadIdx.x / 32 + 2 + NW] = besti; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int f = flag[2], bi = flag[2 + NW];
+        double bv = red[0];
+        for (int w = 1; w < NW; ++w) {
+          f = min(f, flag[2 + w]);
+          if (red[w] > bv || (red[w] == bv && flag[2 + NW + w] < bi)) { bv = red[w]; bi = flag[2 + NW + w]; }
+        }
+        const int p = f < 0x7fffffff ? f : (bi < 0x7fffffff ? bi : 0);
+        flag[1] = min(max(p, 0), m - 1);
+      }
+      __syncthreads();
+    }
+    const int p = flag[1];
+    // x_j = e_p - sum_t conj(Q_t[p]) Q_t with Q_t = X_t / sqrt(ens) for the (unnormalised) tail rows
+    for (int t = threadIdx.x; t < j; t += QT) {
+      const double s = t < J0 ? 1.0 : 1.0 / ens[t - J0];
+      Hs[t] = zscale(zconj(__ldcg(X + (long long)t * m + p)), s);
+    }
+    zc* x = X + (long long)j * m;
+    for (int c = c0 + threadIdx.x; c < c1; c += QT) x[c] = zmake(c == p ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    slab_update(X, m, j, 1, j, Hs, j, c0, c1);
+    {
+      double s = 0;
+      for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(x[c]);
+      s = block_sum(s, red);
+      if (threadIdx.x == 0) S.Pn[(a & 1) * B + b] = zmake(s, 0.0);
+    }
+    if (!group_sync(W, B)) return -1;
+    const double en2 = sum_over_blocks(S.Pn + (a & 1) * B, B);
+    if (threadIdx.x == 0) ens[a] = en2;
+    const double inv = en2 > 0.0 ? 1.0 / en2 : 0.0;
+    for (int c = threadIdx.x; c < m; c += QT) cq[c] += zabs2(__ldcg(x + c)) * inv;
+    __syncthreads();
+  }
+  // normalise the completions on the slab
+  for (int a = 0; a < Tn; ++a) {
+    const double inv = ens[a] > 0.0 ? 1.0 / sqrt(ens[a]) : 0.0;
+    zc* x = X + (long long)(J0 + a) * m;
+    for (int c = c0 + threadIdx.x; c < c1; c += QT) x[c] = zscale(x[c], inv);
+  }
+  if (!group_sync(W, B)) return -1;
+  // R rows of the dropped rows: against rows < J0 the two projection passes (plus the panel's
+  // passes for rows the panel had already projected), against the completions the dot products
+  // of the backed-up rows, zero on and above the diagonal
+  for (int e = gw; e < Tn * Tn; e += nwarps) {
+    const int a = e / Tn, a2 = e % Tn;
+    const int j = J0 + a, t = J0 + a2;
+    zc v = zmake(0, 0);
+    if (a2 < a) v = warp_dot(BK + (long long)j * m, X + (long long)t * m, m);
+    if (lane == 0) J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
+  }
+  if (b == 0) {
+    for (int e = threadIdx.x; e < Tn * J0; e += QT) {
+      const int a = e / J0, t = e % J0, j = J0 + a;
+      zc v = zadd(__ldcg(HT1 + (long long)a * n + t), __ldcg(HT2 + (long long)a * n + t));
+      if (j < pend && t < j0) {
+        const int rr = j - j0;
+        v = zadd(v, zadd(__ldcg(S.H1 + rr * n + t), __ldcg(S.H2 + rr * n + t)));
+      }
+      J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
+    }
+  }
+  return 1;
+}
+
 __global__ void __launch_bounds__(QT)
 bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites, int B,
            double rtol, int dn, int dm) {
@@ -232,7 +393,9 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
   __shared__ double Gd[PB];
   __shared__ zc sdot[NW];
   __shared__ double red[NW];
-  __shared__ int flag[2];
+  __shared__ int flag[2 + 2 * NW];
+  __shared__ double ens[QR_NMAX];
+  int tail_tries = 0;
   const int r = blockIdx.x / B, b = blockIdx.x % B;
   const SiteDev* sdr = sd + (long long)r * N_sites;
   const WorkDev& W = wk[r];
@@ -488,6 +651,13 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
         colsq[c] += zabs2(v);
       }
       if (!group_sync(W, B)) return;
+      // after a dropped row, try to finish every later row as a completion in one go
+      if (!full && tail_tries < 2 && n - (j + 1) >= 2 && m <= TAIL_CQ) {
+        ++tail_tries;
+        const int rc = qr_tail(J, W, S, j + 1, j0, j0 + nb, b, B, gw, nwarps, c0, c1, thresh, Hs, red, ens, flag);
+        if (rc < 0) return;
+        if (rc == 1) return;
+      }
     }
   }
 }

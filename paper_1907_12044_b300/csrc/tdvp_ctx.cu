@@ -703,9 +703,6 @@ int qr_mode(tdvp_ctx* ctx, int R, int m, int n) {
   if (ctx->qr_force > 0) return -ctx->qr_force;
   auto it = ctx->qr_tuned.find(std::make_tuple(R, m, n));
   if (it != ctx->qr_tuned.end()) return it->second;
-  if (n <= 256)
-    for (int C : {16, 8, 4, 2, 1})
-      if (cqr_fits(ctx, C, m, n)) return -C;
   return qr_grid_default(ctx, R, m);
 }
 
@@ -889,6 +886,7 @@ int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
   if ((rc = dalloc(ctx, H.mps_allocs, &W.qpart, (size_t)3 * 148 * (Dmax + 4)))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.qhp, Dmax))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.colsq, mmax))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.qtail, (size_t)(nmax + 2 * Dmax * Dmax + Dmax * 74 + 16)))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.obs, ctx->n_el + 4))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.ks, 1))) return rc;
   {

@@ -109,6 +109,8 @@ struct WorkDev {
   zc* qpart;    // QR partial sums [qr_blocks][Dmax+4] x 3
   zc* qhp;      // QR completion coefficients [Dmax]
   double* colsq;// QR column norms [d*Dmax]
+  zc* qtail;    // QR rank-deficient tail: row backup [Dmax*d*Dmax], two coefficient tables
+                // [Dmax][Dmax], per-block residual norms [Dmax][148] (as doubles)
   double* obs;  // observables: [n_el] <n>, then <Psi|Psi>, energy numerator
   KState* ks;
   // tensor-core operands (packed tiles, see kernels_tc.cu)
