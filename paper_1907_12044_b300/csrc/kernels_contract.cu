@@ -125,6 +125,7 @@ __device__ bool make_desc(int op, int site, int b, const SiteDev* sdr, const Wor
       g.B = wk.T1; g.ldb = Dr;
       g.C = (site % 2 == 0) ? wk.bond : wk.bond2; g.ldc = Dr;
       g.M = Dr; g.N = Dr; g.K = Dl * d;
+      g.ws = wk.T2;
       return true;
     }
   }

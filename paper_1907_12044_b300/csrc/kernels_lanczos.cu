@@ -34,7 +34,7 @@ __device__ __forceinline__ long long vec_len(const SiteDev* sdr, int site, int k
 __device__ __forceinline__ VecGeom geom(long long n, int b) {
   VecGeom g;
   g.n = n;
-  long long nb = (n + 511) / 512;
+  long long nb = (n + TDVP_VEC_CHUNK - 1) / TDVP_VEC_CHUNK;
   if (nb > TDVP_MAX_VEC_BLOCKS) nb = TDVP_MAX_VEC_BLOCKS;
   if (nb < 1) nb = 1;
   g.nblk = (int)nb;

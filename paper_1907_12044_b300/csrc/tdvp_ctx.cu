@@ -524,7 +524,7 @@ double gemm_flops(tdvp_ctx* ctx, const Views& v, int op, int site) {
 // K splits for a GEMM with few output tiles: enough blocks to cover every SM twice, limited by the
 // inner tile count and by the workspace (T1 or T2 of each realisation, ws_cap elements).
 int split_for(tdvp_ctx* ctx, const Views& v, int op, int site, int M, int Nn, int nb) {
-  const bool splittable = op == OP_MV3 || op == OP_EL3 || op == OP_ER3 || op == OP_Z1 || op == OP_Z3;
+  const bool splittable = op == OP_MV3 || op == OP_EL3 || op == OP_ER3 || op == OP_Z1 || op == OP_Z3 || op == OP_TR3;
   if (!splittable) return 1;
   const long long tiles = (long long)cdivi(M, 32) * cdivi(Nn, 32) * nb * v.R;
   if (tiles >= 296) return 1;
@@ -536,6 +536,7 @@ int split_for(tdvp_ctx* ctx, const Views& v, int op, int site, int M, int Nn, in
     case OP_ER3: K = ctx->d[site] * m.Dr; break;
     case OP_Z1: K = m.Dr; break;
     case OP_Z3: K = m.Dr; nz = ctx->Wb[site + 1]; break;
+    case OP_TR3: K = m.Dl * ctx->d[site]; break;
   }
   const int kt = nz * cdivi(K, 16);
   int S = (int)std::min<long long>(cdivi(296, tiles), 16);
@@ -740,11 +741,22 @@ int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i];
   const int mm = dir == 0 ? m.Dl * d : d * m.Dr, nn = dir == 0 ? m.Dr : m.Dl;
+  if (ctx->prof) {
+    // algorithmic flops of the definition: two Gram-Schmidt passes (dots and updates) per row,
+    // 2 n^2 m complex multiply-adds of 8 real flops
+    double f = 0;
+    for (int r = v.r0; r < v.r0 + v.R; ++r) {
+      const auto& bd = ctx->rh[r].bd;
+      const double n = dir == 0 ? bd[i + 1] : bd[i], mr = dir == 0 ? (double)bd[i] * d : (double)d * bd[i + 1];
+      f += 16.0 * n * n * mr;
+    }
+    ctx->stats.prof_flops[TDVP_CAT_QR] += f;
+  }
   return run_qr_timed(ctx, TDVP_CAT_QR, v, dir, i, mm, nn, qr_mode(ctx, v.R, mm, nn), ctx->rank_rtol, 0, 0);
 }
 
 int nblk_for(long long n) {
-  long long nb = (n + 511) / 512;
+  long long nb = (n + TDVP_VEC_CHUNK - 1) / TDVP_VEC_CHUNK;
   return (int)std::max(1LL, std::min<long long>(nb, TDVP_MAX_VEC_BLOCKS));
 }
 

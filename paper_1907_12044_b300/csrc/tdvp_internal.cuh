@@ -15,6 +15,8 @@ typedef double2 zc;
 #define TDVP_KMAX_HARD 128        // largest Krylov dimension supported
 #define TDVP_VEC_THREADS 256      // threads of the Lanczos vector kernels
 #define TDVP_MAX_VEC_BLOCKS 160   // chunks per vector (bounds the partial-sum table)
+#define TDVP_VEC_CHUNK 256        // elements per chunk before the cap: one per thread, so a
+                                  // 640 x 64 site vector spreads over every SM
 #define TDVP_QR_THREADS 256
 
 // Learned Krylov controller (kernels_mlp.cu): 8 features -> 64 -> 64 -> 1
