@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="mixed arm without the learned Krylov controller")
     ap.add_argument("--only-timed-arm", action="store_true",
                     help="skip the FP64 reference arm (for profiling captures; no population error then)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="timed arm launch by launch instead of replaying each step as a CUDA graph "
+                         "(the FP64 arm is always launch by launch: the plain method)")
     ap.add_argument("--kernel-case", choices=["heff", "qr"], default=None,
                     help="time one hot operation at the bench's full-size shapes instead of steps (for "
                          "kernel captures): heff = one H_eff matvec at a bath-mode site of a random D-bond "
@@ -147,9 +150,13 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
     """W warm-up steps, then K timed steps (L2 flushed before each); returns timing and populations.
 
     The plain method tests Lanczos convergence at every k.  With ``learned`` the warm-up steps
-    log their solves, the controller is trained on them and the timed steps use it."""
+    log their solves, the controller is trained on them and the timed steps use it.  A mixed arm
+    replays each step as a CUDA graph (unless --no-graph): the last warm-up step captures it, and
+    since per-launch events are not available inside a graph, one more step after the timed ones
+    runs launch by launch with CUDA-event timing for the per-kernel breakdown."""
     import torch
     import paper_1907_12044_b300 as pkg
+    graph = precision != "fp64" and not args.no_graph and args.warmup >= 1
     eng = pkg.Engine(n_realisations=1, stream=stream.cuda_stream)
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
     eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
@@ -158,7 +165,7 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
     pops = [eng.observables(0)[0]]
     if learned:
         eng.controller_logging(1 << 20)
-    for _ in range(args.warmup):
+    for _ in range(args.warmup - (1 if graph else 0)):
         eng.step(args.dt, 1, precision=PREC[precision], tol=args.tol)
         pops.append(eng.observables(0)[0])
     ctl = None
@@ -167,9 +174,13 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
         eng.controller_logging(0)
         ctl = {"train_loss": train_controller(eng), "samples": int(nlog)}
     mode = pkg.KRYLOV_LEARNED if learned else pkg.KRYLOV_ADAPTIVE
+    if graph:
+        eng.set_option(pkg.OPT_GRAPH, 1)
+        eng.step(args.dt, 1, precision=PREC[precision], krylov_mode=mode, tol=args.tol)   # capture
+        pops.append(eng.observables(0)[0])
     torch.cuda.synchronize()
     eng.reset_stats()
-    if prof:
+    if prof and not graph:
         eng.set_profiling(True)
     times = []
     if world > 1:
@@ -191,13 +202,25 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
         torch.distributed.barrier()
     st = eng.stats()
     eng.set_profiling(False)
+    if prof and graph:
+        # per-kernel CUDA-event breakdown of one more (untimed) step, launch by launch
+        eng.set_option(pkg.OPT_GRAPH, 0)
+        eng.reset_stats()
+        eng.set_profiling(True)
+        eng.step(args.dt, 1, precision=PREC[precision], krylov_mode=mode, tol=args.tol)
+        eng.set_profiling(False)
+        ps = eng.stats()
+        for k in ("prof_ms", "prof_flops", "prof_launches"):
+            st[k] = {c: v * args.steps for c, v in ps[k].items()}
+        st["prof_note"] = "per-kernel breakdown from one launch-by-launch step after the timed ones, x steps"
     eng.close()
     ms = float(np.sum(times))
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    return {"ms": ms, "stats": st, "pops": np.array(pops), "clocks": clk.summary(), "controller": ctl}
+    return {"ms": ms, "stats": st, "pops": np.array(pops), "clocks": clk.summary(), "controller": ctl,
+            "graph": graph}
 
 
 # kernel and arithmetic of each timed category with algorithmic flop counts
@@ -260,6 +283,8 @@ def run_ours(args, rank, world):
                      "tf32x3": "tf32x3 split tensor cores, f32 accumulate; f64 Lanczos/QR"}[args.precision],
            "data": "synthetic (seeded FMO-sized Frenkel-Holstein chain)",
            "config": dict(cfg, precision=args.precision,
+                          execution=("each step replayed as one CUDA graph (a conditional while node per "
+                                     "Lanczos exponential)") if run["graph"] else "launch by launch",
                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                           l2="flushed between timed steps (256 MiB write)"),
            "fp64_arm": {"value": fp64_value, "unit": UNIT, "ms_per_step": ref["ms"] / args.steps,
@@ -301,15 +326,19 @@ def run_batched(args, R):
         eng.init_mps(r, Ds[r], q.exciton_site)
     eng.autotune()
     eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
+    graph = not args.no_graph and args.warmup >= 1
     if not args.no_learned:
         eng.controller_logging(1 << 22)
-    for _ in range(args.warmup):
+    for _ in range(args.warmup - (1 if graph else 0)):
         eng.step(args.dt, 1, precision=PREC[args.precision], tol=args.tol)
     mode = pkg.KRYLOV_ADAPTIVE
     if not args.no_learned:
         eng.controller_logging(0)
         train_controller(eng)
         mode = pkg.KRYLOV_LEARNED
+    if graph:
+        eng.set_option(pkg.OPT_GRAPH, 1)
+        eng.step(args.dt, 1, precision=PREC[args.precision], krylov_mode=mode, tol=args.tol)   # capture
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -326,7 +355,8 @@ def run_batched(args, R):
     return {"realisations": R, "bond_dims": "ragged from {32,48,64,96,128} (seed 12044)",
             "precision": args.precision, "value": (2 * N - 1) * R * args.steps / (ms / 1e3),
             "unit": UNIT, "ms_per_step": ms / args.steps, "gpu_launches": int(st["kernel_launches"]),
-            "qr_blocks": "autotuned", "krylov": "learned controller" if not args.no_learned else "adaptive"}
+            "qr_blocks": "autotuned", "krylov": "learned controller" if not args.no_learned else "adaptive",
+            "execution": "each step of all realisations replayed as one CUDA graph" if graph else "launch by launch"}
 
 
 def run_e2e(args, p):
@@ -346,15 +376,19 @@ def run_e2e(args, p):
     torch.cuda.synchronize()
     upload_s = time.perf_counter() - t0
     learned = args.precision != "fp64" and not args.no_learned
+    graph = args.precision != "fp64" and not args.no_graph and args.warmup >= 1
     if learned:
         eng.controller_logging(1 << 20)
-    for _ in range(args.warmup):
+    for _ in range(args.warmup - (1 if graph else 0)):
         eng.step(args.dt, 1, precision=PREC[args.precision], tol=args.tol)
     mode = pkg.KRYLOV_ADAPTIVE
     if learned:
         eng.controller_logging(0)
         train_controller(eng)
         mode = pkg.KRYLOV_LEARNED
+    if graph:
+        eng.set_option(pkg.OPT_GRAPH, 1)
+        eng.step(args.dt, 1, precision=PREC[args.precision], krylov_mode=mode, tol=args.tol)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):

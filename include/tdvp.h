@@ -258,10 +258,20 @@ int tdvp_autotune(tdvp_ctx* ctx);
  *     choice, else the cooperative-grid kernel; 0: the
  *     cooperative-grid kernel (blocked Gram-Schmidt with Cholesky-QR panels); 1, 2, 4, 8, 16: the
  *     cluster kernel with that many CTAs per realisation (a shape that does not fit its shared
- *     memory fails with TDVP_ERR_INVALID_ARG).  All compute the same decomposition. */
+ *     memory fails with TDVP_ERR_INVALID_ARG).  All compute the same decomposition.
+ *   TDVP_OPT_GRAPH: 1 = tdvp_ps_step captures one whole step (every realisation) into a CUDA
+ *     graph and replays it n_steps times.  Each Lanczos exponential is a conditional while node
+ *     whose body is one iteration; the device ends the loop, so a step needs no host round trip.
+ *     Convergence tests start from each realisation's previous Krylov dimension of the same
+ *     (site, kind) minus 2 (or every k with TDVP_OPT_KRYLOV_CHECK_ALL, or at the learned
+ *     prediction).  The graph is captured on the first call for a (dt, tolerance, precision,
+ *     Krylov mode) and kept until build/init, autotune or any option change.  Ignored while
+ *     profiling is on (per-launch timing needs the launch-by-launch path).  0 (default): launch
+ *     by launch, one host flag read per exponential. */
 #define TDVP_OPT_RANK_RTOL         1
 #define TDVP_OPT_KRYLOV_CHECK_ALL  2
 #define TDVP_OPT_QR_KERNEL         3
+#define TDVP_OPT_GRAPH             4
 int tdvp_set_option(tdvp_ctx* ctx, int option, double value);
 
 const char* tdvp_last_error(const tdvp_ctx* ctx);

@@ -51,6 +51,7 @@ CATEGORIES = ["gemm", "wapply", "lanczos_vec", "tridiag", "qr", "other", "tc_gem
 OPT_RANK_RTOL = 1
 OPT_KRYLOV_CHECK_ALL = 2
 OPT_QR_KERNEL = 3
+OPT_GRAPH = 4
 
 
 class StatsC(C.Structure):

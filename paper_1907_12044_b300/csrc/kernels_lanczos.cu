@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
     ks->kcap = (int)(g.n < a.kmax ? g.n : a.kmax);
     ks->notconv = 0;
     ks->err = 0;
+    ks->jcur = 0;
     const bool bad = !isfinite(nrm);
     ks->status = bad ? -6 : 0;
     ks->done = (nrm == 0.0 || bad) ? 1 : 0;
@@ -191,6 +192,7 @@ __global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
   if (W.ks->done) return;
+  if (a.devj) j = W.ks->jcur;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
   if (b >= g.nblk) return;
@@ -204,6 +206,7 @@ __global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
   if (W.ks->done) return;
+  if (a.devj) j = W.ks->jcur;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
   if (b >= g.nblk) return;
@@ -359,6 +362,7 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
   const WorkDev& W = a.wk[r];
   KState* ks = W.ks;
   if (ks->done) return;
+  if (a.devj) j = ks->jcur;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const VecGeom g = geom(vec_len(sdr, a.site, a.kind), 0);
   if (threadIdx.x < 32) {
@@ -371,7 +375,10 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
   const double beta = betaj_s;
   const int k = j + 1;
   if (!isfinite(beta) || !isfinite(ks->alpha[j])) {
-    if (threadIdx.x == 0) { ks->status = -6; ks->done = 1; ks->k = 0; flags[r] = -1; }
+    if (threadIdx.x == 0) {
+      ks->status = -6; ks->done = 1; ks->k = 0; flags[r] = -1;
+      if (a.devj) atomicExch(W.err, -7);
+    }
     return;
   }
   const bool last = (k >= ks->kcap) || beta == 0.0;
@@ -397,7 +404,10 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
       __syncthreads();
     }
   }
-  const int jcheck = a.mlp ? max(1, ks->kpred) : a.jcheck;
+  // a.jcheck = 0: from the previous Krylov dimension of this (site, kind) minus 2 (device-driven
+  // loops; the host-driven loop passes the same rule evaluated on the host)
+  const int jcheck = a.mlp ? max(1, ks->kpred)
+                           : (a.jcheck > 0 ? a.jcheck : max(1, W.kprev[2 * a.site + a.kind] - 2));
   if (k < jcheck && !last) {
     if (threadIdx.x == 0) { ks->beta[j] = beta; ks->inv_beta = 1.0 / beta; }
     return;
@@ -405,7 +415,10 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
   if (threadIdx.x == 0) (*W.tri_count)++;
   const bool ok = tridiag_expi(ks->alpha, ks->beta, k, a.theta, c, sh);
   if (!ok) {
-    if (threadIdx.x == 0) { ks->status = -1; ks->done = 1; ks->k = 0; flags[r] = -1; }
+    if (threadIdx.x == 0) {
+      ks->status = -1; ks->done = 1; ks->k = 0; flags[r] = -1;
+      if (a.devj) atomicExch(W.err, -7);
+    }
     return;
   }
   const double err = ks->nrm * beta * sqrt(zabs2(c[k - 1]));
@@ -419,6 +432,12 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
       ks->done = 1;
       flags[r] = k | (ks->notconv << 16);
       W.kprev[2 * a.site + a.kind] = k;
+      if (a.devj) {
+        ks->dim_sum += k;
+        ks->dim_max = max(ks->dim_max, k);
+        ks->solves += 1;
+        ks->nc_count += ks->notconv;
+      }
       if (a.log) {
         const unsigned slot = atomicAdd(a.log_count, 1u);
         if ((long long)slot < a.log_cap) {
@@ -438,6 +457,7 @@ __global__ void __launch_bounds__(NT) lz_next(LzArgs a, int j) {
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
   if (W.ks->done) return;
+  if (a.devj) j = W.ks->jcur;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
   if (b >= g.nblk) return;
@@ -468,7 +488,37 @@ __global__ void __launch_bounds__(NT) lz_combine(LzArgs a) {
   }
 }
 
+// Loop control of a device-driven solve (one warp).  The body's kernels have all finished when
+// this runs (graph dependency), so every unfinished solve's iteration index can advance.
+__global__ void lz_loop_ctl(LzArgs a, int which) {
+  int active = 0;
+  for (int r = threadIdx.x; r < a.R; r += 32) {
+    KState* ks = a.wk[r].ks;
+    if (!ks->done) {
+      if (which == 1) ks->jcur += 1;
+      if (ks->jcur >= a.kmax) {
+        // cannot happen while the tridiagonal kernel stops every solve at its cap; it bounds the
+        // device loop even so
+        ks->done = 1;
+        atomicExch(a.wk[r].err, -7);
+      } else {
+        active = 1;
+      }
+    }
+  }
+  active = __any_sync(0xffffffffu, active);
+  if (threadIdx.x == 0) {
+    if (which == 1 && a.loop_iters) a.loop_iters[a.loop_id] += 1u;
+    cudaGraphSetConditional(a.cond, active ? 1u : 0u);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_lz_loop_ctl(const LzArgs& a, int which, cudaStream_t st) {
+  lz_loop_ctl<<<1, 32, 0, st>>>(a, which);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st) {
   dim3 grid(a.nblk, a.R);

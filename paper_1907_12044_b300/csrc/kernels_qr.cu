@@ -667,9 +667,18 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
 cudaError_t launch_row_qr(int dir, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
                           int blocks_per_r, double rtol, int dbg_n, int dbg_m, cudaStream_t st) {
   int B = blocks_per_r < 1 ? 1 : blocks_per_r;
-  void* args[] = {&dir, &site, (void*)&sd, (void*)&wk, &N_sites, &B, &rtol, &dbg_n, &dbg_m};
-  dim3 grid(R * B), block(QT);
-  return cudaLaunchCooperativeKernel((const void*)bqr_kernel, grid, block, args, 0, st);
+  // co-resident blocks (the group barrier waits on every block of a realisation); launched with
+  // the cooperative attribute so that the launch can also be captured into a CUDA graph
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.gridDim = dim3(R * B);
+  cfg.blockDim = dim3(QT);
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bqr_kernel, dir, site, sd, wk, N_sites, B, rtol, dbg_n, dbg_m);
 }
 
 int qr_max_coresident_blocks(int device) {

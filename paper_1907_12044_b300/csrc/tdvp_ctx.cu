@@ -73,6 +73,19 @@ struct tdvp_ctx {
   int l_split = -1, r_split = -1;
   int prof = 0;
   int krylov_mode = TDVP_KRYLOV_ADAPTIVE;
+  // CUDA-graph execution of whole steps (TDVP_OPT_GRAPH)
+  int graph_on = 0;
+  bool capturing = false;
+  cudaStream_t body_st = nullptr;      // captures the body of each Lanczos while-node
+  cudaStream_t cap_st = nullptr;       // captures the step
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double> gkey;            // configuration the graph was captured for
+  unsigned* d_loop_iters = nullptr;    // [loop] body executions since the last read
+  int loop_cap = 0, loop_n = 0;
+  std::vector<int> loop_body_launches; // kernels per body execution of each loop
+  long long graph_outer_launches = 0;  // kernels of one replay outside the loops
+  int graph_nc = 0;                    // a replayed solve stopped at kmax above the tolerance
   std::vector<cudaEvent_t> ev;   // pairs
   std::vector<int> ev_cat;
   size_t ev_used = 0;
@@ -202,6 +215,15 @@ void add_op(std::vector<double>& T, int Wr, int dd, int wl, int wr, const std::v
   for (int q = 0; q < dd * dd; ++q) base[q] += coef * op[q];
 }
 
+// drop a captured step graph (its shapes, options or tables may no longer hold)
+void graph_reset(tdvp_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->gexec = nullptr;
+  ctx->graph = nullptr;
+  ctx->gkey.clear();
+}
+
 }  // namespace
 
 // --------------------------------------------------------------------------------------------- ABI
@@ -255,6 +277,10 @@ void tdvp_destroy(tdvp_ctx* ctx) {
   cudaFree(ctx->d_mlp_v);
   cudaFree(ctx->d_log);
   cudaFree(ctx->d_log_count);
+  graph_reset(ctx);
+  if (ctx->body_st) cudaStreamDestroy(ctx->body_st);
+  if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
+  cudaFree(ctx->d_loop_iters);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
 }
@@ -263,6 +289,7 @@ const char* tdvp_last_error(const tdvp_ctx* ctx) { return ctx ? ctx->err.c_str()
 
 int tdvp_build_mpo(tdvp_ctx* ctx, int r, const tdvp_fh_params* p) {
   if (!ctx) return TDVP_ERR_INVALID_ARG;
+  graph_reset(ctx);
   if (r < 0 || r >= ctx->R || !p || p->n_el < 1 || !p->E || !p->J || !p->n_modes || !p->el_order)
     return fail(ctx, TDVP_ERR_INVALID_ARG, "build_mpo: bad arguments");
   CK(cudaSetDevice(ctx->dev));
@@ -551,6 +578,7 @@ int split_for(tdvp_ctx* ctx, const Views& v, int op, int site, int M, int Nn, in
 int g_op(tdvp_ctx* ctx, const Views& v, int op, int site, int M, int Nn, int nb) {
   const int S = split_for(ctx, v, op, site, M, Nn, nb);
   LAUNCHC(TDVP_CAT_GEMM, launch_gemm(op, site, v.sd, v.wk, v.R, ctx->N, M, Nn, nb, S, ctx->st));
+  if (S > 1) ctx->stats.kernel_launches++;     // the split-K reduction
   if (ctx->prof) ctx->stats.prof_flops[TDVP_CAT_GEMM] += gemm_flops(ctx, v, op, site);
   return TDVP_OK;
 }
@@ -763,11 +791,92 @@ int nblk_for(long long n) {
 // exp(i theta H) applied to the start vector `src` (0 = x, 1 = site tensor, 2 = bond) with
 // H = H[site] (kind 0) or the zero-site H0 of bond (site, site+1) (kind 1); the result goes to
 // `dst` (1 = site tensor, 2 = bond, 3 = w).  Returns TDVP_OK or an error; sets *notconv.
-int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
-         int* notconv, int prec = TDVP_PREC_FP64) {
+// The matvec of one Lanczos iteration (site or bond, FP64 or tensor cores).
+int lanczos_matvec(tdvp_ctx* ctx, const Views& v, int kind, int site, int prec, int split) {
+  if (prec != TDVP_PREC_FP64) {
+    if (kind == 0) return matvec_site_tc(ctx, v, site, split);
+    return matvec_bond_tc(ctx, v, site, split);
+  }
+  if (kind == 0) return matvec_site(ctx, v, site, OP_MV1);
+  return matvec_bond(ctx, v, site);
+}
+
+// Lanczos exponential while a step is being captured into a CUDA graph: the iterations become
+// the body of a conditional while node (condition default 1 at every launch, then set by
+// lz_loop_ctl at the end of each body run), the iteration index lives on the device, the
+// convergence tests start from the device copy of the previous Krylov dimension (or every k, or
+// at the learned prediction), and results, counters and failures stay on the device until the
+// host reads them after the replays.
+int expm_graph(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
+               int prec) {
   const Dims m = maxdims(ctx, site, v);
   const long long n = kind == 0 ? (long long)m.Dl * ctx->d[site] * m.Dr : (long long)m.Dr * m.Dr;
-  LzArgs a;
+  if (ctx->loop_n >= ctx->loop_cap) return fail(ctx, TDVP_ERR_STATE, "graph capture: too many Lanczos loops");
+  LzArgs a{};
+  a.sd = v.sd; a.wk = v.wk; a.R = v.R; a.N_sites = ctx->N; a.site = site; a.kind = kind;
+  a.src = src; a.dst = dst; a.theta = theta; a.tol = tol; a.kmax = ctx->kmax;
+  a.nblk = nblk_for(n); a.flags = v.flags;
+  a.mlp = (ctx->krylov_mode == TDVP_KRYLOV_LEARNED && ctx->mlp_ready) ? ctx->d_mlp : nullptr;
+  a.log = ctx->logging ? ctx->d_log : nullptr;
+  a.log_count = ctx->d_log_count;
+  a.log_cap = ctx->log_cap;
+  a.jcheck = ctx->check_every ? 1 : 0;
+  a.devj = 1;
+  a.loop_iters = ctx->d_loop_iters;
+  a.loop_id = ctx->loop_n++;
+  CK(cudaMemsetAsync(v.flags, 0, sizeof(int) * v.R, ctx->st));
+  const int split = prec == TDVP_PREC_TF32X3 ? 1 : 0;
+  int rc;
+  if (prec != TDVP_PREC_FP64 && (rc = prepare_tc_solve(ctx, v, kind, site, split))) return rc;
+  LAUNCHC(TDVP_CAT_LZVEC, launch_lz_start(a, ctx->st));
+  ctx->stats.kernel_launches++;     // two kernels
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(ctx->st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return fail(ctx, TDVP_ERR_STATE, "graph capture: stream not capturing");
+  CK(cudaGraphConditionalHandleCreate(&a.cond, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = a.cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(ctx->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  // the body: one iteration, captured from the second stream
+  CK(cudaStreamBeginCaptureToGraph(ctx->body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  const cudaStream_t main_st = ctx->st;
+  const long long before = ctx->stats.kernel_launches;
+  ctx->st = ctx->body_st;
+  rc = lanczos_matvec(ctx, v, kind, site, prec, split);
+  if (!rc) {
+    cudaError_t e = launch_lz_iter_pre(a, 0, ctx->st);
+    if (e == cudaSuccess) e = launch_lz_iter_post(a, 0, ctx->st);
+    if (e == cudaSuccess) e = launch_lz_loop_ctl(a, 1, ctx->st);
+    if (e != cudaSuccess) rc = fail(ctx, TDVP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  ctx->st = main_st;
+  cudaGraph_t tmp = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(ctx->body_st, &tmp);
+  if (rc) return rc;
+  if (ee != cudaSuccess) return fail(ctx, TDVP_ERR_CUDA, cudaGetErrorString(ee));
+  // kernels of one body run: the matvec's (counted while capturing) + dots, two passes,
+  // tridiagonal, next vector, loop control
+  ctx->loop_body_launches.push_back((int)(ctx->stats.kernel_launches - before) + 6);
+  ctx->stats.kernel_launches = before;
+  LAUNCHC(TDVP_CAT_LZVEC, launch_lz_combine(a, ctx->st));
+  return TDVP_OK;
+}
+
+int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
+         int* notconv, int prec = TDVP_PREC_FP64) {
+  if (ctx->capturing) return expm_graph(ctx, v, kind, site, src, dst, theta, tol, prec);
+  const Dims m = maxdims(ctx, site, v);
+  const long long n = kind == 0 ? (long long)m.Dl * ctx->d[site] * m.Dr : (long long)m.Dr * m.Dr;
+  LzArgs a{};
   a.sd = v.sd; a.wk = v.wk; a.R = v.R; a.N_sites = ctx->N; a.site = site; a.kind = kind;
   a.src = src; a.dst = dst; a.theta = theta; a.tol = tol; a.kmax = ctx->kmax;
   a.nblk = nblk_for(n); a.flags = v.flags;
@@ -785,6 +894,7 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
     if (rc0) return rc0;
   }
   LAUNCHC(TDVP_CAT_LZVEC, launch_lz_start(a, ctx->st));
+  ctx->stats.kernel_launches++;     // two kernels
   int j = 0, batch = guess, rc;
   bool all_done = false;
   while (j < ctx->kmax && !all_done) {
@@ -797,8 +907,9 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
       } else if ((rc = matvec_bond(ctx, v, site))) {
         return rc;
       }
-      LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));
-      LAUNCHC(TDVP_CAT_TRIDIAG, launch_lz_iter_post(a, j, ctx->st));
+      LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));      // three kernels
+      LAUNCHC(TDVP_CAT_TRIDIAG, launch_lz_iter_post(a, j, ctx->st));   // two kernels
+      ctx->stats.kernel_launches += 3;
       ctx->stats.matvecs += v.R;
     }
     CK(cudaMemcpyAsync(ctx->h_flags + v.r0, v.flags, sizeof(int) * v.R, cudaMemcpyDeviceToHost, ctx->st));
@@ -832,9 +943,11 @@ int check_device_errors(tdvp_ctx* ctx) {
     if (ctx->h_err[r] != 0) {
       const int code = ctx->h_err[r];
       cudaMemsetAsync(ctx->d_err, 0, sizeof(int) * ctx->R, ctx->st);
-      return fail(ctx, code == -5 ? TDVP_ERR_DEVICE_TIMEOUT : (code == -6 ? TDVP_ERR_NAN : TDVP_ERR_INVALID_ARG),
+      return fail(ctx, code == -5 ? TDVP_ERR_DEVICE_TIMEOUT : ((code == -6 || code == -7) ? TDVP_ERR_NAN : TDVP_ERR_INVALID_ARG),
                   code == -5 ? "device barrier timed out"
-                             : (code == -6 ? "gauge-shift QR met a non-positive Gram pivot" : "device kernel rejected its sizes"));
+                  : code == -6 ? "gauge-shift QR met a non-positive Gram pivot"
+                  : code == -7 ? "Lanczos: non-finite value or unsupported exponent"
+                               : "device kernel rejected its sizes");
     }
   return TDVP_OK;
 }
@@ -943,12 +1056,113 @@ bool all_ready(tdvp_ctx* ctx) {
   return true;
 }
 
+// One TDVP-PS step of every realisation (Eq. ps_trotter): left-to-right half sweep with tau/2,
+// the last site with tau, right-to-left half sweep with tau/2.
+int enqueue_step(tdvp_ctx* ctx, const Views& v, double tau, double tol, int P, int* nc) {
+  const int N = ctx->N;
+  int rc;
+  ctx->l_site = ctx->r_site = -1;
+  if (N == 1) return expm(ctx, v, 0, 0, 1, 1, -tau, tol, nc, P);
+  for (int i = 0; i < N - 1; ++i) {
+    if ((rc = expm(ctx, v, 0, i, i == 0 ? 1 : 0, 1, -0.5 * tau, tol, nc, P))) return rc;
+    if ((rc = gauge_qr(ctx, v, i, 0))) return rc;
+    if ((rc = env_left(ctx, v, i))) return rc;
+    if ((rc = expm(ctx, v, 1, i, 2, 2, 0.5 * tau, tol, nc, P))) return rc;
+    const Dims m = maxdims(ctx, i + 1, v);
+    if ((rc = g_op(ctx, v, OP_ABS_L, i, m.Dl, ctx->d[i + 1] * m.Dr, 1))) return rc;
+  }
+  if ((rc = expm(ctx, v, 0, N - 1, 0, 1, -tau, tol, nc, P))) return rc;
+  for (int i = N - 1; i >= 1; --i) {
+    if ((rc = gauge_qr(ctx, v, i, 1))) return rc;
+    if ((rc = env_right(ctx, v, i))) return rc;
+    if ((rc = expm(ctx, v, 1, i - 1, 2, 2, 0.5 * tau, tol, nc, P))) return rc;
+    const Dims m = maxdims(ctx, i - 1, v);
+    if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
+    if ((rc = expm(ctx, v, 0, i - 1, 0, 1, -0.5 * tau, tol, nc, P))) return rc;
+  }
+  return TDVP_OK;
+}
+
+// n_steps replays of one captured step.  The graph is captured once per configuration (dt,
+// tolerance, precision, Krylov mode and options) and kept until a state or option change.
+int graph_steps(tdvp_ctx* ctx, const Views& v, double tau, double tol, int P, int n_steps) {
+  const std::vector<double> key = {tau, tol, (double)P, (double)ctx->krylov_mode, (double)ctx->check_every,
+                                   (double)ctx->mlp_ready, (double)ctx->logging, (double)ctx->log_cap};
+  if (!ctx->gexec || ctx->gkey != key) {
+    graph_reset(ctx);
+    if (!ctx->body_st) CK(cudaStreamCreateWithFlags(&ctx->body_st, cudaStreamNonBlocking));
+    const int need = 4 * ctx->N + 8;
+    if (ctx->loop_cap < need) {
+      cudaFree(ctx->d_loop_iters);
+      ctx->d_loop_iters = nullptr;
+      ctx->loop_cap = 0;
+      CK(cudaMalloc(&ctx->d_loop_iters, sizeof(unsigned) * need));
+      ctx->loop_cap = need;
+    }
+    CK(cudaMemsetAsync(ctx->d_loop_iters, 0, sizeof(unsigned) * ctx->loop_cap, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->loop_n = 0;
+    ctx->loop_body_launches.clear();
+    // captured on a private stream (the caller's may be the legacy default stream, which cannot
+    // be captured); the graph is then launched on the caller's stream
+    if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+    const long long before = ctx->stats.kernel_launches;
+    const cudaStream_t user_st = ctx->st;
+    ctx->st = ctx->cap_st;
+    cudaError_t e = cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { ctx->st = user_st; return fail(ctx, TDVP_ERR_CUDA, cudaGetErrorString(e)); }
+    ctx->capturing = true;
+    int nc = 0;
+    int rc = enqueue_step(ctx, v, tau, tol, P, &nc);
+    ctx->capturing = false;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(ctx->st, &g);
+    ctx->st = user_st;
+    ctx->graph_outer_launches = ctx->stats.kernel_launches - before;
+    ctx->stats.kernel_launches = before;
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(ctx, TDVP_ERR_CUDA, cudaGetErrorString(e));
+    ctx->graph = g;
+    CK(cudaGraphInstantiate(&ctx->gexec, g, 0));
+    ctx->gkey = key;
+  }
+  // device counters of the Krylov solves start from zero
+  for (int r = v.r0; r < v.r0 + v.R; ++r)
+    CK(cudaMemsetAsync(&ctx->h_work[r].ks->dim_sum, 0, sizeof(long long) + 4 * sizeof(int), ctx->st));
+  for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+  // launches and Krylov statistics from the device counters
+  std::vector<unsigned> iters(ctx->loop_n);
+  if (ctx->loop_n) {
+    CK(cudaMemcpyAsync(iters.data(), ctx->d_loop_iters, sizeof(unsigned) * ctx->loop_n, cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaMemsetAsync(ctx->d_loop_iters, 0, sizeof(unsigned) * ctx->loop_n, ctx->st));
+  }
+  struct { long long dim_sum; int dim_max, solves, nc_count, pad; } kc;
+  long long launches = ctx->graph_outer_launches * n_steps;
+  for (int q = 0; q < ctx->loop_n; ++q) launches += (long long)iters[q] * ctx->loop_body_launches[q];
+  for (int r = v.r0; r < v.r0 + v.R; ++r) {
+    CK(cudaMemcpyAsync(&kc, &ctx->h_work[r].ks->dim_sum, sizeof(kc), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->stats.krylov_dim_sum += kc.dim_sum;
+    ctx->stats.krylov_dim_max = std::max(ctx->stats.krylov_dim_max, kc.dim_max);
+    ctx->stats.krylov_solves += kc.solves;
+    ctx->stats.not_converged += kc.nc_count;
+    if (kc.nc_count) ctx->graph_nc = 1;
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->stats.kernel_launches += launches;
+  ctx->stats.host_syncs += 1;
+  ctx->l_site = ctx->r_site = -1;
+  return TDVP_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site) {
   if (!ctx) return TDVP_ERR_INVALID_ARG;
+  graph_reset(ctx);
   if (r < 0 || r >= ctx->R || D < 1 || D > 256) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps: bad r or D");
   if (!ctx->rh[r].mpo) return fail(ctx, TDVP_ERR_STATE, "init_mps: build_mpo first");
   if (exciton_site < 0 || exciton_site >= ctx->n_el) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps: bad exciton site");
@@ -990,6 +1204,7 @@ int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site) {
 
 int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const double* re_im) {
   if (!ctx) return TDVP_ERR_INVALID_ARG;
+  graph_reset(ctx);
   if (r < 0 || r >= ctx->R || !bond_dims || !re_im) return fail(ctx, TDVP_ERR_INVALID_ARG, "init_mps_tensors: bad args");
   if (!ctx->rh[r].mpo) return fail(ctx, TDVP_ERR_STATE, "init_mps_tensors: build_mpo first");
   CK(cudaSetDevice(ctx->dev));
@@ -1025,6 +1240,7 @@ int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const doub
     a.sd = v.sd; a.wk = v.wk; a.R = 1; a.N_sites = N; a.site = 0; a.kind = 0; a.src = 1; a.dst = 1;
     a.kmax = ctx->kmax; a.nblk = nblk_for((long long)m.Dl * ctx->d[0] * m.Dr); a.flags = v.flags;
     LAUNCH(launch_lz_start(a, ctx->st));
+    ctx->stats.kernel_launches++;
     LAUNCH(launch_copy_vec(1, 0, v.sd, v.wk, 1, N, m.Dl * ctx->d[0] * m.Dr, ctx->st));
   }
   ctx->l_site = ctx->r_site = -1;
@@ -1051,36 +1267,22 @@ int tdvp_ps_step(tdvp_ctx* ctx, double dt_fs, int n_steps, int precision, int kr
   const double tau = dt_fs * kPhasePerCmFs;
   int rc, nc = 0;
   const int P = precision;
-  for (int step = 0; step < n_steps; ++step) {
-    ctx->l_site = ctx->r_site = -1;
-    if (N == 1) {
-      if ((rc = expm(ctx, v, 0, 0, 1, 1, -tau, krylov_tol, &nc, P))) return rc;
-    } else {
-      for (int i = 0; i < N - 1; ++i) {
-        if ((rc = expm(ctx, v, 0, i, i == 0 ? 1 : 0, 1, -0.5 * tau, krylov_tol, &nc, P))) return rc;
-        if ((rc = gauge_qr(ctx, v, i, 0))) return rc;
-        if ((rc = env_left(ctx, v, i))) return rc;
-        if ((rc = expm(ctx, v, 1, i, 2, 2, 0.5 * tau, krylov_tol, &nc, P))) return rc;
-        const Dims m = maxdims(ctx, i + 1, v);
-        if ((rc = g_op(ctx, v, OP_ABS_L, i, m.Dl, ctx->d[i + 1] * m.Dr, 1))) return rc;
-      }
-      if ((rc = expm(ctx, v, 0, N - 1, 0, 1, -tau, krylov_tol, &nc, P))) return rc;
-      for (int i = N - 1; i >= 1; --i) {
-        if ((rc = gauge_qr(ctx, v, i, 1))) return rc;
-        if ((rc = env_right(ctx, v, i))) return rc;
-        if ((rc = expm(ctx, v, 1, i - 1, 2, 2, 0.5 * tau, krylov_tol, &nc, P))) return rc;
-        const Dims m = maxdims(ctx, i - 1, v);
-        if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
-        if ((rc = expm(ctx, v, 0, i - 1, 0, 1, -0.5 * tau, krylov_tol, &nc, P))) return rc;
-      }
+  if (ctx->graph_on && !ctx->prof && n_steps > 0) {
+    if ((rc = graph_steps(ctx, v, tau, krylov_tol, P, n_steps))) return rc;
+  } else {
+    for (int step = 0; step < n_steps; ++step) {
+      if ((rc = enqueue_step(ctx, v, tau, krylov_tol, P, &nc))) return rc;
     }
-    ctx->stats.steps++;
-    ctx->stats.site_updates += (long long)(2 * N - 1) * ctx->R;
   }
+  ctx->stats.steps += n_steps;
+  ctx->stats.site_updates += (long long)(2 * N - 1) * ctx->R * n_steps;
   if ((rc = check_device_errors(ctx))) return rc;
   if ((rc = collect_tri_counts(ctx))) return rc;
   if (ctx->prof && (rc = prof_collect(ctx))) return rc;
-  if (nc) return fail(ctx, TDVP_ERR_KRYLOV_NOT_CONVERGED, "some Lanczos solve stopped at kmax above the tolerance");
+  if (nc || ctx->graph_nc) {
+    ctx->graph_nc = 0;
+    return fail(ctx, TDVP_ERR_KRYLOV_NOT_CONVERGED, "some Lanczos solve stopped at kmax above the tolerance");
+  }
   return TDVP_OK;
 }
 
@@ -1418,6 +1620,7 @@ int tdvp_controller_train(tdvp_ctx* ctx, int epochs, int batch, float lr, float*
 
 int tdvp_autotune(tdvp_ctx* ctx) {
   if (!ctx) return TDVP_ERR_INVALID_ARG;
+  graph_reset(ctx);
   if (!all_ready(ctx)) return fail(ctx, TDVP_ERR_STATE, "autotune: every realisation needs build_mpo and init");
   CK(cudaSetDevice(ctx->dev));
   const Views v = all_views(ctx);
@@ -1510,6 +1713,7 @@ int tdvp_autotune(tdvp_ctx* ctx) {
 
 int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
   if (!ctx) return TDVP_ERR_INVALID_ARG;
+  graph_reset(ctx);
   switch (option) {
     case TDVP_OPT_RANK_RTOL:
       if (!(value > 0.0 && value < 1.0)) return fail(ctx, TDVP_ERR_INVALID_ARG, "rank rtol must be in (0, 1)");
@@ -1517,6 +1721,9 @@ int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
       return TDVP_OK;
     case TDVP_OPT_KRYLOV_CHECK_ALL:
       ctx->check_every = value != 0.0 ? 1 : 0;
+      return TDVP_OK;
+    case TDVP_OPT_GRAPH:
+      ctx->graph_on = value != 0.0 ? 1 : 0;
       return TDVP_OK;
     case TDVP_OPT_QR_KERNEL: {
       const int c = (int)value;

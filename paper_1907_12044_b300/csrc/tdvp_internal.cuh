@@ -92,8 +92,11 @@ struct KState {
   int notconv;                 // stopped at kcap above tolerance
   int status;                  // 0 ok, TDVP_ERR_NAN ...
   int kpred;                   // Krylov dimension predicted by the learned controller (0: none)
-  int pad;
+  int jcur;                    // iteration index of a device-driven (graph) loop
   float feat[MLP_NIN];         // controller features of the solve in flight
+  // counters of device-driven solves (read and cleared by the host after a graph replay)
+  long long dim_sum;
+  int dim_max, solves, nc_count, pad2;
 };
 
 // Per-realisation work buffers.
@@ -188,6 +191,11 @@ struct LzArgs {
   float* log;       // solve log rows [8 features, k] (null: no logging)
   unsigned* log_count;
   long long log_cap;
+  // device-driven loop (CUDA graph with a conditional while node per solve)
+  int devj;                          // 1: the iteration index comes from KState::jcur
+  cudaGraphConditionalHandle cond;   // loop condition set by lz_loop_ctl
+  unsigned* loop_iters;              // [loop_id] body executions, for launch accounting
+  int loop_id;
 };
 
 // Controller inference by the first MLP_NH threads of a block; y is returned to every thread.
@@ -226,6 +234,10 @@ cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st);
 cudaError_t launch_lz_iter_pre(const LzArgs& a, int j, cudaStream_t st);   // orthogonalisation
 cudaError_t launch_lz_iter_post(const LzArgs& a, int j, cudaStream_t st);  // tridiagonal exp, next vector
 cudaError_t launch_lz_combine(const LzArgs& a, cudaStream_t st);
+// loop control of a device-driven solve: which = 0 before the loop (condition = some solve not
+// done), 1 at the end of the body (advance the iteration index of unfinished solves, count the
+// body execution, condition = some solve not done)
+cudaError_t launch_lz_loop_ctl(const LzArgs& a, int which, cudaStream_t st);
 
 // QR of the gauge shift (dir 0: left-to-right on site tensor via transpose scratch, result
 // L = Q in A[site], D = R in bond; dir 1: right-to-left LQ in place, D = L-factor in bond;
