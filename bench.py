@@ -162,6 +162,7 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
     eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
+    eng.autotune()          # QR launch shape per gauge-shift shape (both arms)
     pops = [eng.observables(0)[0]]
     if learned:
         eng.controller_logging(1 << 20)
@@ -375,6 +376,7 @@ def run_e2e(args, p):
     eng.init_mps(0, args.D, p.exciton_site)
     torch.cuda.synchronize()
     upload_s = time.perf_counter() - t0
+    eng.autotune()
     learned = args.precision != "fp64" and not args.no_learned
     graph = args.precision != "fp64" and not args.no_graph and args.warmup >= 1
     if learned:

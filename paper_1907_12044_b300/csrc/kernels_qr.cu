@@ -229,18 +229,22 @@ struct Scratch {
 // Q_t (residuals only shrink) and the rounding differences are O(eps ||x||), every later row is
 // dropped under the exact rule as well.  The completions are then built one per group barrier:
 // rows are kept unnormalised with their squared norms (so no row another block reads is
-// rewritten), every block keeps its own copy of all m column sums sum_t |Q_t[c]|^2 and picks
-// the next unit vector itself.  A completion is e_p minus its projection with the exact
+// rewritten) and every block picks the next unit vector itself, scanning forward from the
+// previous one.  A completion is e_p minus its projection with the exact
 // first-pass coefficients conj(Q_t[p]); being at distance >= 1/2 from the span (or the farthest
 // unit vector), one pass leaves it orthogonal to O(eps).  Finally rows are normalised and the
 // R coefficients of the dropped rows against the completions are taken from the backed-up rows.
 // Returns 1 when rows J0..n-1 are done, 0 when the tail test failed (rows restored), -1 when a
 // group barrier gave up.
-constexpr int TAIL_CQ = (PB * QR_NMAX - QR_NMAX) * 2;   // doubles of the column-sum copy in Hs
+
+constexpr int TAIL_KB = 8;   // completions per group barrier in the tail
 
 __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J0, int j0, int pend, int b, int B,
                        int gw, int nwarps, int c0, int c1, double thresh, zc* Hs, double* red, double* ens,
                        int* flag) {
+  __shared__ zc Gb[TAIL_KB][TAIL_KB], Lb[TAIL_KB][TAIL_KB], Li[TAIL_KB][TAIL_KB];
+  __shared__ zc Yb[QT];
+  __shared__ int tflag[TAIL_KB + 1];
   const int n = J.n, m = J.m, Tn = n - J0, lane = threadIdx.x % 32;
   zc* X = J.X;
   zc* BK = W.qtail;                                     // [n][m] backup of rows J0..n-1
@@ -260,18 +264,22 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
       if (lane == 0) HT[(long long)a * n + t] = s;
     }
     if (!group_sync(W, B)) return -1;
-    for (int a0 = 0; a0 < Tn; a0 += PB) {
-      const int nb = min(PB, Tn - a0);
+    // all tail rows in one slab pass when their coefficients fit in Hs, else in chunks
+    const int chunk = J0 > 0 ? max(1, min(Tn, (PB * QR_NMAX) / J0)) : Tn;
+    for (int a0 = 0; a0 < Tn; a0 += chunk) {
+      const int nb = min(chunk, Tn - a0);
+      if (a0 > 0) __syncthreads();
       for (int e = threadIdx.x; e < nb * J0; e += QT) Hs[e] = __ldcg(HT + (long long)(a0 + e / J0) * n + e % J0);
       __syncthreads();
       slab_update(X, m, J0 + a0, nb, J0, Hs, J0, c0, c1);
     }
     if (pass == 1) {
-      for (int a = 0; a < Tn; ++a) {
+      // squared residual norms over this block's columns, one warp per row
+      for (int a = threadIdx.x / 32; a < Tn; a += NW) {
         double s = 0;
-        for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(X[(long long)(J0 + a) * m + c]);
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) TPN[(long long)a * B + b] = s;
+        for (int c = c0 + lane; c < c1; c += 32) s += zabs2(X[(long long)(J0 + a) * m + c]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) TPN[(long long)a * B + b] = s;
       }
     }
     if (!group_sync(W, B)) return -1;
@@ -293,52 +301,204 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
       return group_sync(W, B) ? 0 : -1;
     }
   }
-  // completions, one group barrier each
-  double* cq = reinterpret_cast<double*>(Hs + QR_NMAX);  // all m column sums (this block's copy)
-  for (int c = threadIdx.x; c < m; c += QT) cq[c] = __ldcg(W.colsq + c);
-  __syncthreads();
-  for (int a = 0; a < Tn; ++a) {
+  // completions, one group barrier each.  The first qualifying column only moves forward: a
+  // column at distance < 1/2 stays so (the sums only grow) and a completed column drops to
+  // distance 0, so the scan resumes after the previous choice, one warp per candidate column.
+  // A warp loads its column of every earlier row in one round of loads, together with the
+  // previous row's norm partials: the same values give the column's distance and, scaled, the
+  // projection coefficients conj(Q_t[p]) if it is chosen.  Only when no column ahead qualifies
+  // are all columns searched for the farthest one.
+  const int wid = threadIdx.x / 32;
+  int pnext = 0;
+  int a = 0;
+  bool prev_single = false;   // the previous row is a single completion whose norm is pending
+  while (true) {
     const int j = J0 + a;
-    // next unit vector: the first column at distance >= 1/2 (1 - cq >= 1/4), else the farthest
-    {
-      int first = 0x7fffffff, besti = 0x7fffffff;
+    // 1 / squared norm of a pending single completion (row j - 1), from its norm partials
+    double einv_prev = 0.0;
+    if (prev_single) {
+      const double en2 = sum_over_blocks(S.Pn + ((a - 1) & 1) * B, B);
+      einv_prev = en2 > 0.0 ? 1.0 / en2 : 0.0;
+      if (threadIdx.x == 0) { ens[a - 1] = en2; ens[QR_NMAX + a - 1] = einv_prev; }
+    }
+    if (a >= Tn) break;
+    // coefficient scale of row t: 1 for rows < J0 and batch completions (normalised),
+    // 1/|x_t|^2 for single completions (stored unnormalised)
+    auto scale = [&](int t) -> double {
+      return t < J0 ? 1.0 : ((prev_single && t == j - 1) ? einv_prev : ens[QR_NMAX + t - J0]);
+    };
+    // squared norm of stored row t (1 for normalised rows)
+    auto rnorm2 = [&](int t) -> double {
+      return t < J0 ? 1.0 : ((prev_single && t == j - 1) ? 1.0 / einv_prev : ens[t - J0]);
+    };
+    const int ldc = j;
+    int KB = min(TAIL_KB, Tn - a);
+    if ((NW + KB) * ldc > PB * QR_NMAX) KB = max(1, (PB * QR_NMAX) / ldc - NW);
+    if ((NW + KB) * ldc > PB * QR_NMAX) KB = 0;
+    zc* cv = Hs;                    // [NW][ldc] this round's candidate columns, as coefficients
+    zc* bslot = Hs + NW * ldc;      // [KB][ldc] accepted candidates, in column order
+    // scan forward for up to max(KB, 1) qualifying columns
+    const int want = max(KB, 1);
+    int nf = 0, fw0 = -1;
+    for (int c0s = pnext; c0s < m && nf < want; c0s += NW) {
+      const int c = c0s + wid;
+      int ok = 0;
+      if (c < m) {
+        double s = 0;
+        for (int t = lane; t < j; t += 32) {
+          const zc v = __ldcg(X + (long long)t * m + c);
+          const double sc = scale(t);
+          cv[wid * ldc + t] = zscale(zconj(v), sc);
+          if (t >= J0) s += zabs2(v) * sc;
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        ok = (1.0 - (__ldcg(W.colsq + c) + s)) >= 0.25;
+      }
+      if (lane == 0) flag[2 + wid] = ok ? c : 0x7fffffff;
+      __syncthreads();
+      // accept qualifying columns of this round in order (the same decisions in every thread)
+      int take[NW];
+      int nt = 0;
+      for (int w = 0; w < NW; ++w)
+        if (flag[2 + w] != 0x7fffffff && nf + nt < want) take[nt++] = w;
+      if (KB > 0) {
+        for (int q2 = 0; q2 < nt; ++q2) {
+          for (int t = threadIdx.x; t < j; t += QT) bslot[(nf + q2) * ldc + t] = cv[take[q2] * ldc + t];
+          if (threadIdx.x == 0) tflag[nf + q2] = flag[2 + take[q2]];
+        }
+      } else if (nt > 0 && nf == 0) {
+        fw0 = take[0];
+        if (threadIdx.x == 0) tflag[0] = flag[2 + take[0]];
+      }
+      nf += nt;
+      __syncthreads();
+    }
+    if (nf == 0) {
+      // no column ahead at distance >= 1/2: the farthest column (first on ties), single
+      int besti = 0x7fffffff;
       double bestv = -2.0;
-      for (int c = threadIdx.x; c < m; c += QT) {
-        const double dist = 1.0 - cq[c];
-        if (dist >= 0.25 && c < first) first = c;
-        if (dist > bestv || (dist == bestv && c < besti)) { bestv = dist; besti = c; }
+      for (int c = wid; c < m; c += NW) {
+        double s = 0;
+        for (int t = J0 + lane; t < j; t += 32) s += zabs2(__ldcg(X + (long long)t * m + c)) * scale(t);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double dv = 1.0 - (__ldcg(W.colsq + c) + s);
+        if (dv > bestv || (dv == bestv && c < besti)) { bestv = dv; besti = c; }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const int f2 = __shfl_xor_sync(0xffffffffu, first, o);
-        const double v2 = __shfl_xor_sync(0xffffffffu, bestv, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, besti, o);
-        first = min(first, f2);
-        if (v2 > bestv || (v2 == bestv && i2 < besti)) { bestv = v2; besti = i2; }
-      }
-      if (lane == 0) { red[threadIdx.x / 32] = bestv; flag[threadIdx.x / 32 + 2] = first; flag[threadIdx.x / 32 + 2 + NW] = besti; }
+      if (lane == 0) { red[wid] = bestv; flag[2 + wid] = besti; }
       __syncthreads();
       if (threadIdx.x == 0) {
-        int f = flag[2], bi = flag[2 + NW];
         double bv = red[0];
-        for (int w = 1; w < NW; ++w) {
-          f = min(f, flag[2 + w]);
-          if (red[w] > bv || (red[w] == bv && flag[2 + NW + w] < bi)) { bv = red[w]; bi = flag[2 + NW + w]; }
-        }
-        const int p = f < 0x7fffffff ? f : (bi < 0x7fffffff ? bi : 0);
-        flag[1] = min(max(p, 0), m - 1);
+        int bi = flag[2];
+        for (int w = 1; w < NW; ++w)
+          if (red[w] > bv || (red[w] == bv && flag[2 + w] < bi)) { bv = red[w]; bi = flag[2 + w]; }
+        tflag[0] = min(max(bi < 0x7fffffff ? bi : 0, 0), m - 1);
       }
       __syncthreads();
+      for (int t = threadIdx.x; t < j; t += QT) cv[t] = zscale(zconj(__ldcg(X + (long long)t * m + tflag[0])), scale(t));
+      fw0 = 0;
+      nf = 1;
+      __syncthreads();
     }
-    const int p = flag[1];
-    // x_j = e_p - sum_t conj(Q_t[p]) Q_t with Q_t = X_t / sqrt(ens) for the (unnormalised) tail rows
-    for (int t = threadIdx.x; t < j; t += QT) {
-      const double s = t < J0 ? 1.0 : 1.0 / ens[t - J0];
-      Hs[t] = zscale(zconj(__ldcg(X + (long long)t * m + p)), s);
+    int K = 0;
+    if (nf >= 2 && KB >= 2) {
+      // Gram matrix of the projected unit vectors y_k = e_{p_k} - sum_t conj(Q_t[p_k]) Q_t:
+      // G_kl = delta_kl - sum_t conj(Q_t[p_k]) Q_t[p_l]; with the stored coefficients
+      // cv_k[t] = conj(Q_t[p_k]) / |x_t| this is delta_kl - sum_t cv_k[t] conj(cv_l[t]) |x_t|^2
+      const int Kc = nf;
+      for (int e2 = wid; e2 < Kc * (Kc + 1) / 2; e2 += NW) {
+        int kk = 0;
+        while ((kk + 1) * (kk + 2) / 2 <= e2) ++kk;
+        const int ll = e2 - kk * (kk + 1) / 2;
+        zc s2 = zmake(0, 0);
+        for (int t = lane; t < j; t += 32) {
+          const zc u = bslot[kk * ldc + t], v = bslot[ll * ldc + t];
+          s2 = zadd(s2, zscale(zmul(u, zconj(v)), rnorm2(t)));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          s2.x += __shfl_xor_sync(0xffffffffu, s2.x, o);
+          s2.y += __shfl_xor_sync(0xffffffffu, s2.y, o);
+        }
+        if (lane == 0) Gb[kk][ll] = zmake((kk == ll ? 1.0 : 0.0) - s2.x, -s2.y);
+      }
+      __syncthreads();
+      // Cholesky G = L L^H in warp 0; pivot k is the distance of p_k after the batch's earlier
+      // completions, so the batch stops at the first pivot below 1/4 (the exact rule would skip
+      // that column there)
+      if (threadIdx.x < 32) {
+        int kgood = Kc;
+        for (int jj = 0; jj < Kc; ++jj) {
+          const double sp = Gb[jj][jj].x;
+          if (!(sp >= 0.25)) { kgood = jj; break; }
+          const double d = sqrt(sp), inv = 1.0 / d;
+          for (int i = lane; i < Kc; i += 32)
+            Lb[i][jj] = (i < jj) ? zmake(0, 0) : (i == jj ? zmake(d, 0) : zscale(Gb[i][jj], inv));
+          __syncwarp();
+          const int Tt = Kc - jj - 1;
+          for (int e2 = lane; e2 < Tt * Tt; e2 += 32) {
+            const int i = jj + 1 + e2 / Tt, k2 = jj + 1 + e2 % Tt;
+            if (k2 <= i) Gb[i][k2] = zfms(Lb[i][jj], zconj(Lb[k2][jj]), Gb[i][k2]);
+          }
+          __syncwarp();
+        }
+        if (lane == 0) tflag[TAIL_KB] = kgood;
+      }
+      __syncthreads();
+      K = tflag[TAIL_KB];
     }
+    if (K >= 2) {
+      // Li = L^{-1} (lower triangular), one warp per column
+      for (int cc = wid; cc < K; cc += NW) {
+        if (lane == 0) Li[cc][cc] = zmake(1.0 / Lb[cc][cc].x, 0.0);
+        for (int i = 0; i < cc; ++i) if (lane == 0) Li[i][cc] = zmake(0, 0);
+        __syncwarp();
+        for (int i = cc + 1; i < K; ++i) {
+          zc s2 = zmake(0, 0);
+          for (int k2 = cc + lane; k2 < i; k2 += 32) s2 = zfma(Lb[i][k2], Li[k2][cc], s2);
+          for (int o = 16; o > 0; o >>= 1) {
+            s2.x += __shfl_xor_sync(0xffffffffu, s2.x, o);
+            s2.y += __shfl_xor_sync(0xffffffffu, s2.y, o);
+          }
+          if (lane == 0) Li[i][cc] = zscale(s2, -1.0 / Lb[i][i].x);
+          __syncwarp();
+        }
+      }
+      // y_k on this block's columns into rows j..j+K-1, then rows <- Li y (column by column)
+      for (long long e2 = threadIdx.x; e2 < (long long)K * (c1 - c0); e2 += QT) {
+        const int k2 = (int)(e2 / (c1 - c0)), c = c0 + (int)(e2 % (c1 - c0));
+        X[(long long)(j + k2) * m + c] = zmake(c == tflag[k2] ? 1.0 : 0.0, 0.0);
+      }
+      __syncthreads();
+      slab_update(X, m, j, K, j, bslot, ldc, c0, c1);
+      const int ccols = max(1, QT / K);
+      for (int cb = c0; cb < c1; cb += ccols) {
+        const int nc = min(ccols, c1 - cb);
+        for (int e2 = threadIdx.x; e2 < K * nc; e2 += QT) Yb[e2] = X[(long long)(j + e2 / nc) * m + cb + e2 % nc];
+        __syncthreads();
+        for (int e2 = threadIdx.x; e2 < K * nc; e2 += QT) {
+          const int k2 = e2 / nc, cl = e2 % nc;
+          zc v = zmake(0, 0);
+          for (int k3 = 0; k3 <= k2; ++k3) v = zfma(Li[k2][k3], Yb[k3 * nc + cl], v);
+          X[(long long)(j + k2) * m + cb + cl] = v;
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0)
+        for (int k2 = 0; k2 < K; ++k2) { ens[a + k2] = 1.0; ens[QR_NMAX + a + k2] = 1.0; }
+      pnext = tflag[K - 1] + 1;
+      a += K;
+      prev_single = false;
+      __syncthreads();
+      if (!group_sync(W, B)) return -1;
+      continue;
+    }
+    // single completion: x_j = e_p - sum_t conj(Q_t[p]) Q_t, norm over the blocks at the barrier
+    const int p = tflag[0];
+    const zc* hc = (KB > 0 && fw0 < 0) ? bslot : cv + (fw0 > 0 ? fw0 : 0) * ldc;
+    pnext = p + 1;
     zc* x = X + (long long)j * m;
     for (int c = c0 + threadIdx.x; c < c1; c += QT) x[c] = zmake(c == p ? 1.0 : 0.0, 0.0);
     __syncthreads();
-    slab_update(X, m, j, 1, j, Hs, j, c0, c1);
+    slab_update(X, m, j, 1, j, hc, ldc, c0, c1);
     {
       double s = 0;
       for (int c = c0 + threadIdx.x; c < c1; c += QT) s += zabs2(x[c]);
@@ -346,12 +506,10 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
       if (threadIdx.x == 0) S.Pn[(a & 1) * B + b] = zmake(s, 0.0);
     }
     if (!group_sync(W, B)) return -1;
-    const double en2 = sum_over_blocks(S.Pn + (a & 1) * B, B);
-    if (threadIdx.x == 0) ens[a] = en2;
-    const double inv = en2 > 0.0 ? 1.0 / en2 : 0.0;
-    for (int c = threadIdx.x; c < m; c += QT) cq[c] += zabs2(__ldcg(x + c)) * inv;
-    __syncthreads();
+    a += 1;
+    prev_single = true;
   }
+  __syncthreads();
   // normalise the completions on the slab
   for (int a = 0; a < Tn; ++a) {
     const double inv = ens[a] > 0.0 ? 1.0 / sqrt(ens[a]) : 0.0;
@@ -394,7 +552,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
   __shared__ zc sdot[NW];
   __shared__ double red[NW];
   __shared__ int flag[2 + 2 * NW];
-  __shared__ double ens[QR_NMAX];
+  __shared__ double ens[2 * QR_NMAX];   // tail rows: squared norms, then their reciprocals
   int tail_tries = 0;
   const int r = blockIdx.x / B, b = blockIdx.x % B;
   const SiteDev* sdr = sd + (long long)r * N_sites;
@@ -652,7 +810,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
       }
       if (!group_sync(W, B)) return;
       // after a dropped row, try to finish every later row as a completion in one go
-      if (!full && tail_tries < 2 && n - (j + 1) >= 2 && m <= TAIL_CQ) {
+      if (!full && tail_tries < 2 && n - (j + 1) >= 2) {
         ++tail_tries;
         const int rc = qr_tail(J, W, S, j + 1, j0, j0 + nb, b, B, gw, nwarps, c0, c1, thresh, Hs, red, ens, flag);
         if (rc < 0) return;

@@ -100,6 +100,16 @@ def test_qr_rank_deficient_matches_oracle(c1_random, qr_kernel):
     F[:, 5] = F[:, 2] * (0.5 - 1j)
     F[:, 17] = F[:, 3] + F[:, 9]
     cases.append(F)
+    # kept directions concentrated on a few rows of C: completing those unit vectors one after
+    # another pushes a later candidate below distance 1/2, so the rule skips it (row 5 for the
+    # rank-1 case, rows 5 and 8 for the rank-2 one)
+    v = np.zeros(64)
+    v[:6] = 1 / np.sqrt(6)
+    u = np.zeros(64)
+    u[3:9] = 1 / np.sqrt(6)
+    w1 = rng.normal(size=16) + 1j * rng.normal(size=16)
+    cases.append(np.outer(v, w1))
+    cases.append(np.outer(v, w1) + np.outer(u, rng.normal(size=16)))
     for C in cases:
         out = debug_qr_or_rejected(eng, qr_kernel, C)
         if out is None:
