@@ -255,7 +255,8 @@ int tdvp_autotune(tdvp_ctx* ctx);
  *   TDVP_OPT_KRYLOV_CHECK_ALL: 1 = test Lanczos convergence at every k, 0 (default) = from the
  *     last Krylov dimension of the same site minus 2 on.
  *   TDVP_OPT_QR_KERNEL: which kernel runs the gauge-shift QR.  -1 (default): the autotuned
- *     choice, else the cooperative-grid kernel; 0: the
+ *     choice, else the cooperative-grid kernel; -2: the cluster kernel with the largest cluster
+ *     the shape fits, else the cooperative-grid kernel; 0: the
  *     cooperative-grid kernel (blocked Gram-Schmidt with Cholesky-QR panels); 1, 2, 4, 8, 16: the
  *     cluster kernel with that many CTAs per realisation (a shape that does not fit its shared
  *     memory fails with TDVP_ERR_INVALID_ARG).  All compute the same decomposition.

@@ -223,19 +223,19 @@ struct Scratch {
 };
 
 // ---- rank-deficient tail ----
-// Taken after a dropped row j when every later row is dropped too.  With Q_t (t < J0 = j+1)
-// final, rows J0..n-1 are projected twice onto them (block Gram-Schmidt); if every residual is
-// <= thresh/2 then, since the exact process tests each later row against a superset of these
-// Q_t (residuals only shrink) and the rounding differences are O(eps ||x||), every later row is
-// dropped under the exact rule as well.  The completions are then built one per group barrier:
+// Taken after a dropped row j.  With Q_t (t < J0 = j+1) final, rows J0..n-1 are projected twice
+// onto them (block Gram-Schmidt); a row whose residual is <= thresh/2 is dropped under the exact
+// rule as well, since the exact process tests it against a superset of these Q_t (residuals only
+// shrink) and the rounding differences are O(eps ||x||).  The completions are then built one per group barrier:
 // rows are kept unnormalised with their squared norms (so no row another block reads is
 // rewritten) and every block picks the next unit vector itself, scanning forward from the
 // previous one.  A completion is e_p minus its projection with the exact
 // first-pass coefficients conj(Q_t[p]); being at distance >= 1/2 from the span (or the farthest
 // unit vector), one pass leaves it orthogonal to O(eps).  Finally rows are normalised and the
 // R coefficients of the dropped rows against the completions are taken from the backed-up rows.
-// Returns 1 when rows J0..n-1 are done, 0 when the tail test failed (rows restored), -1 when a
-// group barrier gave up.
+// Only the prefix of rows whose residual is <= thresh/2 is finished this way (a later row may
+// be kept); the rows after it are restored and return to the row path.  Returns the number of
+// rows finished (0: none, rows restored), -1 when a group barrier gave up.
 
 constexpr int TAIL_KB = 8;   // completions per group barrier in the tail
 
@@ -284,16 +284,22 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
     }
     if (!group_sync(W, B)) return -1;
   }
-  // tail test: every residual <= thresh/2 (the same sums in the same order in every block)
+  // rows certainly dropped: the prefix of rows whose residual is <= thresh/2 (the same sums in
+  // the same order in every block); later rows go back to the exact row path
+  int Tc;
   {
-    int bad = 0;
+    __shared__ int first_bad;
+    if (threadIdx.x == 0) first_bad = Tn;
+    __syncthreads();
     for (int a = threadIdx.x; a < Tn; a += QT) {
       double s = 0;
       for (int bb = 0; bb < B; ++bb) s += __ldcg(TPN + (long long)a * B + bb);
-      if (!(sqrt(s) <= 0.5 * thresh)) bad = 1;
+      if (!(sqrt(s) <= 0.5 * thresh)) atomicMin(&first_bad, a);
     }
-    bad = __syncthreads_or(bad);
-    if (bad) {
+    __syncthreads();
+    Tc = first_bad;
+    __syncthreads();
+    if (Tc == 0) {
       for (long long e = threadIdx.x; e < (long long)Tn * (c1 - c0); e += QT) {
         const int j = J0 + (int)(e / (c1 - c0)), c = c0 + (int)(e % (c1 - c0));
         X[(long long)j * m + c] = BK[(long long)j * m + c];
@@ -321,7 +327,7 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
       einv_prev = en2 > 0.0 ? 1.0 / en2 : 0.0;
       if (threadIdx.x == 0) { ens[a - 1] = en2; ens[QR_NMAX + a - 1] = einv_prev; }
     }
-    if (a >= Tn) break;
+    if (a >= Tc) break;
     // coefficient scale of row t: 1 for rows < J0 and batch completions (normalised),
     // 1/|x_t|^2 for single completions (stored unnormalised)
     auto scale = [&](int t) -> double {
@@ -332,7 +338,7 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
       return t < J0 ? 1.0 : ((prev_single && t == j - 1) ? 1.0 / einv_prev : ens[t - J0]);
     };
     const int ldc = j;
-    int KB = min(TAIL_KB, Tn - a);
+    int KB = min(TAIL_KB, Tc - a);
     if ((NW + KB) * ldc > PB * QR_NMAX) KB = max(1, (PB * QR_NMAX) / ldc - NW);
     if ((NW + KB) * ldc > PB * QR_NMAX) KB = 0;
     zc* cv = Hs;                    // [NW][ldc] this round's candidate columns, as coefficients
@@ -510,17 +516,28 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
     prev_single = true;
   }
   __syncthreads();
-  // normalise the completions on the slab
-  for (int a = 0; a < Tn; ++a) {
+  // normalise the completions on the slab, add them to the column sums the row path uses, and
+  // put the rows after them back as they were
+  for (int a = 0; a < Tc; ++a) {
     const double inv = ens[a] > 0.0 ? 1.0 / sqrt(ens[a]) : 0.0;
     zc* x = X + (long long)(J0 + a) * m;
     for (int c = c0 + threadIdx.x; c < c1; c += QT) x[c] = zscale(x[c], inv);
+  }
+  __syncthreads();
+  for (int c = c0 + threadIdx.x; c < c1; c += QT) {
+    double s = W.colsq[c];
+    for (int a = 0; a < Tc; ++a) s += zabs2(X[(long long)(J0 + a) * m + c]);
+    W.colsq[c] = s;
+  }
+  for (long long e = threadIdx.x; e < (long long)(Tn - Tc) * (c1 - c0); e += QT) {
+    const int j = J0 + Tc + (int)(e / (c1 - c0)), c = c0 + (int)(e % (c1 - c0));
+    X[(long long)j * m + c] = BK[(long long)j * m + c];
   }
   if (!group_sync(W, B)) return -1;
   // R rows of the dropped rows: against rows < J0 the two projection passes (plus the panel's
   // passes for rows the panel had already projected), against the completions the dot products
   // of the backed-up rows, zero on and above the diagonal
-  for (int e = gw; e < Tn * Tn; e += nwarps) {
+  for (int e = gw; e < Tc * Tn; e += nwarps) {
     const int a = e / Tn, a2 = e % Tn;
     const int j = J0 + a, t = J0 + a2;
     zc v = zmake(0, 0);
@@ -528,7 +545,7 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
     if (lane == 0) J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
   }
   if (b == 0) {
-    for (int e = threadIdx.x; e < Tn * J0; e += QT) {
+    for (int e = threadIdx.x; e < Tc * J0; e += QT) {
       const int a = e / J0, t = e % J0, j = J0 + a;
       zc v = zadd(__ldcg(HT1 + (long long)a * n + t), __ldcg(HT2 + (long long)a * n + t));
       if (j < pend && t < j0) {
@@ -538,7 +555,10 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
       J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
     }
   }
-  return 1;
+  // when the row path continues, the next panel rewrites the panel coefficients (S.H1, S.H2)
+  // and the next tail the row backup, which block 0 and the dot products above still read
+  if (Tc < Tn && !group_sync(W, B)) return -1;
+  return Tc;
 }
 
 __global__ void __launch_bounds__(QT)
@@ -591,8 +611,10 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
   const double fro2 = sum_over_blocks(S.Pn, B);
   const double thresh = rtol * sqrt(fro2);
 
-  for (int j0 = 0; j0 < n; j0 += PB) {
+  int jnext = n;
+  for (int j0 = 0; j0 < n; j0 = jnext) {
     const int nb = min(PB, n - j0);
+    jnext = j0 + nb;
     // ---- two block Gram-Schmidt passes against rows 0..j0-1 ----
     for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
       zc* Hb = pass ? S.H2 : S.H1;
@@ -810,11 +832,15 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
       }
       if (!group_sync(W, B)) return;
       // after a dropped row, try to finish every later row as a completion in one go
-      if (!full && tail_tries < 2 && n - (j + 1) >= 2) {
+      if (!full && tail_tries < 8 && n - (j + 1) >= 2) {
         ++tail_tries;
-        const int rc = qr_tail(J, W, S, j + 1, j0, j0 + nb, b, B, gw, nwarps, c0, c1, thresh, Hs, red, ens, flag);
-        if (rc < 0) return;
-        if (rc == 1) return;
+        const int done = qr_tail(J, W, S, j + 1, j0, j0 + nb, b, B, gw, nwarps, c0, c1, thresh, Hs, red, ens, flag);
+        if (done < 0) return;
+        if (j + 1 + done >= n) return;
+        if (done > 0) {
+          j += done;                       // rows up to j are final
+          if (j + 1 >= j0 + nb) { jnext = j + 1; break; }
+        }
       }
     }
   }

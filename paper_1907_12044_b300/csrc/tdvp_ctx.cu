@@ -730,6 +730,11 @@ bool cqr_fits(tdvp_ctx* ctx, int C, int m, int n) {
 int qr_mode(tdvp_ctx* ctx, int R, int m, int n) {
   if (ctx->qr_force == 0) return qr_grid_default(ctx, R, m);
   if (ctx->qr_force > 0) return -ctx->qr_force;
+  if (ctx->qr_force == -2) {
+    for (int C : {16, 8, 4, 2, 1})
+      if (cqr_fits(ctx, C, m, n)) return -C;
+    return qr_grid_default(ctx, R, m);
+  }
   auto it = ctx->qr_tuned.find(std::make_tuple(R, m, n));
   if (it != ctx->qr_tuned.end()) return it->second;
   return qr_grid_default(ctx, R, m);
@@ -1727,8 +1732,8 @@ int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
       return TDVP_OK;
     case TDVP_OPT_QR_KERNEL: {
       const int c = (int)value;
-      if ((double)c != value || !(c == -1 || c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || c == 16))
-        return fail(ctx, TDVP_ERR_INVALID_ARG, "QR kernel option must be -1, 0, 1, 2, 4, 8 or 16");
+      if ((double)c != value || !(c == -2 || c == -1 || c == 0 || c == 1 || c == 2 || c == 4 || c == 8 || c == 16))
+        return fail(ctx, TDVP_ERR_INVALID_ARG, "QR kernel option must be -2, -1, 0, 1, 2, 4, 8 or 16");
       if (c > 0 && !ctx->cqr_ok[c]) return fail(ctx, TDVP_ERR_INVALID_ARG, "cluster size not launchable on this device");
       ctx->qr_force = c;
       return TDVP_OK;

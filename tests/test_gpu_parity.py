@@ -110,6 +110,12 @@ def test_qr_rank_deficient_matches_oracle(c1_random, qr_kernel):
     w1 = rng.normal(size=16) + 1j * rng.normal(size=16)
     cases.append(np.outer(v, w1))
     cases.append(np.outer(v, w1) + np.outer(u, rng.normal(size=16)))
+    # dropped runs between kept columns: 0-3 kept, 4-7 dropped, 8 kept, 9-15 dropped (the tail
+    # finishes 5-7, hands 8 back to the row path, and is taken again after 9)
+    G = rng.normal(size=(200, 16)) + 1j * rng.normal(size=(200, 16))
+    G[:, 4:8] = G[:, 0:4] @ (rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4)))
+    G[:, 9:16] = G[:, 0:9] @ rng.normal(size=(9, 7))
+    cases.append(G)
     for C in cases:
         out = debug_qr_or_rejected(eng, qr_kernel, C)
         if out is None:
@@ -330,9 +336,32 @@ def test_truncated_sweep_with_each_qr_kernel_matches_oracle(kernel):
         eng.step(10.0)
         tdvp_ps_step(st, 10.0)
         assert rel_pop_err(eng.observables(0)[0], populations(st, p)) <= POP_TOL
-    for bad in (3, 32, 0.5, -2):
+    for bad in (3, 32, 0.5, -3):
         with pytest.raises(pkg.TDVPError):
             eng.set_option(pkg.OPT_QR_KERNEL, bad)
+
+
+def test_fmo_product_start_sweeps_agree_between_qr_kernels():
+    """Eight FMO-sized steps (D = 64, rank threshold 1e-6) from the product start: the bonds are
+    far below full rank with kept and dropped rows interleaved, so the grid QR kernel runs its
+    rank-deficient tail repeatedly inside sweeps; the cluster kernel computes the same rule row
+    by row (its QR is pinned to the oracle above)."""
+    p = wl.fmo_sized()
+
+    def make(kernel):
+        e = pkg.Engine()
+        e.set_option(pkg.OPT_RANK_RTOL, 1e-6)
+        e.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
+        e.set_option(pkg.OPT_QR_KERNEL, kernel)
+        e.build_mpo(0, p)
+        e.init_mps(0, 64, p.exciton_site)
+        return e
+
+    grid, cluster = make(0), make(-2)
+    for _ in range(8):
+        grid.step(10.0)
+        cluster.step(10.0)
+        assert rel_pop_err(grid.observables(0)[0], cluster.observables(0)[0]) <= 1e-12
 
 
 def test_rank_threshold_option_matches_oracle():
