@@ -173,18 +173,21 @@ struct TcDesc {
   const char* A;     // packed, 128-row tiles
   const char* B;     // packed, 64-row tiles
   int M, N, K;       // logical sizes
-  int mode;          // 0: planar FP32 (Cr, Ci), 1: complex FP64 (C64), 2: packed A of the next GEMM
+  int mode;          // 0: planar FP32 (Cr, Ci), 1: complex FP64 (C64), 2: packed A of the next GEMM,
+                     // 3: environment, column (w c) of row i to C64[(w Dc + i) Dc + c]
+  int lanczos;       // 1: a stage of a Lanczos matvec (skipped once the solve is done)
   float* Cr;
   float* Ci;
   zc* C64;
   int ldc;
   char* P;           // mode 2 target
-  int pDb, pnkt;     // mode 2: row m = w*Db + l' -> (l', w*Db + n)
+  int pDb, pnkt;     // mode 2: row m = w*Db + l' -> (l', w*Db + n); mode 3: pDb = Dc
 };
 
 // operands of the four tensor-core GEMMs, derived on the device from the site tables
 __device__ bool tc_desc(int op, int site, const SiteDev* sdr, const WorkDev& W, TcDesc& g) {
   const SiteDev& s = sdr[site];
+  g.lanczos = op <= TC_Z3 ? 1 : 0;
   switch (op) {
     case TC_MV1:   // T1[(w a')][(s b)] = sum_a L[w][a'][a] x[a][(s b)]
       g.A = W.tc_l; g.B = W.tc_x;
@@ -210,6 +213,26 @@ __device__ bool tc_desc(int op, int site, const SiteDev* sdr, const WorkDev& W, 
       g.mode = 1; g.C64 = W.w; g.ldc = Db;
       return true;
     }
+    case TC_EL1:   // T1[(w l')][(s r)] = sum_l L[w][l'][l] A[l][(s r)]
+      g.A = W.tc_l; g.B = W.tc_x;
+      g.M = s.Wl * s.Dl; g.N = s.d * s.Dr; g.K = s.Dl;
+      g.mode = 0; g.Cr = W.tc_t1; g.Ci = W.tc_t1 + W.tc_t1_plane; g.ldc = s.d * s.Dr;
+      return true;
+    case TC_EL3:   // Lenv(i+1)[w'][r'][r] = sum_{(l' s')} conj(A[(l' s')][r']) T2[(l' s')][(w' r)]
+      g.A = W.tc_e1; g.B = W.tc_e2;
+      g.M = s.Dr; g.N = s.Wr * s.Dr; g.K = s.Dl * s.d;
+      g.mode = 3; g.C64 = sdr[site + 1].Lenv; g.pDb = s.Dr;
+      return true;
+    case TC_ER1:   // T1[(l s)][(w' r')] = sum_r A[(l s)][r] R[w'][r'][r]
+      g.A = W.tc_e1; g.B = W.tc_e2;
+      g.M = s.Dl * s.d; g.N = s.Wr * s.Dr; g.K = s.Dr;
+      g.mode = 0; g.Cr = W.tc_t1; g.Ci = W.tc_t1 + W.tc_t1_plane; g.ldc = s.Wr * s.Dr;
+      return true;
+    case TC_ER3:   // Renv(i-1)[w][l'][l] = sum_{(s' r')} conj(A[l'][(s' r')]) T2[w][l][(s' r')]
+      g.A = W.tc_e1; g.B = W.tc_e2;
+      g.M = s.Dl; g.N = s.Wl * s.Dl; g.K = s.d * s.Dr;
+      g.mode = 3; g.C64 = sdr[site - 1].Renv; g.pDb = s.Dl;
+      return true;
   }
   return false;
 }
@@ -234,7 +257,8 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
   const WorkDev& W = wk[r];
   if (threadIdx.x == 0) {
     const SiteDev* sdr = sd + (long long)r * N_sites;
-    live = tc_desc(op, site, sdr, W, g) && !W.ks->done && (int)blockIdx.y * BM < g.M && (int)blockIdx.x * BN < g.N;
+    live = tc_desc(op, site, sdr, W, g) && !(g.lanczos && W.ks->done) && (int)blockIdx.y * BM < g.M &&
+           (int)blockIdx.x * BN < g.N;
     abort_flag = 0;
   }
   __syncthreads();
@@ -393,6 +417,9 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
           g.Ci[(long long)row * g.ldc + gcol] = vi;
         } else if (g.mode == 1) {
           g.C64[(long long)row * g.ldc + gcol] = zmake((double)vr, (double)vi);
+        } else if (g.mode == 3) {
+          const int Dc = g.pDb, w = gcol / Dc, c = gcol % Dc;
+          g.C64[((long long)w * Dc + row) * Dc + c] = zmake((double)vr, (double)vi);
         } else {
           const int w = row / g.pDb, lp = row % g.pDb;
           pk_store(g.P, BM, g.pnkt, lp, w * g.pDb + gcol, (double)vr, (double)vi, split);
@@ -482,6 +509,99 @@ __global__ void wapply_tc_kernel(int site, const SiteDev* __restrict__ sd, const
   pk_store(W.tc_t2, BM, nkt, ap * d + sp, wp * Dr + b, ar, ai, split);
 }
 
+// Site tensor of an environment update as a packed operand; the grid covers the padded tiles.
+//   kind 0: A^H as A operand, row r', k (l s);    kind 1: A as A operand, row (l s), k r
+//   kind 2: conj(A) as A operand, row l', k (s r); kind 3: A as B operand, row (s r), k l
+__global__ void pack_site_kernel(int kind, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
+                                 int N_sites, int split) {
+  const int r = blockIdx.y;
+  const SiteDev& s = sd[(long long)r * N_sites + site];
+  const WorkDev& W = wk[r];
+  const int Dl = s.Dl, d = s.d, Dr = s.Dr;
+  int rows, K, RT;
+  char* dst;
+  switch (kind) {
+    case 0: rows = Dr; K = Dl * d; RT = BM; dst = W.tc_e1; break;
+    case 1: rows = Dl * d; K = Dr; RT = BM; dst = W.tc_e1; break;
+    case 2: rows = Dl; K = d * Dr; RT = BM; dst = W.tc_e1; break;
+    default: rows = d * Dr; K = Dl; RT = BN; dst = W.tc_x; break;
+  }
+  const int rp = cdivd(rows, RT) * RT, kp = cdivd(K, BK) * BK;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rp * kp) return;
+  const int row = (int)(e / kp), k = (int)(e % kp);
+  zc v = zmake(0, 0);
+  if (row < rows && k < K) {
+    switch (kind) {
+      case 0: v = zconj(s.A[(long long)k * Dr + row]); break;
+      case 1: v = s.A[(long long)row * Dr + k]; break;
+      case 2: v = zconj(s.A[(long long)row * d * Dr + k]); break;
+      default: v = s.A[(long long)k * d * Dr + row]; break;
+    }
+  }
+  pk_store(dst, RT, cdivd(K, BK), row, k, v.x, v.y, split);
+}
+
+// Renv[site] as the B operand of the right-update first stage: row (w' r'), k r.
+__global__ void pack_renv_rows_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
+                                      int N_sites, int split) {
+  const int r = blockIdx.y;
+  const SiteDev& s = sd[(long long)r * N_sites + site];
+  const WorkDev& W = wk[r];
+  const int Dr = s.Dr, rows = s.Wr * Dr, K = Dr;
+  const int rp = cdivd(rows, BN) * BN, kp = cdivd(K, BK) * BK;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rp * kp) return;
+  const int row = (int)(e / kp), k = (int)(e % kp);
+  const zc v = (row < rows && k < K) ? s.Renv[(long long)row * Dr + k] : zmake(0, 0);
+  pk_store(W.tc_e2, BN, cdivd(K, BK), row, k, v.x, v.y, split);
+}
+
+// Sparse MPO stage of an environment update from the planar FP32 first-stage output, written as
+// the packed B operand of the last stage (one output element per thread, padded tiles included).
+//   which 0 (left):  T2[(l' s')][(w' r)] = sum_e val T1[(w l')][(s r)] over the forward CSR row
+//                    (w', s'); B row (w' r), k (l' s').
+//   which 1 (right): T2[w][(l s')][r'] = sum_e val T1[(l s)][(w' r')] over the backward CSR row
+//                    (w, s'); B row (w l), k (s' r').
+__global__ void wapply_env_kernel(int which, int site, const SiteDev* __restrict__ sd,
+                                  const WorkDev* __restrict__ wk, int N_sites, int split) {
+  const int r = blockIdx.y;
+  const SiteDev& s = sd[(long long)r * N_sites + site];
+  const WorkDev& W = wk[r];
+  const int Dl = s.Dl, d = s.d, Dr = s.Dr;
+  const int rows = which == 0 ? s.Wr * Dr : s.Wl * Dl;
+  const int K = which == 0 ? Dl * d : d * Dr;
+  const int rp = cdivd(rows, BN) * BN, kp = cdivd(K, BK) * BK;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rp * kp) return;
+  const int row = (int)(e / kp), k = (int)(e % kp);
+  double ar = 0, ai = 0;
+  if (row < rows && k < K) {
+    const float* T1r = W.tc_t1;
+    const float* T1i = W.tc_t1 + W.tc_t1_plane;
+    if (which == 0) {
+      const int wp = row / Dr, b = row % Dr, ap = k / d, sp = k % d;
+      const int crow = wp * d + sp;
+      const long long ld = (long long)d * Dr;
+      for (int q = s.fw.ptr[crow]; q < s.fw.ptr[crow + 1]; ++q) {
+        const long long off = ((long long)s.fw.ci[q] * Dl + ap) * ld + (long long)s.fw.si[q] * Dr + b;
+        ar += s.fw.val[q] * (double)T1r[off];
+        ai += s.fw.val[q] * (double)T1i[off];
+      }
+    } else {
+      const int w = row / Dl, l = row % Dl, sp = k / Dr, rr = k % Dr;
+      const int crow = w * d + sp;
+      const long long ld = (long long)s.Wr * Dr;
+      for (int q = s.bw.ptr[crow]; q < s.bw.ptr[crow + 1]; ++q) {
+        const long long off = ((long long)l * d + s.bw.si[q]) * ld + (long long)s.bw.ci[q] * Dr + rr;
+        ar += s.bw.val[q] * (double)T1r[off];
+        ai += s.bw.val[q] * (double)T1i[off];
+      }
+    }
+  }
+  pk_store(W.tc_e2, BN, cdivd(K, BK), row, k, ar, ai, split);
+}
+
 inline int cdivh(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
@@ -534,6 +654,31 @@ cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* 
                           long long max_elems, int split, cudaStream_t st) {
   dim3 grid(cdivh(max_elems, 256), R);
   pack_x_kernel<<<grid, 256, 0, st>>>(kind, site, sd, wk, N_sites, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_site(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                             long long max_rows, long long max_k, int split, cudaStream_t st) {
+  const int RT = kind == 3 ? BN : BM;
+  const long long total = (long long)cdivh(max_rows, RT) * RT * cdivh(max_k, BK) * BK;
+  dim3 grid(cdivh(total, 256), R);
+  pack_site_kernel<<<grid, 256, 0, st>>>(kind, site, sd, wk, N_sites, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_renv_rows(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                                  long long max_rows, long long max_k, int split, cudaStream_t st) {
+  const long long total = (long long)cdivh(max_rows, BN) * BN * cdivh(max_k, BK) * BK;
+  dim3 grid(cdivh(total, 256), R);
+  pack_renv_rows_kernel<<<grid, 256, 0, st>>>(site, sd, wk, N_sites, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wapply_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                              long long max_rows, long long max_k, int split, cudaStream_t st) {
+  const long long total = (long long)cdivh(max_rows, BN) * BN * cdivh(max_k, BK) * BK;
+  dim3 grid(cdivh(total, 256), R);
+  wapply_env_kernel<<<grid, 256, 0, st>>>(which, site, sd, wk, N_sites, split);
   return cudaGetLastError();
 }
 

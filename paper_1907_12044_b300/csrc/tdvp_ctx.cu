@@ -627,6 +627,71 @@ int memset_tc(tdvp_ctx* ctx, const Views& v, int field, int which, int site) {
   return TDVP_OK;
 }
 
+int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int split);
+
+// the left environment of `site` packed in tc_l (kept while it stays valid)
+int ensure_l_pack(tdvp_ctx* ctx, const Views& v, int site, int split) {
+  if (ctx->l_site == site && ctx->l_split == split) return TDVP_OK;
+  int rc = memset_tc(ctx, v, 0, 0, site);
+  if (rc) return rc;
+  const Dims m = maxdims(ctx, site, v);
+  LAUNCH(launch_pack_env(0, site, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[site] * m.Dl * m.Dl, split, ctx->st));
+  ctx->l_site = site;
+  ctx->l_split = split;
+  return TDVP_OK;
+}
+
+// Left update on the tensor cores: T1 = L A (stage 1, as the matvec's), the MPO stage written as
+// the B operand of the last stage, Lenv(i+1) = A^H T2.
+int env_left_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
+  const Dims m = maxdims(ctx, i, v);
+  const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
+  int rc;
+  if ((rc = ensure_l_pack(ctx, v, i, split))) return rc;
+  LAUNCH(launch_pack_site(3, i, v.sd, v.wk, v.R, ctx->N, (long long)d * m.Dr, m.Dl, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_EL1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, m.Dl, split, ctx->st));
+  LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_env(0, i, v.sd, v.wk, v.R, ctx->N, (long long)Wr * m.Dr, (long long)m.Dl * d,
+                                             split, ctx->st));
+  LAUNCH(launch_pack_site(0, i, v.sd, v.wk, v.R, ctx->N, m.Dr, (long long)m.Dl * d, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_EL3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, Wr * m.Dr, m.Dl * d, split, ctx->st));
+  if (ctx->l_site == i + 1) ctx->l_site = -1;
+  if (ctx->prof) {
+    double f = 0;
+    for (int r = v.r0; r < v.r0 + v.R; ++r) {
+      const auto& bd = ctx->rh[r].bd;
+      const double Dl = bd[i], Dr = bd[i + 1];
+      f += 8.0 * (Wl * Dl * d * Dr * Dl + Dr * Wr * Dr * Dl * d);
+    }
+    ctx->stats.prof_flops[TDVP_CAT_TC] += f;
+  }
+  return TDVP_OK;
+}
+
+// Right update on the tensor cores: T1 = A R^T (all w' at once), the backward MPO stage written as
+// the B operand of the last stage, Renv(i-1) = conj(A) T2^T.
+int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
+  const Dims m = maxdims(ctx, i, v);
+  const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
+  LAUNCH(launch_pack_site(1, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dl * d, m.Dr, split, ctx->st));
+  LAUNCH(launch_pack_renv_rows(i, v.sd, v.wk, v.R, ctx->N, (long long)Wr * m.Dr, m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_ER1, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, Wr * m.Dr, m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_env(1, i, v.sd, v.wk, v.R, ctx->N, (long long)Wl * m.Dl, (long long)d * m.Dr,
+                                             split, ctx->st));
+  LAUNCH(launch_pack_site(2, i, v.sd, v.wk, v.R, ctx->N, m.Dl, (long long)d * m.Dr, split, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_ER3, i, v.sd, v.wk, v.R, ctx->N, m.Dl, Wl * m.Dl, d * m.Dr, split, ctx->st));
+  if (ctx->r_site == i - 1) ctx->r_site = -1;
+  if (ctx->prof) {
+    double f = 0;
+    for (int r = v.r0; r < v.r0 + v.R; ++r) {
+      const auto& bd = ctx->rh[r].bd;
+      const double Dl = bd[i], Dr = bd[i + 1];
+      f += 8.0 * (Dl * d * Wr * Dr * Dr + Dl * Wl * Dl * d * Dr);
+    }
+    ctx->stats.prof_flops[TDVP_CAT_TC] += f;
+  }
+  return TDVP_OK;
+}
+
 int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int split) {
   if (ctx->l_site != lsite || ctx->l_split != split) {
     int rc = memset_tc(ctx, v, 0, 0, lsite);
@@ -696,7 +761,13 @@ int matvec_bond_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
   return TDVP_OK;
 }
 
-int env_left(tdvp_ctx* ctx, const Views& v, int i) {
+int env_left_tc(tdvp_ctx* ctx, const Views& v, int i, int split);
+int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int split);
+
+// Left environment of site i+1 from site i (Eq. tdvp1_h1i); FP64, or TF32 / TF32x3 on the
+// tensor cores in the mixed-precision sweep.
+int env_left(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
+  if (P != TDVP_PREC_FP64) return env_left_tc(ctx, v, i, P == TDVP_PREC_TF32X3 ? 1 : 0);
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
@@ -706,7 +777,9 @@ int env_left(tdvp_ctx* ctx, const Views& v, int i) {
   return g_op(ctx, v, OP_EL3, i, m.Dr, m.Dr, Wr);
 }
 
-int env_right(tdvp_ctx* ctx, const Views& v, int i) {
+// Right environment of site i-1 from site i (Eq. tdvp1_hiN); FP64 or on the tensor cores.
+int env_right(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
+  if (P != TDVP_PREC_FP64) return env_right_tc(ctx, v, i, P == TDVP_PREC_TF32X3 ? 1 : 0);
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
@@ -1020,15 +1093,21 @@ int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
   if ((rc = dalloc(ctx, H.mps_allocs, &W.obs, ctx->n_el + 4))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.ks, 1))) return rc;
   {
-    long long bl = 1, br = 1, bx = 1, bt2 = 1, bt1 = 1;
+    long long bl = 1, br = 1, bx = 1, bt2 = 1, bt1 = 1, be1 = 1, be2 = 1;
     for (int i = 0; i < N; ++i) {
       const long long Dl = bd[i], Dr = bd[i + 1], d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
       bl = std::max(bl, tc_pack_bytes(128, Wl * Dl, Dl));
       br = std::max(br, tc_pack_bytes(64, Dr, Wr * Dr));
       bx = std::max(bx, std::max(tc_pack_bytes(64, d * Dr, Dl), tc_pack_bytes(64, Dr, Dr)));
       bt2 = std::max(bt2, std::max(tc_pack_bytes(128, Dl * d, Wr * Dr), tc_pack_bytes(128, Dr, Wr * Dr)));
-      bt1 = std::max(bt1, Wl * Dl * d * Dr);
+      bt1 = std::max(bt1, std::max(Wl * Dl * d * Dr, Dl * d * Wr * Dr));
+      be1 = std::max(be1, std::max(tc_pack_bytes(128, Dr, Dl * d),
+                                   std::max(tc_pack_bytes(128, Dl * d, Dr), tc_pack_bytes(128, Dl, d * Dr))));
+      be2 = std::max(be2, std::max(tc_pack_bytes(64, Wr * Dr, Dl * d),
+                                   std::max(tc_pack_bytes(64, Wr * Dr, Dr), tc_pack_bytes(64, Wl * Dl, d * Dr))));
     }
+    if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_e1, (size_t)be1))) return rc;
+    if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_e2, (size_t)be2))) return rc;
     if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_l, (size_t)bl))) return rc;
     if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_r, (size_t)br))) return rc;
     if ((rc = dalloc(ctx, H.mps_allocs, &W.tc_x, (size_t)bx))) return rc;
@@ -1071,7 +1150,7 @@ int enqueue_step(tdvp_ctx* ctx, const Views& v, double tau, double tol, int P, i
   for (int i = 0; i < N - 1; ++i) {
     if ((rc = expm(ctx, v, 0, i, i == 0 ? 1 : 0, 1, -0.5 * tau, tol, nc, P))) return rc;
     if ((rc = gauge_qr(ctx, v, i, 0))) return rc;
-    if ((rc = env_left(ctx, v, i))) return rc;
+    if ((rc = env_left(ctx, v, i, P))) return rc;
     if ((rc = expm(ctx, v, 1, i, 2, 2, 0.5 * tau, tol, nc, P))) return rc;
     const Dims m = maxdims(ctx, i + 1, v);
     if ((rc = g_op(ctx, v, OP_ABS_L, i, m.Dl, ctx->d[i + 1] * m.Dr, 1))) return rc;
@@ -1079,7 +1158,7 @@ int enqueue_step(tdvp_ctx* ctx, const Views& v, double tau, double tol, int P, i
   if ((rc = expm(ctx, v, 0, N - 1, 0, 1, -tau, tol, nc, P))) return rc;
   for (int i = N - 1; i >= 1; --i) {
     if ((rc = gauge_qr(ctx, v, i, 1))) return rc;
-    if ((rc = env_right(ctx, v, i))) return rc;
+    if ((rc = env_right(ctx, v, i, P))) return rc;
     if ((rc = expm(ctx, v, 1, i - 1, 2, 2, 0.5 * tau, tol, nc, P))) return rc;
     const Dims m = maxdims(ctx, i - 1, v);
     if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;

@@ -123,6 +123,8 @@ struct WorkDev {
   char* tc_r;   // B operand: right environment [r'][(w r)]
   char* tc_x;   // B operand: the Lanczos vector
   char* tc_t2;  // A operand of the third stage
+  char* tc_e1;  // A operand of an environment update (site tensor, its conjugate or adjoint)
+  char* tc_e2;  // B operand of an environment update (environment rows or the MPO stage)
   float* tc_t1; // first-stage output, planar FP32 (re plane, then im plane)
   long long tc_t1_plane;
   int* kprev;   // [2*N] last Krylov dimension per (site, kind)
@@ -149,7 +151,9 @@ enum GemmOp {
 };
 
 // Tensor-core GEMMs of the mixed-precision matvecs.
-enum TcOp { TC_MV1 = 0, TC_MV3 = 1, TC_Z1 = 2, TC_Z3 = 3 };
+// Tensor-core GEMMs: the Lanczos matvec stages (skipped once the solve is done) and the
+// environment updates of the mixed-precision sweep.
+enum TcOp { TC_MV1 = 0, TC_MV3 = 1, TC_Z1 = 2, TC_Z3 = 3, TC_EL1 = 4, TC_EL3 = 5, TC_ER1 = 6, TC_ER3 = 7 };
 
 struct GemmDesc {
   const zc* A;
@@ -281,6 +285,20 @@ cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDe
                             long long max_elems, int split, cudaStream_t st);
 cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
                           long long max_elems, int split, cudaStream_t st);
+// Environment updates on the tensor cores (kernels_tc.cu).  which = 0: left (site i -> Lenv of
+// i+1), 1: right (site i -> Renv of i-1).  Stage operands:
+//   pack_site (kind 0) A^H as A operand [r'][(l s)]; (kind 1) A as A operand [(l s)][r];
+//             (kind 2) conj(A) as A operand [l'][(s r)]; (kind 3) A as B operand [(s r)][l]
+//   pack_renv_rows: R as B operand [(w' r')][r]
+//   wapply_env (which 0) T2[(l' s')][(w' r)] as B operand [(w' r)][(l' s')];
+//              (which 1) T2[w][(l s')][r'] as B operand [(w l)][(s' r')]
+// Every pack covers the padded tiles (zeros outside the valid region).
+cudaError_t launch_pack_site(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                             long long max_rows, long long max_k, int split, cudaStream_t st);
+cudaError_t launch_pack_renv_rows(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                                  long long max_rows, long long max_k, int split, cudaStream_t st);
+cudaError_t launch_wapply_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
+                              long long max_rows, long long max_k, int split, cudaStream_t st);
 cudaError_t launch_wapply_tc(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int max_xy,
                              int n_rows, int split, cudaStream_t st);
 
