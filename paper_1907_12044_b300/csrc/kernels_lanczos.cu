@@ -5,8 +5,9 @@
 // Per iteration j the host enqueues: matvec (x -> w), then
 //   dots     p_t = <V_t, w>                         (partial sums per chunk)
 //   upd1     h1 = sum p; w -= V h1; p2_t = <V_t, w>  (first Gram-Schmidt pass)
-//   upd2     h2 = sum p2; w -= V h2; |w|^2 partials  (re-orthogonalisation pass)
-//   tri      beta_j = |w|; alpha_j = Re(h1_j + h2_j); c = exp(i theta T_{j+1}) e_1 (Chebyshev);
+//   upd2     h2 = sum p2; w -= V h2; |w|^2 partials  (re-orthogonalisation pass); the block
+//            that finishes last (atomic count per realisation) then takes the tridiagonal step:
+//            beta_j = |w|; alpha_j = Re(h1_j + h2_j); c = exp(i theta T_{j+1}) e_1 (Chebyshev);
 //            stop when ||v|| beta_j |c_j| <= tol, or k = kcap, or beta_j = 0
 //   next     V_{j+1} = x = w / beta_j
 // Every kernel of an iteration returns at once when the solve of its realisation is done, so
@@ -19,6 +20,10 @@ namespace {
 
 constexpr int NT = TDVP_VEC_THREADS;
 constexpr int PSTRIDE = TDVP_KMAX_HARD + 2;
+constexpr int TRI_THREADS = NT;   // the tridiagonal step runs in a block of the vector kernel
+constexpr int MAX_CHEB = 512;
+constexpr int BESSEL_CAP = MAX_CHEB + 128;
+constexpr int TRI_SH = 3 * TRI_THREADS + MAX_CHEB + 2 * (TRI_THREADS / 32) + 8 + 2 * BESSEL_CAP;
 
 struct VecGeom {
   long long n;       // vector length
@@ -199,7 +204,11 @@ __global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
   chunk_dots(W, g, j, 0, b, red);
 }
 
-// pass 1 (tab_in = 0, tab_out = 1) or pass 2 (tab_in = 1, norm partials into table 2)
+__device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, double* al, double* be,
+                         double* betaj_s);
+
+// pass 1 (tab_in = 0, tab_out = 1) or pass 2 (tab_in = 1, norm partials into table 2; the last
+// block to finish then takes the tridiagonal step)
 __global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
   __shared__ double red[2 * 8 * NT / 32];
   __shared__ zc h[TDVP_KMAX_HARD];
@@ -226,6 +235,23 @@ __global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
     const zc s = block_zsum(zmake(nn, 0), red);
     if (threadIdx.x == 0) *P(W, 2, b, 0) = s;
     if (b == 0 && threadIdx.x == 0) W.ks->alpha[j] += h[j].x;
+    // the last block of this realisation to finish takes the tridiagonal step
+    __shared__ int last;
+    __shared__ double sh[TRI_SH];
+    __shared__ zc c[TRI_THREADS];
+    __shared__ double al[TDVP_KMAX_HARD], be[TDVP_KMAX_HARD], betaj_s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned old = atomicAdd(W.lzc, 1u);
+      last = old == (unsigned)(g.nblk - 1);
+      if (last) *W.lzc = 0u;     // every block of this realisation has arrived: reset for the next pass
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      tri_step(a, r, j, sh, c, al, be, &betaj_s);
+    }
   }
 }
 
@@ -253,20 +279,58 @@ __device__ void bessel_j(double x, int N, double* J) {
   for (int n = 0; n <= N; ++n) J[n] *= inv;
 }
 
-constexpr int TRI_THREADS = 128;
-constexpr int MAX_CHEB = 512;
+
+// The same values by every thread of the block: the recurrence factors 2n/x are computed in
+// parallel, thread 0 runs the recurrence (one fused multiply-add per step, the overflow guard every
+// 8 steps), and the normalisation sum and scaling are block reductions.  Needs m = N + 25 + x + 1
+// <= BESSEL_CAP; `cf`, `raw`: BESSEL_CAP doubles each, `red`: one double per warp.
+__device__ void bessel_block(double x, int N, double* J, double* cf, double* raw, double* red) {
+  const int t = threadIdx.x;
+  int m = N + 24 + (int)x;
+  m += (m & 1);
+  const double ix = 1.0 / x;
+  for (int n = t + 1; n <= m; n += blockDim.x) cf[n] = (2.0 * n) * ix;
+  __syncthreads();
+  if (t == 0) {
+    double jp1 = 0.0, jn = 1e-200;
+    raw[m] = jn;
+    for (int n = m; n >= 1; --n) {
+      const double jm1 = fma(cf[n], jn, -jp1);
+      jp1 = jn;
+      jn = jm1;
+      raw[n - 1] = jn;
+      if ((n & 7) == 0 && fabs(jn) > 1e140) {
+        jn *= 1e-150; jp1 *= 1e-150;
+        for (int q2 = n - 1; q2 <= m; ++q2) raw[q2] *= 1e-150;
+      }
+    }
+  }
+  __syncthreads();
+  // S = raw_0 + 2 sum_{k >= 1} raw_{2k}
+  double s = 0.0;
+  for (int n = 2 * (t + 1); n <= m; n += 2 * blockDim.x) s += raw[n];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (t % 32 == 0) red[t / 32] = s;
+  __syncthreads();
+  double S = 0.0;
+  for (int w = 0; w < (int)blockDim.x / 32; ++w) S += red[w];
+  S = raw[0] + 2.0 * S;
+  const double inv = 1.0 / S;
+  for (int n = t; n <= N; n += blockDim.x) J[n] = raw[n] * inv;
+  __syncthreads();
+}
 
 // c = exp(i theta T) e_1 for T = tridiag(beta[0..k-2], alpha[0..k-1]) by a Chebyshev expansion on
 // the Gershgorin interval [lo, hi]: exp(i x T~) = sum_n (2 - delta_n0) i^n J_n(x) T_n(T~)
 // (Jacobi-Anger), T~ = (T - c0)/h, x = theta h.  The vectors T_n(T~) e_1 are real.
 // Thread t (< k) owns component t.  Returns false when the expansion would need too many terms.
 __device__ bool tridiag_expi(const double* alpha, const double* beta, int k, double theta, zc* out,
-                             double* sh /* >= 3*TRI_THREADS + MAX_CHEB + 8 doubles */) {
+                             double* sh /* >= TRI_SH doubles */) {
   const int t = threadIdx.x;
   double* vcur = sh;                       // [TRI_THREADS]
   double* J = sh + TRI_THREADS;            // [MAX_CHEB]
-  double* red = J + MAX_CHEB;              // [8]
-  double* bnd = red + 8;                   // lo, hi
+  double* red = J + MAX_CHEB;              // [2 per warp]
+  double* bnd = red + 2 * (TRI_THREADS / 32);   // lo, hi
   // Gershgorin bounds
   double lo = 1e300, hi = -1e300;
   double at = 0, bl = 0, br = 0;
@@ -304,10 +368,56 @@ __device__ bool tridiag_expi(const double* alpha, const double* beta, int k, dou
     return true;
   }
   if (N + 1 > MAX_CHEB) return false;
-  if (t == 0) bessel_j(ax, N, J);
-  __syncthreads();
+  {
+    double* cfb = bnd + 8;
+    double* raw = cfb + BESSEL_CAP;
+    const int mneed = N + 24 + (int)ax + 2;
+    if (mneed + 1 <= BESSEL_CAP) {
+      bessel_block(ax, N, J, cfb, raw, red);
+    } else {
+      if (t == 0) bessel_j(ax, N, J);
+      __syncthreads();
+    }
+  }
   const double sgn = x >= 0 ? 1.0 : -1.0;      // J_n(-a) = (-1)^n J_n(a)
   const double ih = 1.0 / h;
+  int Nlast = N;
+  while (Nlast > 2 && fabs(J[Nlast]) < 1e-18 && fabs(J[Nlast - 1]) < 1e-18) --Nlast;
+  if (k <= 32) {
+    // one warp: component t in lane t, neighbours by shuffles, no block barriers in the loop;
+    // T_{n+1} e_1 = 2 T~ T_n e_1 - T_{n-1} e_1 with T~ = (T - c0)/h
+    if (t < 32) {
+      const bool act = t < k;
+      const double A = act ? 2.0 * (at - c0) * ih : 0.0;
+      const double BL = (act && t > 0) ? 2.0 * bl * ih : 0.0;
+      const double BR = (act && t < k - 1) ? 2.0 * br * ih : 0.0;
+      double vp = (t == 0) ? 1.0 : 0.0;
+      double vc;
+      {
+        const double left = __shfl_up_sync(0xffffffffu, vp, 1), right = __shfl_down_sync(0xffffffffu, vp, 1);
+        vc = 0.5 * fma(A, vp, fma(BL, left, BR * right));
+      }
+      zc acc = zmake(J[0] * vp, 2.0 * J[1] * sgn * vc);
+      for (int n = 1; n < Nlast; ++n) {
+        const double left = __shfl_up_sync(0xffffffffu, vc, 1), right = __shfl_down_sync(0xffffffffu, vc, 1);
+        const double vn = fma(A, vc, fma(BL, left, fma(BR, right, -vp)));
+        const int m = n + 1;
+        double cf = 2.0 * J[m];
+        if (sgn < 0 && (m & 1)) cf = -cf;
+        switch (m & 3) {
+          case 0: acc.x = fma(cf, vn, acc.x); break;
+          case 1: acc.y = fma(cf, vn, acc.y); break;
+          case 2: acc.x = fma(-cf, vn, acc.x); break;
+          default: acc.y = fma(-cf, vn, acc.y); break;
+        }
+        vp = vc;
+        vc = vn;
+      }
+      if (act) out[t] = zmul(ph, acc);
+    }
+    __syncthreads();
+    return true;
+  }
   // coefficient of T_n: (2 - delta) i^n J_n(x); i^n cycles 1, i, -1, -i
   double vprev = (t == 0) ? 1.0 : 0.0;          // T_0 e_1
   vcur[t] = vprev;
@@ -326,8 +436,6 @@ __device__ bool tridiag_expi(const double* alpha, const double* beta, int k, dou
   vcur[t] = v1;
   double vc = v1;
   __syncthreads();
-  int Nlast = N;
-  while (Nlast > 2 && fabs(J[Nlast]) < 1e-18 && fabs(J[Nlast - 1]) < 1e-18) --Nlast;
   for (int n = 1; n < Nlast; ++n) {
     double vn = 0;
     if (t < k) {
@@ -354,27 +462,32 @@ __device__ bool tridiag_expi(const double* alpha, const double* beta, int k, dou
   return true;
 }
 
-__global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flags) {
-  __shared__ double sh[3 * TRI_THREADS + MAX_CHEB + 16];
-  __shared__ zc c[TRI_THREADS];
-  __shared__ double betaj_s;
-  const int r = blockIdx.x;
+// The tridiagonal step of iteration j of realisation r: beta_j from the norm partials, controller
+// features and prediction at j = 0, then (from the first tested k on) exp(i theta T_k) e_1 and the
+// a-posteriori test.  Run by the last block of the second orthogonalisation pass to finish; every
+// value the other blocks wrote in that kernel is read through L2.  `al`, `be`: KMAX doubles each.
+__device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, double* al, double* be,
+                         double* betaj_s) {
+  int* flags = a.flags;
   const WorkDev& W = a.wk[r];
   KState* ks = W.ks;
-  if (ks->done) return;
-  if (a.devj) j = ks->jcur;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const VecGeom g = geom(vec_len(sdr, a.site, a.kind), 0);
   if (threadIdx.x < 32) {
     double s = 0;
-    for (int b = threadIdx.x; b < g.nblk; b += 32) s += P(W, 2, b, 0)->x;
+    for (int b = threadIdx.x; b < g.nblk; b += 32) s += __ldcg(&P(W, 2, b, 0)->x);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) betaj_s = sqrt(s);
+    if (threadIdx.x == 0) *betaj_s = sqrt(s);
+  }
+  for (int t = threadIdx.x; t <= j; t += blockDim.x) {
+    al[t] = __ldcg(&ks->alpha[t]);
+    if (t < j) be[t] = __ldcg(&ks->beta[t]);
   }
   __syncthreads();
-  const double beta = betaj_s;
+  const double beta = *betaj_s;
   const int k = j + 1;
-  if (!isfinite(beta) || !isfinite(ks->alpha[j])) {
+  if (!isfinite(beta) || !isfinite(al[j])) {
+
     if (threadIdx.x == 0) {
       ks->status = -6; ks->done = 1; ks->k = 0; flags[r] = -1;
       if (a.devj) atomicExch(W.err, -7);
@@ -385,7 +498,7 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
   if (j == 0) {
     // controller features, known after the first Lanczos step
     if (threadIdx.x == 0) {
-      const double th = fabs(a.theta), a0 = ks->alpha[0];
+      const double th = fabs(a.theta), a0 = al[0];
       const double hn = sqrt(a0 * a0 + beta * beta);
       ks->feat[0] = (float)log10(1.0 + th * hn);
       ks->feat[1] = (float)a.kind;
@@ -413,7 +526,7 @@ __global__ void __launch_bounds__(TRI_THREADS) lz_tri(LzArgs a, int j, int* flag
     return;
   }
   if (threadIdx.x == 0) (*W.tri_count)++;
-  const bool ok = tridiag_expi(ks->alpha, ks->beta, k, a.theta, c, sh);
+  const bool ok = tridiag_expi(al, be, k, a.theta, c, sh);
   if (!ok) {
     if (threadIdx.x == 0) {
       ks->status = -1; ks->done = 1; ks->k = 0; flags[r] = -1;
@@ -536,7 +649,6 @@ cudaError_t launch_lz_iter_pre(const LzArgs& a, int j, cudaStream_t st) {
 }
 
 cudaError_t launch_lz_iter_post(const LzArgs& a, int j, cudaStream_t st) {
-  lz_tri<<<a.R, TRI_THREADS, 0, st>>>(a, j, a.flags);
   dim3 grid(a.nblk, a.R);
   lz_next<<<grid, NT, 0, st>>>(a, j);
   return cudaGetLastError();

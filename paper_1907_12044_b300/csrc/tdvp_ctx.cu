@@ -941,9 +941,9 @@ int expm_graph(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int d
   const cudaError_t ee = cudaStreamEndCapture(ctx->body_st, &tmp);
   if (rc) return rc;
   if (ee != cudaSuccess) return fail(ctx, TDVP_ERR_CUDA, cudaGetErrorString(ee));
-  // kernels of one body run: the matvec's (counted while capturing) + dots, two passes,
-  // tridiagonal, next vector, loop control
-  ctx->loop_body_launches.push_back((int)(ctx->stats.kernel_launches - before) + 6);
+  // kernels of one body run: the matvec's (counted while capturing) + dots, two passes (the
+  // tridiagonal step inside the second), next vector, loop control
+  ctx->loop_body_launches.push_back((int)(ctx->stats.kernel_launches - before) + 5);
   ctx->stats.kernel_launches = before;
   LAUNCHC(TDVP_CAT_LZVEC, launch_lz_combine(a, ctx->st));
   return TDVP_OK;
@@ -985,9 +985,9 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
       } else if ((rc = matvec_bond(ctx, v, site))) {
         return rc;
       }
-      LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));      // three kernels
-      LAUNCHC(TDVP_CAT_TRIDIAG, launch_lz_iter_post(a, j, ctx->st));   // two kernels
-      ctx->stats.kernel_launches += 3;
+      LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));      // three kernels (tridiagonal step inside)
+      LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_post(a, j, ctx->st));     // next vector
+      ctx->stats.kernel_launches += 2;
       ctx->stats.matvecs += v.R;
     }
     CK(cudaMemcpyAsync(ctx->h_flags + v.r0, v.flags, sizeof(int) * v.R, cudaMemcpyDeviceToHost, ctx->st));
@@ -1118,6 +1118,8 @@ int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
   if ((rc = dalloc(ctx, H.mps_allocs, &W.bar, 2 + 16))) return rc;   // root, generation, group counters
   if ((rc = dalloc(ctx, H.mps_allocs, &W.kprev, 2 * N))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.tri_count, 1))) return rc;
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.lzc, 1))) return rc;
+  CK(cudaMemsetAsync(W.lzc, 0, sizeof(unsigned), ctx->st));
   W.err = ctx->d_err + r;
   // boundary environments are the scalar 1
   const zc one = zmake(1.0, 0.0);

@@ -129,6 +129,7 @@ struct WorkDev {
   long long tc_t1_plane;
   int* kprev;   // [2*N] last Krylov dimension per (site, kind)
   int* tri_count; // tridiagonal exponentials evaluated (convergence tests)
+  unsigned* lzc;  // blocks of the second orthogonalisation pass that have finished (reset by the last)
   unsigned* bar;// [0]=count, [1]=generation of the QR group barrier
   int* err;     // device-side error flag of this realisation
 };
