@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="timed arm launch by launch instead of replaying each step as a CUDA graph "
                          "(the FP64 arm is always launch by launch: the plain method)")
+    ap.add_argument("--no-pdl", action="store_true",
+                    help="launch the step's kernels in plain stream order (no programmatic dependent launch)")
     ap.add_argument("--kernel-case", choices=["heff", "qr"], default=None,
                     help="time one hot operation at the bench's full-size shapes instead of steps (for "
                          "kernel captures): heff = one H_eff matvec at a bath-mode site of a random D-bond "
@@ -466,6 +468,11 @@ def run_kernel_case(args):
 
 def main():
     args = parse()
+    if args.no_pdl:
+        import paper_1907_12044_b300 as pkg
+        e = pkg.Engine()
+        e.set_option(pkg.OPT_PDL, 0)     # process-wide
+        e.close()
     if args.kernel_case:
         run_kernel_case(args)
         return

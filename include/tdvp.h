@@ -268,11 +268,15 @@ int tdvp_autotune(tdvp_ctx* ctx);
  *     prediction).  The graph is captured on the first call for a (dt, tolerance, precision,
  *     Krylov mode) and kept until build/init, autotune or any option change.  Ignored while
  *     profiling is on (per-launch timing needs the launch-by-launch path).  0 (default): launch
- *     by launch, one host flag read per exponential. */
+ *     by launch, one host flag read per exponential.
+ *   TDVP_OPT_PDL: 1 (default) = kernels of the step are launched as programmatic dependents of
+ *     their predecessor (they start while it finishes and wait for it before touching memory);
+ *     0 = plain stream order.  Process-wide: it applies to every context. */
 #define TDVP_OPT_RANK_RTOL         1
 #define TDVP_OPT_KRYLOV_CHECK_ALL  2
 #define TDVP_OPT_QR_KERNEL         3
 #define TDVP_OPT_GRAPH             4
+#define TDVP_OPT_PDL               5
 int tdvp_set_option(tdvp_ctx* ctx, int option, double value);
 
 const char* tdvp_last_error(const tdvp_ctx* ctx);

@@ -52,6 +52,7 @@ OPT_RANK_RTOL = 1
 OPT_KRYLOV_CHECK_ALL = 2
 OPT_QR_KERNEL = 3
 OPT_GRAPH = 4
+OPT_PDL = 5
 
 
 class StatsC(C.Structure):

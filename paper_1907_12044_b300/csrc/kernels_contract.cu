@@ -148,6 +148,7 @@ __device__ __forceinline__ zc load_op(const zc* P, int ld, int op, int row, int 
 __global__ void __launch_bounds__(GEMM_THREADS)
 zgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
              int nbatch, int nsplit) {
+  pdl_wait();
   __shared__ GemmDesc g;
   __shared__ int live;
   __shared__ zc As[TK][TM + 1];
@@ -221,6 +222,7 @@ zgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __
 __global__ void __launch_bounds__(256)
 zgemm_reduce_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
                     int nbatch, int nsplit) {
+  pdl_wait();
   __shared__ GemmDesc g;
   __shared__ int live;
   const int r = blockIdx.y / nbatch, b = blockIdx.y % nbatch;
@@ -243,6 +245,7 @@ zgemm_reduce_kernel(int op, int site, const SiteDev* __restrict__ sd, const Work
 __global__ void __launch_bounds__(256)
 wapply_kernel(int dir, int site, int lanczos, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
               int N_sites) {
+  pdl_wait();
   const int r = blockIdx.z;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const WorkDev& W = wk[r];
@@ -268,6 +271,7 @@ wapply_kernel(int dir, int site, int lanczos, const SiteDev* __restrict__ sd, co
 // Site tensor (Dl*d x Dr) <-> scratch (Dr x Dl*d), realisation r = blockIdx.z.
 __global__ void transpose_site_kernel(int to_scratch, int site, const SiteDev* __restrict__ sd,
                                       const WorkDev* __restrict__ wk, int N_sites) {
+  pdl_wait();
   __shared__ zc tile[32][33];
   const int r = blockIdx.z;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -315,6 +319,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 __global__ void set_identity_kernel(const WorkDev* __restrict__ wk, int n) {
+  pdl_wait();
   const int r = blockIdx.x;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x)
     wk[r].bond2[e] = zmake((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
@@ -323,6 +328,7 @@ __global__ void set_identity_kernel(const WorkDev* __restrict__ wk, int n) {
 // <n> at an electronic site: sum_{l', r} conj(A[l'][1][r]) T1[l'][1][r], T1 = E A.
 __global__ void obs_local_kernel(int site, int slot, const SiteDev* __restrict__ sd,
                                  const WorkDev* __restrict__ wk, int N_sites) {
+  pdl_wait();
   __shared__ double red[32];
   const int r = blockIdx.x;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -339,6 +345,7 @@ __global__ void obs_local_kernel(int site, int slot, const SiteDev* __restrict__
 }
 
 __global__ void obs_norm_kernel(int site, int slot, const WorkDev* __restrict__ wk) {
+  pdl_wait();
   const int r = blockIdx.x;
   const WorkDev& W = wk[r];
   if (threadIdx.x == 0) W.obs[slot] = ((site % 2 == 0) ? W.bond : W.bond2)[0].x;
@@ -347,6 +354,7 @@ __global__ void obs_norm_kernel(int site, int slot, const WorkDev* __restrict__ 
 // <C|w> with C the site-0 tensor (w = H[0] C): energy numerator.
 __global__ void obs_energy_kernel(int slot, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
                                   int N_sites) {
+  pdl_wait();
   __shared__ double red[32];
   const int r = blockIdx.x;
   const SiteDev& s = sd[(long long)r * N_sites + 0];
@@ -367,6 +375,7 @@ __global__ void obs_energy_kernel(int slot, const SiteDev* __restrict__ sd, cons
 // what 0: x <- A[site]; what 1: A[site] <- x; what 2: A[site] <- w
 __global__ void copy_vec_kernel(int what, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
                                 int N_sites) {
+  pdl_wait();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const long long n = (long long)s.Dl * s.d * s.Dr;
@@ -378,6 +387,7 @@ __global__ void copy_vec_kernel(int what, int site, const SiteDev* __restrict__ 
 }
 
 __global__ void reset_ks_kernel(const WorkDev* __restrict__ wk) {
+  pdl_wait();
   if (threadIdx.x == 0) { wk[blockIdx.x].ks->done = 0; wk[blockIdx.x].ks->status = 0; }
 }
 
@@ -390,10 +400,10 @@ cudaError_t launch_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, 
   if (maxM <= 0 || maxN <= 0 || nbatch <= 0) return cudaSuccess;
   if (nsplit < 1) nsplit = 1;
   dim3 grid(cdiv(maxN, TN), cdiv(maxM, TM), R * nbatch * nsplit);
-  zgemm_kernel<<<grid, GEMM_THREADS, 0, st>>>(op, site, sd, wk, N_sites, nbatch, nsplit);
+  { const cudaError_t e_ = launch_pdl(zgemm_kernel, grid, GEMM_THREADS, 0, st, op, site, sd, wk, N_sites, nbatch, nsplit); if (e_ != cudaSuccess) return e_; }
   if (nsplit > 1) {
     dim3 g2(cdiv((long long)maxM * maxN, 256), R * nbatch);
-    zgemm_reduce_kernel<<<g2, 256, 0, st>>>(op, site, sd, wk, N_sites, nbatch, nsplit);
+    { const cudaError_t e_ = launch_pdl(zgemm_reduce_kernel, g2, 256, 0, st, op, site, sd, wk, N_sites, nbatch, nsplit); if (e_ != cudaSuccess) return e_; }
   }
   return cudaGetLastError();
 }
@@ -401,46 +411,46 @@ cudaError_t launch_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, 
 cudaError_t launch_wapply(int dir, int site, int lanczos, const SiteDev* sd, const WorkDev* wk, int R,
                           int N_sites, int max_xy, int n_rows, cudaStream_t st) {
   dim3 grid(cdiv(max_xy, 256), n_rows, R);
-  wapply_kernel<<<grid, 256, 0, st>>>(dir, site, lanczos, sd, wk, N_sites);
+  { const cudaError_t e_ = launch_pdl(wapply_kernel, grid, 256, 0, st, dir, site, lanczos, sd, wk, N_sites); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_transpose_site(int to_scratch, int site, const SiteDev* sd, const WorkDev* wk, int R,
                                   int N_sites, int maxRows, int maxCols, cudaStream_t st) {
   dim3 grid = to_scratch ? dim3(cdiv(maxCols, 32), cdiv(maxRows, 32), R) : dim3(cdiv(maxRows, 32), cdiv(maxCols, 32), R);
-  transpose_site_kernel<<<grid, 256, 0, st>>>(to_scratch, site, sd, wk, N_sites);
+  { const cudaError_t e_ = launch_pdl(transpose_site_kernel, grid, 256, 0, st, to_scratch, site, sd, wk, N_sites); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_identity_bond2(const WorkDev* wk, int R, int n, cudaStream_t st) {
-  set_identity_kernel<<<R, 128, 0, st>>>(wk, n);
+  { const cudaError_t e_ = launch_pdl(set_identity_kernel, R, 128, 0, st, wk, n); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_obs_local(int site, int slot, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
                              cudaStream_t st) {
-  obs_local_kernel<<<R, 256, 0, st>>>(site, slot, sd, wk, N_sites);
+  { const cudaError_t e_ = launch_pdl(obs_local_kernel, R, 256, 0, st, site, slot, sd, wk, N_sites); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_obs_norm(int site, int slot, const WorkDev* wk, int R, cudaStream_t st) {
-  obs_norm_kernel<<<R, 32, 0, st>>>(site, slot, wk);
+  { const cudaError_t e_ = launch_pdl(obs_norm_kernel, R, 32, 0, st, site, slot, wk); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_obs_energy(int slot, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, cudaStream_t st) {
-  obs_energy_kernel<<<R, 256, 0, st>>>(slot, sd, wk, N_sites);
+  { const cudaError_t e_ = launch_pdl(obs_energy_kernel, R, 256, 0, st, slot, sd, wk, N_sites); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy_vec(int what, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxn,
                             cudaStream_t st) {
   dim3 grid(cdiv(maxn, 256), R);
-  copy_vec_kernel<<<grid, 256, 0, st>>>(what, site, sd, wk, N_sites);
+  { const cudaError_t e_ = launch_pdl(copy_vec_kernel, grid, 256, 0, st, what, site, sd, wk, N_sites); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_reset_ks(const WorkDev* wk, int R, cudaStream_t st) {
-  reset_ks_kernel<<<R, 32, 0, st>>>(wk);
+  { const cudaError_t e_ = launch_pdl(reset_ks_kernel, R, 32, 0, st, wk); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }

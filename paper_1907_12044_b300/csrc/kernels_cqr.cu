@@ -152,6 +152,7 @@ __device__ double cta_sum(double v, double* red) {
 __global__ void __launch_bounds__(CT)
 cqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
            double rtol, int dn, int dm) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[CNW];
   __shared__ double sc[4];

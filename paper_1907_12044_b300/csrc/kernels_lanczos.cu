@@ -148,6 +148,7 @@ __device__ void chunk_dots(const WorkDev& W, const VecGeom& g, int j, int tab, i
 }
 
 __global__ void __launch_bounds__(NT) lz_start1(LzArgs a) {
+  pdl_enter();
   __shared__ double red[2 * 8 * NT / 32];
   const int r = blockIdx.y, b = blockIdx.x;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
@@ -162,6 +163,7 @@ __global__ void __launch_bounds__(NT) lz_start1(LzArgs a) {
 }
 
 __global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
+  pdl_enter();
   __shared__ zc h[1];
   const int r = blockIdx.y, b = blockIdx.x;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
 }
 
 __global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
+  pdl_enter();
   __shared__ double red[2 * 8 * NT / 32];
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
@@ -210,6 +213,7 @@ __device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, doubl
 // pass 1 (tab_in = 0, tab_out = 1) or pass 2 (tab_in = 1, norm partials into table 2; the last
 // block to finish then takes the tridiagonal step)
 __global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
+  pdl_enter();
   __shared__ double red[2 * 8 * NT / 32];
   __shared__ zc h[TDVP_KMAX_HARD];
   const int r = blockIdx.y, b = blockIdx.x;
@@ -567,6 +571,7 @@ __device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, doubl
 }
 
 __global__ void __launch_bounds__(NT) lz_next(LzArgs a, int j) {
+  pdl_enter();
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
   if (W.ks->done) return;
@@ -584,6 +589,7 @@ __global__ void __launch_bounds__(NT) lz_next(LzArgs a, int j) {
 }
 
 __global__ void __launch_bounds__(NT) lz_combine(LzArgs a) {
+  pdl_enter();
   __shared__ zc cf[TDVP_KMAX_HARD];
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
@@ -604,6 +610,7 @@ __global__ void __launch_bounds__(NT) lz_combine(LzArgs a) {
 // Loop control of a device-driven solve (one warp).  The body's kernels have all finished when
 // this runs (graph dependency), so every unfinished solve's iteration index can advance.
 __global__ void lz_loop_ctl(LzArgs a, int which) {
+  pdl_enter();
   int active = 0;
   for (int r = threadIdx.x; r < a.R; r += 32) {
     KState* ks = a.wk[r].ks;
@@ -629,33 +636,33 @@ __global__ void lz_loop_ctl(LzArgs a, int which) {
 }  // namespace
 
 cudaError_t launch_lz_loop_ctl(const LzArgs& a, int which, cudaStream_t st) {
-  lz_loop_ctl<<<1, 32, 0, st>>>(a, which);
+  { const cudaError_t e_ = launch_pdl(lz_loop_ctl, 1, 32, 0, st, a, which); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st) {
   dim3 grid(a.nblk, a.R);
-  lz_start1<<<grid, NT, 0, st>>>(a);
-  lz_start2<<<grid, NT, 0, st>>>(a);
+  { const cudaError_t e_ = launch_pdl(lz_start1, grid, NT, 0, st, a); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_pdl(lz_start2, grid, NT, 0, st, a); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_lz_iter_pre(const LzArgs& a, int j, cudaStream_t st) {
   dim3 grid(a.nblk, a.R);
-  lz_dots<<<grid, NT, 0, st>>>(a, j);
-  lz_upd<<<grid, NT, 0, st>>>(a, j, 1);
-  lz_upd<<<grid, NT, 0, st>>>(a, j, 2);
+  { const cudaError_t e_ = launch_pdl(lz_dots, grid, NT, 0, st, a, j); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_pdl(lz_upd, grid, NT, 0, st, a, j, 1); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_pdl(lz_upd, grid, NT, 0, st, a, j, 2); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_lz_iter_post(const LzArgs& a, int j, cudaStream_t st) {
   dim3 grid(a.nblk, a.R);
-  lz_next<<<grid, NT, 0, st>>>(a, j);
+  { const cudaError_t e_ = launch_pdl(lz_next, grid, NT, 0, st, a, j); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_lz_combine(const LzArgs& a, cudaStream_t st) {
   dim3 grid(a.nblk, a.R);
-  lz_combine<<<grid, NT, 0, st>>>(a);
+  { const cudaError_t e_ = launch_pdl(lz_combine, grid, NT, 0, st, a); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }

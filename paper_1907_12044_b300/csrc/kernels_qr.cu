@@ -564,6 +564,7 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
 __global__ void __launch_bounds__(QT)
 bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites, int B,
            double rtol, int dn, int dm) {
+  pdl_wait();
   __shared__ zc Hs[PB * QR_NMAX];
   __shared__ zc L1[PB][PB];
   __shared__ zc L2[PB][PB];

@@ -244,6 +244,7 @@ static_assert(2 * BM * PART_LD * 4 <= STAGE_BYTES, "partial tile must fit in the
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
                 int split, int S) {
+  pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ TcDesc g;
   __shared__ uint64_t full_bar[STAGES];
@@ -438,6 +439,7 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
 // Lenv[site] stacked as the A operand: row = w*Dl + a', k = a
 __global__ void pack_env_l_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
                                   int N_sites, int split) {
+  pdl_enter();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const WorkDev& W = wk[r];
@@ -452,6 +454,7 @@ __global__ void pack_env_l_kernel(int site, const SiteDev* __restrict__ sd, cons
 // Renv[site] as the B operand: row = b', k = w*Dr + b
 __global__ void pack_env_r_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
                                   int N_sites, int split) {
+  pdl_enter();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const WorkDev& W = wk[r];
@@ -467,6 +470,7 @@ __global__ void pack_env_r_kernel(int site, const SiteDev* __restrict__ sd, cons
 // x as the B operand.  kind 0 (site): row = (s b), k = a;  kind 1 (bond D[l][r]): row = r, k = l
 __global__ void pack_x_kernel(int kind, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
                               int N_sites, int split) {
+  pdl_enter();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const WorkDev& W = wk[r];
@@ -485,6 +489,7 @@ __global__ void pack_x_kernel(int kind, int site, const SiteDev* __restrict__ sd
 // T2[(a' s')][(w' b)] = sum_e val * T1[(w a')][(s b)]  over the CSR row (w', s').
 __global__ void wapply_tc_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
                                  int N_sites, int split) {
+  pdl_wait();
   const int r = blockIdx.z;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const WorkDev& W = wk[r];
@@ -514,6 +519,7 @@ __global__ void wapply_tc_kernel(int site, const SiteDev* __restrict__ sd, const
 //   kind 2: conj(A) as A operand, row l', k (s r); kind 3: A as B operand, row (s r), k l
 __global__ void pack_site_kernel(int kind, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
                                  int N_sites, int split) {
+  pdl_wait();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const WorkDev& W = wk[r];
@@ -545,6 +551,7 @@ __global__ void pack_site_kernel(int kind, int site, const SiteDev* __restrict__
 // Renv[site] as the B operand of the right-update first stage: row (w' r'), k r.
 __global__ void pack_renv_rows_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
                                       int N_sites, int split) {
+  pdl_wait();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const WorkDev& W = wk[r];
@@ -565,6 +572,7 @@ __global__ void pack_renv_rows_kernel(int site, const SiteDev* __restrict__ sd, 
 //                    (w, s'); B row (w l), k (s' r').
 __global__ void wapply_env_kernel(int which, int site, const SiteDev* __restrict__ sd,
                                   const WorkDev* __restrict__ wk, int N_sites, int split) {
+  pdl_wait();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
   const WorkDev& W = wk[r];
@@ -629,31 +637,36 @@ cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* w
   const int S = tc_splits(tn * tm, R, maxK);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 1;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = S;
+  if (S > 1) {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = S;
+  } else {
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+  }
   cfg.gridDim = dim3(tn, tm, R * S);
   cfg.blockDim = dim3(TC_THREADS);
   cfg.dynamicSmemBytes = STAGES * STAGE_BYTES;
   cfg.stream = st;
   cfg.attrs = at;
-  cfg.numAttrs = S > 1 ? 1 : 0;
+  cfg.numAttrs = (S > 1 || g_tdvp_pdl) ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel, op, site, sd, wk, N_sites, split, S);
 }
 
 cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
                             long long max_elems, int split, cudaStream_t st) {
   dim3 grid(cdivh(max_elems, 256), R);
-  if (which == 0) pack_env_l_kernel<<<grid, 256, 0, st>>>(site, sd, wk, N_sites, split);
-  else pack_env_r_kernel<<<grid, 256, 0, st>>>(site, sd, wk, N_sites, split);
+  if (which == 0) { const cudaError_t e_ = launch_pdl(pack_env_l_kernel, grid, 256, 0, st, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
+  else { const cudaError_t e_ = launch_pdl(pack_env_r_kernel, grid, 256, 0, st, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
                           long long max_elems, int split, cudaStream_t st) {
   dim3 grid(cdivh(max_elems, 256), R);
-  pack_x_kernel<<<grid, 256, 0, st>>>(kind, site, sd, wk, N_sites, split);
+  { const cudaError_t e_ = launch_pdl(pack_x_kernel, grid, 256, 0, st, kind, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -662,7 +675,7 @@ cudaError_t launch_pack_site(int kind, int site, const SiteDev* sd, const WorkDe
   const int RT = kind == 3 ? BN : BM;
   const long long total = (long long)cdivh(max_rows, RT) * RT * cdivh(max_k, BK) * BK;
   dim3 grid(cdivh(total, 256), R);
-  pack_site_kernel<<<grid, 256, 0, st>>>(kind, site, sd, wk, N_sites, split);
+  { const cudaError_t e_ = launch_pdl(pack_site_kernel, grid, 256, 0, st, kind, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -670,7 +683,7 @@ cudaError_t launch_pack_renv_rows(int site, const SiteDev* sd, const WorkDev* wk
                                   long long max_rows, long long max_k, int split, cudaStream_t st) {
   const long long total = (long long)cdivh(max_rows, BN) * BN * cdivh(max_k, BK) * BK;
   dim3 grid(cdivh(total, 256), R);
-  pack_renv_rows_kernel<<<grid, 256, 0, st>>>(site, sd, wk, N_sites, split);
+  { const cudaError_t e_ = launch_pdl(pack_renv_rows_kernel, grid, 256, 0, st, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
@@ -678,13 +691,13 @@ cudaError_t launch_wapply_env(int which, int site, const SiteDev* sd, const Work
                               long long max_rows, long long max_k, int split, cudaStream_t st) {
   const long long total = (long long)cdivh(max_rows, BN) * BN * cdivh(max_k, BK) * BK;
   dim3 grid(cdivh(total, 256), R);
-  wapply_env_kernel<<<grid, 256, 0, st>>>(which, site, sd, wk, N_sites, split);
+  { const cudaError_t e_ = launch_pdl(wapply_env_kernel, grid, 256, 0, st, which, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_wapply_tc(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int max_xy,
                              int n_rows, int split, cudaStream_t st) {
   dim3 grid(cdivh(max_xy, 256), n_rows, R);
-  wapply_tc_kernel<<<grid, 256, 0, st>>>(site, sd, wk, N_sites, split);
+  { const cudaError_t e_ = launch_pdl(wapply_tc_kernel, grid, 256, 0, st, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }

@@ -29,6 +29,8 @@ struct RealHost {
 
 }  // namespace
 
+int g_tdvp_pdl = 1;
+
 struct tdvp_ctx {
   int dev = 0;
   cudaStream_t st = nullptr;
@@ -1810,6 +1812,9 @@ int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
       return TDVP_OK;
     case TDVP_OPT_GRAPH:
       ctx->graph_on = value != 0.0 ? 1 : 0;
+      return TDVP_OK;
+    case TDVP_OPT_PDL:
+      g_tdvp_pdl = value != 0.0 ? 1 : 0;
       return TDVP_OK;
     case TDVP_OPT_QR_KERNEL: {
       const int c = (int)value;

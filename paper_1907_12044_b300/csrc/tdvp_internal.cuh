@@ -12,6 +12,32 @@
 
 typedef double2 zc;
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be scheduled while its
+// predecessor in the stream is still running; it calls pdl_wait() before touching any memory and
+// lets its own successor start early with pdl_trigger().  In a kernel launched without the
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() { pdl_wait(); pdl_trigger(); }
+
+extern int g_tdvp_pdl;   // 1: launch_pdl sets the programmatic-serialization attribute
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = g_tdvp_pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 #define TDVP_KMAX_HARD 128        // largest Krylov dimension supported
 #define TDVP_VEC_THREADS 256      // threads of the Lanczos vector kernels
 #define TDVP_MAX_VEC_BLOCKS 160   // chunks per vector (bounds the partial-sum table)
