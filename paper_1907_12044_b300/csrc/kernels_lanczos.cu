@@ -22,7 +22,16 @@ constexpr int NT = TDVP_VEC_THREADS;
 constexpr int PSTRIDE = TDVP_KMAX_HARD + 2;
 constexpr int TRI_THREADS = NT;   // the tridiagonal step runs in a block of the vector kernel
 constexpr int MAX_CHEB = 512;
-constexpr int BESSEL_CAP = MAX_CHEB + 128;
+constexpr int BESSEL_CAP = 2 * MAX_CHEB;   // Miller start m = N + 24 + x + 1 with N <= 497, x <= 400
+constexpr double CHEB_XSUB = 400.0;        // largest x of one Chebyshev series (N(400) = 497 terms)
+constexpr int CHEB_MAX_SUB = 64;           // substeps of one exponential at most (x <= 25600)
+
+// Terms of the Jacobi-Anger series exp(i x T~) = sum_{n<=N} (2 - delta_n0) i^n J_n(x) T_n(T~) so
+// that the dropped tail 2 sum_{n>N} |J_n(x)| stays below 1e-17: past n = x the Bessel functions
+// fall off over the Airy transition width ~x^(1/3), so N = x + 12 x^(1/3) + 8 (checked against
+// independently computed J_n for x from 1 to 480; a fixed margin N = x + 30 leaves 3e-11 at x = 50
+// and 1e-4 at x = 480).
+__device__ __forceinline__ int cheb_terms(double x) { return (int)ceil(x + 12.0 * cbrt(x)) + 8; }
 constexpr int TRI_SH = 3 * TRI_THREADS + MAX_CHEB + 2 * (TRI_THREADS / 32) + 8 + 2 * BESSEL_CAP;
 
 struct VecGeom {
@@ -191,6 +200,13 @@ __global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
     const bool bad = !isfinite(nrm);
     ks->status = bad ? -6 : 0;
     ks->done = (nrm == 0.0 || bad) ? 1 : 0;
+    // a zero start vector is finished at k = 0 (the result is zero); a non-finite one is an error
+    if (bad) {
+      a.flags[r] = -1;
+      if (a.devj) atomicExch(W.err, -7);
+    } else if (nrm == 0.0) {
+      a.flags[r] = TDVP_KFLAG_DONE;
+    }
   }
 }
 
@@ -327,7 +343,7 @@ __device__ void bessel_block(double x, int N, double* J, double* cf, double* raw
 // c = exp(i theta T) e_1 for T = tridiag(beta[0..k-2], alpha[0..k-1]) by a Chebyshev expansion on
 // the Gershgorin interval [lo, hi]: exp(i x T~) = sum_n (2 - delta_n0) i^n J_n(x) T_n(T~)
 // (Jacobi-Anger), T~ = (T - c0)/h, x = theta h.  The vectors T_n(T~) e_1 are real.
-// Thread t (< k) owns component t.  Returns false when the expansion would need too many terms.
+// Thread t (< k) owns component t.  Returns false when |x| needs more than CHEB_MAX_SUB substeps.
 __device__ bool tridiag_expi(const double* alpha, const double* beta, int k, double theta, zc* out,
                              double* sh /* >= TRI_SH doubles */) {
   const int t = threadIdx.x;
@@ -364,16 +380,19 @@ __device__ bool tridiag_expi(const double* alpha, const double* beta, int k, dou
   sincos(theta * c0, &sr, &cr);
   const zc ph = zmake(cr, sr);                  // exp(i theta c0)
   const double x = theta * h;
-  const double ax = fabs(x);
-  const int N = (int)ceil(ax) + 30;
-  if (h <= 0.0 || ax < 1e-14) {                 // T is a multiple of the identity
+  if (h <= 0.0 || fabs(x) < 1e-14) {           // T is a multiple of the identity
     if (t < k) out[t] = t == 0 ? ph : zmake(0, 0);
     __syncthreads();
     return true;
   }
-  if (N + 1 > MAX_CHEB) return false;
+  // exp(i x T~) = (exp(i (x/s) T~))^s: s = 1 unless one series would need more than MAX_CHEB terms
+  const int nsub = (int)ceil(fabs(x) / CHEB_XSUB);
+  if (nsub > CHEB_MAX_SUB) return false;
+  const int s = nsub < 1 ? 1 : nsub;
+  const double ax = fabs(x) / s;
+  const int N = cheb_terms(ax);
+  double* cfb = bnd + 8;
   {
-    double* cfb = bnd + 8;
     double* raw = cfb + BESSEL_CAP;
     const int mneed = N + 24 + (int)ax + 2;
     if (mneed + 1 <= BESSEL_CAP) {
@@ -387,6 +406,57 @@ __device__ bool tridiag_expi(const double* alpha, const double* beta, int k, dou
   const double ih = 1.0 / h;
   int Nlast = N;
   while (Nlast > 2 && fabs(J[Nlast]) < 1e-18 && fabs(J[Nlast - 1]) < 1e-18) --Nlast;
+  if (s > 1) {
+    // s substeps on a complex vector u (u = e_1, then the previous substep's result): the same
+    // three-term recurrence on the real and imaginary parts, coefficients i^n (2 - delta) J_n
+    double* vr = vcur;
+    double* vi = cfb;                         // Bessel scratch, free again (>= TRI_THREADS doubles)
+    double ur = (t == 0) ? 1.0 : 0.0, ui = 0.0;
+    for (int q = 0; q < s; ++q) {
+      vr[t] = ur; vi[t] = ui;
+      __syncthreads();
+      double pr = ur, pi = ui, cr = 0.0, ci = 0.0;
+      if (t < k) {
+        const double lr = t > 0 ? vr[t - 1] : 0.0, rr = t < k - 1 ? vr[t + 1] : 0.0;
+        const double li = t > 0 ? vi[t - 1] : 0.0, ri = t < k - 1 ? vi[t + 1] : 0.0;
+        cr = ((at - c0) * pr + bl * lr + br * rr) * ih;
+        ci = ((at - c0) * pi + bl * li + br * ri) * ih;
+      }
+      const double cf1 = 2.0 * J[1] * sgn;
+      double ar = J[0] * pr - cf1 * ci, ai = J[0] * pi + cf1 * cr;
+      __syncthreads();
+      vr[t] = cr; vi[t] = ci;
+      __syncthreads();
+      for (int n = 1; n < Nlast; ++n) {
+        double nr = 0.0, ni = 0.0;
+        if (t < k) {
+          const double lr = t > 0 ? vr[t - 1] : 0.0, rr = t < k - 1 ? vr[t + 1] : 0.0;
+          const double li = t > 0 ? vi[t - 1] : 0.0, ri = t < k - 1 ? vi[t + 1] : 0.0;
+          nr = 2.0 * ((at - c0) * cr + bl * lr + br * rr) * ih - pr;
+          ni = 2.0 * ((at - c0) * ci + bl * li + br * ri) * ih - pi;
+        }
+        const int m = n + 1;
+        double cf = 2.0 * J[m];
+        if (sgn < 0 && (m & 1)) cf = -cf;
+        switch (m & 3) {                      // i^m (nr + i ni)
+          case 0: ar += cf * nr; ai += cf * ni; break;
+          case 1: ar -= cf * ni; ai += cf * nr; break;
+          case 2: ar -= cf * nr; ai -= cf * ni; break;
+          default: ar += cf * ni; ai -= cf * nr; break;
+        }
+        pr = cr; pi = ci; cr = nr; ci = ni;
+        __syncthreads();
+        vr[t] = nr; vi[t] = ni;
+        __syncthreads();
+      }
+      ur = t < k ? ar : 0.0;
+      ui = t < k ? ai : 0.0;
+      __syncthreads();
+    }
+    if (t < k) out[t] = zmul(ph, zmake(ur, ui));
+    __syncthreads();
+    return true;
+  }
   if (k <= 32) {
     // one warp: component t in lane t, neighbours by shuffles, no block barriers in the loop;
     // T_{n+1} e_1 = 2 T~ T_n e_1 - T_{n-1} e_1 with T~ = (T - c0)/h
@@ -547,7 +617,7 @@ __device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, doubl
       ks->k = k;
       ks->notconv = (!conv && beta > 0.0) ? 1 : 0;
       ks->done = 1;
-      flags[r] = k | (ks->notconv << 16);
+      flags[r] = k | (ks->notconv << 16) | TDVP_KFLAG_DONE;
       W.kprev[2 * a.site + a.kind] = k;
       if (a.devj) {
         ks->dim_sum += k;

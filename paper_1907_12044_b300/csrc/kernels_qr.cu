@@ -684,10 +684,9 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
         }
         for (int rr = 0; rr < nb; ++rr) X[(long long)(j0 + rr) * m + c] = y[rr];
       }
-      if (!group_sync(W, B)) return;
-    }
-    if (!fallback) {
-      if (b == 0) {
+      if (it == 1 && b == 0) {
+        // the panel's rows of R, before the barrier that ends the panel: past it the other
+        // blocks start the next panel's first-pass dots, which overwrite S.H1
         for (int e = threadIdx.x; e < nb * n; e += QT) {
           const int rr = e / n, t = e % n, j = j0 + rr;
           zc v = zmake(0, 0);
@@ -700,6 +699,9 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
           J.Rout[J.rtrans ? (long long)t * n + j : (long long)j * n + t] = v;
         }
       }
+      if (!group_sync(W, B)) return;
+    }
+    if (!fallback) {
       for (int c = c0 + threadIdx.x; c < c1; c += QT) {
         double s = colsq[c];
         for (int rr = 0; rr < nb; ++rr) s += zabs2(X[(long long)(j0 + rr) * m + c]);

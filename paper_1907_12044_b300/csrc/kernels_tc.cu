@@ -13,11 +13,15 @@
 // re_hi, im_hi, re_lo, im_lo one after another.  Padding rows/columns are zero.  A whole tile is
 // therefore one contiguous block that a 1-D bulk TMA copy moves into shared memory.
 //
-// GEMM kernel: 128 threads per CTA and S CTAs per 128 x 64 output tile, each over its own range
-// of K tiles (split-K; S = 1 when the output alone fills the GPU).  Thread 0 issues the bulk
-// copies (two-stage ring, mbarrier with transaction bytes) and the MMAs (tcgen05.mma, commit to
-// an mbarrier); all four warps then move the accumulators (tcgen05.ld) into shared memory, which
-// the copies no longer use.  The S CTAs of a tile form one thread-block cluster: after a cluster
+// GEMM kernel: 160 threads per CTA and S CTAs per 128 x 64 output tile, each over its own range
+// of K tiles (split-K; S = 1 when the output alone fills the GPU).  One thread of warp 4 issues
+// the bulk copies (two-stage ring, mbarrier with transaction bytes) and the MMAs (tcgen05.mma,
+// commit to mbarriers).  The main products of each K tile go into a fresh tensor-memory
+// accumulator (two alternate), which warps 0-3 add into FP32 registers (tcgen05.ld) while the
+// next tile is multiplied: the tensor cores accumulate with truncation, and a sum over all of K
+// of same-signed terms (environment diagonals) would drift low by about K/8 half-ulps, whereas
+// the register sums round to nearest.  The compensation terms keep one accumulator.  The rows
+// then go into shared memory, which the copies no longer use.  The S CTAs of a tile form one thread-block cluster: after a cluster
 // barrier CTA q sums rows [q*128/S, (q+1)*128/S) of all S partial tiles, read through distributed
 // shared memory in the fixed order 0..S-1 (deterministic), and writes them with coalesced stores.
 // Every wait is bounded: on timeout the CTA records an error, drains its copies and MMAs with
@@ -33,8 +37,12 @@ constexpr int B_TILE = BN * BK * 4;     //  8 KB per plane
 constexpr int NPL = 4;                  // planes: re_hi, im_hi, re_lo, im_lo
 constexpr int STAGE_BYTES = NPL * (A_TILE + B_TILE);   // 96 KB
 constexpr int STAGES = 2;
-constexpr int TC_THREADS = 128;
-constexpr uint32_t TMEM_COLS = 128;     // Dr: 0..63, Di: 64..127
+constexpr int TC_EPI = 128;             // warps 0-3: accumulator drains and epilogue (one TMEM lane each)
+constexpr int TC_THREADS = TC_EPI + 32; // warp 4: bulk copies and MMAs
+// tensor memory: main accumulators 0 and 1 (hi*hi products of alternate K tiles) at columns
+// 0..127 and 128..255, the compensation terms (hi*lo + lo*hi) at 256..383; Dr then Di in each
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC_SMALL = 256;
 constexpr unsigned long long WAIT_NS = 1000000000ull;   // every wait gives up after 1 s
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -68,6 +76,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   while (!mbar_try(bar, parity))
     if (gtimer() - t0 > WAIT_NS) return false;
   return true;
+}
+// bounded wait that also gives up as soon as *stop becomes nonzero
+__device__ __forceinline__ bool mbar_wait_or(uint64_t* bar, uint32_t parity, const volatile int* stop) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity)) {
+    if (*stop) return false;
+    if (gtimer() - t0 > WAIT_NS) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -249,10 +269,12 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
   __shared__ TcDesc g;
   __shared__ uint64_t full_bar[STAGES];
   __shared__ uint64_t done_bar[STAGES];
+  __shared__ uint64_t acc_full[2];     // main accumulator b holds a finished K tile
+  __shared__ uint64_t acc_free[2];     // main accumulator b has been drained
   __shared__ uint64_t drain_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int live, abort_flag, last_stage;
-  __shared__ uint32_t last_parity;
+  __shared__ int live;
+  __shared__ volatile int abort_flag, drain_fail;
   const int r = blockIdx.z / S;
   const int sidx = S > 1 ? (int)cluster_rank() : 0;
   const WorkDev& W = wk[r];
@@ -261,14 +283,16 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
     live = tc_desc(op, site, sdr, W, g) && !(g.lanczos && W.ks->done) && (int)blockIdx.y * BM < g.M &&
            (int)blockIdx.x * BN < g.N;
     abort_flag = 0;
+    drain_fail = 0;
   }
   __syncthreads();
   // the S CTAs of a cluster share realisation and output tile, so all of them leave here or none
   if (!live) return;
-  const int warp = threadIdx.x / 32;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (warp == 0) tmem_alloc(&tmem_base, TMEM_COLS);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&done_bar[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_free[b], TC_EPI); }
     mbar_init(&drain_bar, 1);
     mbar_fence_init();
   }
@@ -282,104 +306,143 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
   const int mt = blockIdx.y, nt = blockIdx.x;
   const int npl = split ? 4 : 2;
   const uint32_t stage_tx = (uint32_t)npl * (A_TILE + B_TILE);
-  if (threadIdx.x == 0) {
-    last_stage = -1;
-    last_parity = 0;
-    auto issue = [&](int kt) {
-      const int s = kt % STAGES;
-      unsigned char* st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full_bar[s], stage_tx);
-      for (int p = 0; p < npl; ++p) {
-        bulk_load(st + p * A_TILE, g.A + ((long long)(mt * nkt_all + kt0 + kt) * NPL + p) * A_TILE, A_TILE,
-                  &full_bar[s]);
-        bulk_load(st + NPL * A_TILE + p * B_TILE, g.B + ((long long)(nt * nkt_all + kt0 + kt) * NPL + p) * B_TILE,
-                  B_TILE, &full_bar[s]);
-      }
-    };
-    const uint32_t id_pos = idesc_tf32(false), id_neg = idesc_tf32(true);
-    const uint32_t dr = tmem, di = tmem + BN;
-    int issued = 0;
-    for (; issued < STAGES && issued < nkt; ++issued) issue(issued);
-    bool started = false;
-    for (int kt = 0; kt < nkt && !abort_flag; ++kt) {
-      const int s = kt % STAGES;
-      const uint32_t par = (uint32_t)((kt / STAGES) & 1);
-      if (!mbar_wait(&full_bar[s], par)) { abort_flag = 1; break; }
-      tc_after();
-      const uint32_t abase = su32(smem + s * STAGE_BYTES);
-      const uint32_t bbase = abase + NPL * A_TILE;
+  // The tensor cores add into an FP32 accumulator with truncation, so a long sum of same-signed
+  // terms (the diagonal of an environment, sum_k |A_k|^2 weighted by the MPO) loses about half an
+  // ulp per addition, always downward.  The main products of each K tile therefore go into a fresh
+  // accumulator (two, alternating), which warps 0-3 add into FP32 registers with rounding to
+  // nearest while the next tile is multiplied; the compensation terms, 2^-11 smaller, keep one
+  // accumulator for the whole K range.
+  float ar[BN], ai[BN];
 #pragma unroll
-      for (int ks = 0; ks < BK / 8; ++ks) {
-        const uint32_t ko = ks * 256;   // 8 TF32 = 2 core matrices of 128 B
-        const uint64_t arh = sdesc(abase + 0 * A_TILE + ko), aih = sdesc(abase + 1 * A_TILE + ko);
-        const uint64_t brh = sdesc(bbase + 0 * B_TILE + ko), bih = sdesc(bbase + 1 * B_TILE + ko);
-        const uint32_t acc = started ? 1u : 0u;
-        mma_tf32(dr, arh, brh, id_pos, acc);
-        mma_tf32(dr, aih, bih, id_neg, 1u);
-        mma_tf32(di, aih, brh, id_pos, acc);
-        mma_tf32(di, arh, bih, id_pos, 1u);
-        if (split) {
-          const uint64_t arl = sdesc(abase + 2 * A_TILE + ko), ail = sdesc(abase + 3 * A_TILE + ko);
-          const uint64_t brl = sdesc(bbase + 2 * B_TILE + ko), bil = sdesc(bbase + 3 * B_TILE + ko);
-          mma_tf32(dr, arh, brl, id_pos, 1u);
-          mma_tf32(dr, arl, brh, id_pos, 1u);
-          mma_tf32(dr, aih, bil, id_neg, 1u);
-          mma_tf32(dr, ail, bih, id_neg, 1u);
-          mma_tf32(di, aih, brl, id_pos, 1u);
-          mma_tf32(di, ail, brh, id_pos, 1u);
-          mma_tf32(di, arh, bil, id_pos, 1u);
-          mma_tf32(di, arl, bih, id_pos, 1u);
+  for (int q = 0; q < BN; ++q) { ar[q] = 0.f; ai[q] = 0.f; }
+  if (warp == TC_EPI / 32) {
+    if (lane == 0) {
+      auto issue = [&](int kt) {
+        const int s = kt % STAGES;
+        unsigned char* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full_bar[s], stage_tx);
+        for (int p = 0; p < npl; ++p) {
+          bulk_load(st + p * A_TILE, g.A + ((long long)(mt * nkt_all + kt0 + kt) * NPL + p) * A_TILE, A_TILE,
+                    &full_bar[s]);
+          bulk_load(st + NPL * A_TILE + p * B_TILE, g.B + ((long long)(nt * nkt_all + kt0 + kt) * NPL + p) * B_TILE,
+                    B_TILE, &full_bar[s]);
         }
-        started = true;
+      };
+      const uint32_t id_pos = idesc_tf32(false), id_neg = idesc_tf32(true);
+      const uint32_t sr = tmem + ACC_SMALL, si = sr + BN;
+      int issued = 0;
+      for (; issued < STAGES && issued < nkt; ++issued) issue(issued);
+      for (int kt = 0; kt < nkt && !abort_flag; ++kt) {
+        const int s = kt % STAGES, b = kt & 1;
+        const uint32_t par = (uint32_t)((kt / STAGES) & 1);
+        if (!mbar_wait(&full_bar[s], par)) { abort_flag = 1; break; }
+        // main accumulator b is free once the drain of tile kt - 2 has read it
+        if (kt >= 2 && !mbar_wait_or(&acc_free[b], (uint32_t)(((kt - 2) >> 1) & 1), &drain_fail)) {
+          abort_flag = 1;
+          break;
+        }
+        tc_after();
+        const uint32_t dr = tmem + (uint32_t)b * (2 * BN), di = dr + BN;
+        const uint32_t abase = su32(smem + s * STAGE_BYTES);
+        const uint32_t bbase = abase + NPL * A_TILE;
+#pragma unroll
+        for (int ks = 0; ks < BK / 8; ++ks) {
+          const uint32_t ko = ks * 256;   // 8 TF32 = 2 core matrices of 128 B
+          const uint64_t arh = sdesc(abase + 0 * A_TILE + ko), aih = sdesc(abase + 1 * A_TILE + ko);
+          const uint64_t brh = sdesc(bbase + 0 * B_TILE + ko), bih = sdesc(bbase + 1 * B_TILE + ko);
+          const uint32_t acc = ks > 0 ? 1u : 0u;
+          mma_tf32(dr, arh, brh, id_pos, acc);
+          mma_tf32(dr, aih, bih, id_neg, 1u);
+          mma_tf32(di, aih, brh, id_pos, acc);
+          mma_tf32(di, arh, bih, id_pos, 1u);
+          if (split) {
+            const uint32_t accs = (kt > 0 || ks > 0) ? 1u : 0u;
+            const uint64_t arl = sdesc(abase + 2 * A_TILE + ko), ail = sdesc(abase + 3 * A_TILE + ko);
+            const uint64_t brl = sdesc(bbase + 2 * B_TILE + ko), bil = sdesc(bbase + 3 * B_TILE + ko);
+            mma_tf32(sr, arh, brl, id_pos, accs);
+            mma_tf32(sr, arl, brh, id_pos, 1u);
+            mma_tf32(sr, aih, bil, id_neg, 1u);
+            mma_tf32(sr, ail, bih, id_neg, 1u);
+            mma_tf32(si, aih, brl, id_pos, accs);
+            mma_tf32(si, ail, brh, id_pos, 1u);
+            mma_tf32(si, arh, bil, id_pos, 1u);
+            mma_tf32(si, arl, bih, id_pos, 1u);
+          }
+        }
+        mma_commit(&done_bar[s]);
+        mma_commit(&acc_full[b]);
+        if (issued < nkt) {
+          // stage s is refilled once the MMAs that read it have completed
+          if (!mbar_wait(&done_bar[s], par)) { abort_flag = 1; break; }
+          issue(issued);
+          ++issued;
+        }
       }
-      mma_commit(&done_bar[s]);
-      last_stage = s;
-      last_parity = par;
-      if (issued < nkt) {
-        // stage s is refilled once the MMAs that read it have completed
-        if (!mbar_wait(&done_bar[s], par)) { abort_flag = 1; break; }
-        issue(issued);
-        ++issued;
+      if (abort_flag) {
+        // drain (bounded): the newest copy of every stage, then every MMA issued so far
+        for (int s = 0; s < STAGES; ++s) {
+          int last = -1;
+          for (int kt = 0; kt < issued; ++kt) if (kt % STAGES == s) last = kt;
+          if (last >= 0) mbar_wait(&full_bar[s], (uint32_t)((last / STAGES) & 1));
+        }
+        mma_commit(&drain_bar);
+        mbar_wait(&drain_bar, 0);
+        atomicExch(W.err, -5);
       }
     }
-    if (abort_flag) {
-      // drain (bounded): the newest copy of every stage, then every MMA issued so far
-      for (int s = 0; s < STAGES; ++s) {
-        int last = -1;
-        for (int kt = 0; kt < issued; ++kt) if (kt % STAGES == s) last = kt;
-        if (last >= 0) mbar_wait(&full_bar[s], (uint32_t)((last / STAGES) & 1));
+    __syncwarp();
+  } else {
+    // drains: warp w reads TMEM lanes 32w..32w+31, thread = output row of the tile
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    bool ok = true;
+    for (int kt = 0; kt < nkt; ++kt) {
+      const int b = kt & 1;
+      const bool got = mbar_wait_or(&acc_full[b], (uint32_t)((kt >> 1) & 1), &abort_flag);
+      if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+      tc_after();
+#pragma unroll
+      for (int cb = 0; cb < BN; cb += 16) {
+        float v[16];
+        tmem_ld16(lane_addr + (uint32_t)b * (2 * BN) + cb, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ar[cb + q] += v[q];
+        tmem_ld16(lane_addr + (uint32_t)b * (2 * BN) + BN + cb, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ai[cb + q] += v[q];
       }
-      mma_commit(&drain_bar);
-      mbar_wait(&drain_bar, 0);
-      atomicExch(W.err, -5);
+      tc_before();
+      mbar_arrive(&acc_free[b]);
+    }
+    if (!ok) {
+      if (lane == 0) drain_fail = 1;
+    } else if (split && nkt > 0) {
+      // every MMA has completed with the last tile's commit
+#pragma unroll
+      for (int cb = 0; cb < BN; cb += 16) {
+        float v[16];
+        tmem_ld16(lane_addr + ACC_SMALL + cb, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ar[cb + q] += v[q];
+        tmem_ld16(lane_addr + ACC_SMALL + BN + cb, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ai[cb + q] += v[q];
+      }
     }
   }
+  tc_before();
   __syncthreads();
-  // accumulators complete once the last commit's barrier flips (no K tiles: the partial is zero)
-  bool ok = !abort_flag;
-  if (ok && last_stage >= 0) ok = mbar_wait(&done_bar[last_stage], last_parity);
   tc_after();
+  // copies and MMAs are all complete here (or drained after an abort)
+  const bool ok = !abort_flag && !drain_fail;
   if (!ok && threadIdx.x == 0) atomicExch(W.err, -5);
-  // ---- accumulators -> shared memory partial tile part[plane][row][col] ----
+  // ---- accumulated rows -> shared memory partial tile part[plane][row][col] ----
   float* part = reinterpret_cast<float*>(smem);
-  {
-    const int row = warp * 32 + (threadIdx.x % 32);
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    const bool have = ok && last_stage >= 0;
-    for (int cb = 0; cb < BN; cb += 16) {
-      float vr[16], vi[16];
-      if (have) {
-        tmem_ld16(lane_addr + cb, vr);
-        tmem_ld16(lane_addr + BN + cb, vi);
-      } else {
+  if (warp < TC_EPI / 32) {
+    const int row = warp * 32 + lane;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) { vr[q] = 0.f; vi[q] = 0.f; }
-      }
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        part[row * PART_LD + cb + q] = vr[q];
-        part[BM * PART_LD + row * PART_LD + cb + q] = vi[q];
-      }
+    for (int q = 0; q < BN; ++q) {
+      part[row * PART_LD + q] = ok ? ar[q] : 0.f;
+      part[BM * PART_LD + row * PART_LD + q] = ok ? ai[q] : 0.f;
     }
   }
   tc_before();

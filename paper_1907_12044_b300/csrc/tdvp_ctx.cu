@@ -1006,7 +1006,7 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
     if (f < 0) return fail(ctx, TDVP_ERR_NAN, "Lanczos: non-finite value or unsupported exponent");
     if (f == 0) return fail(ctx, TDVP_ERR_KRYLOV_NOT_CONVERGED, "Lanczos: solve did not finish");
     const int k = f & 0xffff;
-    if (f >> 16) { ctx->stats.not_converged++; if (notconv) *notconv = 1; }
+    if ((f >> 16) & 1) { ctx->stats.not_converged++; if (notconv) *notconv = 1; }
     kmaxr = std::max(kmaxr, k);
     ctx->stats.krylov_dim_sum += k;
     ctx->stats.krylov_dim_max = std::max(ctx->stats.krylov_dim_max, k);
@@ -1314,15 +1314,22 @@ int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const doub
     off += n;
   }
   const Views v = one_view(ctx, r);
-  // right-canonicalise: C_i = D_i R_i from the last site, D_i absorbed into site i-1
+  // right-canonicalise: C_i = D_i R_i from the last site, D_i absorbed into site i-1, which is
+  // then normalised (x = C/||C||, C <- x): the norm of a generic product of site tensors grows or
+  // shrinks geometrically with the chain length, and only the normalised state is wanted
   for (int i = N - 1; i >= 1; --i) {
     if ((rc = gauge_qr(ctx, v, i, 1))) return rc;
     const Dims m = maxdims(ctx, i - 1, v);
     if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
     LAUNCH(launch_copy_vec(1, i - 1, v.sd, v.wk, v.R, N, m.Dl * ctx->d[i - 1] * m.Dr, ctx->st));
+    LzArgs a{};
+    a.sd = v.sd; a.wk = v.wk; a.R = 1; a.N_sites = N; a.site = i - 1; a.kind = 0; a.src = 1; a.dst = 1;
+    a.kmax = ctx->kmax; a.nblk = nblk_for((long long)m.Dl * ctx->d[i - 1] * m.Dr); a.flags = v.flags;
+    LAUNCH(launch_lz_start(a, ctx->st));
+    ctx->stats.kernel_launches++;
+    LAUNCH(launch_copy_vec(1, i - 1, v.sd, v.wk, 1, N, m.Dl * ctx->d[i - 1] * m.Dr, ctx->st));
   }
-  // normalise the centre: x = C/||C||, C <- x
-  {
+  if (N == 1) {
     LzArgs a{};
     const Dims m = maxdims(ctx, 0, v);
     a.sd = v.sd; a.wk = v.wk; a.R = 1; a.N_sites = N; a.site = 0; a.kind = 0; a.src = 1; a.dst = 1;

@@ -39,6 +39,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 }
 
 #define TDVP_KMAX_HARD 128        // largest Krylov dimension supported
+#define TDVP_KFLAG_DONE (1 << 20) // finished-solve bit of a Krylov flag word: k | notconv << 16 | this
 #define TDVP_VEC_THREADS 256      // threads of the Lanczos vector kernels
 #define TDVP_MAX_VEC_BLOCKS 160   // chunks per vector (bounds the partial-sum table)
 #define TDVP_VEC_CHUNK 256        // elements per chunk before the cap: one per thread, so a
@@ -217,7 +218,7 @@ struct LzArgs {
   int kmax;
   int jcheck;       // convergence is tested only once k >= jcheck
   int nblk;         // chunks per vector (max over realisations)
-  int* flags;       // [R] device: Krylov dimension once a solve is done, -1 on failure
+  int* flags;       // [R] device: k | notconv << 16 | TDVP_KFLAG_DONE once a solve is done, -1 on failure
   const float* mlp; // learned controller weights (null: tests start at jcheck)
   float* log;       // solve log rows [8 features, k] (null: no logging)
   unsigned* log_count;

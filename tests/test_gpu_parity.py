@@ -20,7 +20,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_1907_12044_b300 as pkg  # noqa: E402
-from gpu_util import engine_for, oracle_from_gpu_tensors, rel_pop_err  # noqa: E402
+from gpu_util import engine_for, oracle_from_gpu_tensors, rel_pop_err, debug_qr_or_rejected  # noqa: E402
 
 POP_TOL = 1e-10
 
@@ -37,22 +37,6 @@ def c1_random():
 
 # -1: default choice; 0: cooperative-grid kernel; C > 0: cluster kernel with C CTAs
 QR_KERNELS = [-1, 0, 1, 2, 4, 8, 16]
-
-
-def cluster_fits(C, m, n):
-    """Whether an n x m QR fits the cluster kernel's shared memory with C CTAs (220 KiB each)."""
-    ld = (-(-m // C)) | 1
-    return C <= m and 16 * (n * ld + 2 * (n + 4) + 3 * n) + 8 * ld <= 220 * 1024
-
-
-def debug_qr_or_rejected(eng, kernel, C):
-    """debug_qr, or None after checking that a forced cluster size too small for C is rejected."""
-    m, n = C.shape
-    if kernel > 0 and not cluster_fits(kernel, m, n):
-        with pytest.raises(pkg.TDVPError):
-            eng.debug_qr(C)
-        return None
-    return eng.debug_qr(C)
 
 
 @pytest.fixture
@@ -157,6 +141,43 @@ def test_heff_and_expm_match_oracle_at_c1_sites(c1_random, site):
         assert np.abs(out - outo).max() <= 1e-10 * np.abs(outo).max()
     finally:
         eng.center_to_zero(0)
+
+
+@pytest.mark.parametrize("x_target", [30.0, 250.0, 1500.0, 6000.0])
+def test_expm_wide_exponents_match_dense_exponential(x_target):
+    """exp(-i tau H_eff) C at a 32-dimensional site, where the Lanczos space reaches the whole
+    space (k = n) and the result is the exact exponential, for theta ||H_eff|| from a short
+    Chebyshev series up to several substeps.  Pinned to a dense matrix exponential of H_eff; the
+    norm is preserved exactly by the Krylov construction."""
+    p = wl.tiny_chain()
+    tens = wl.random_mps_tensors(p.phys_dims(), 4, seed=5)
+    eng = engine_for(p, tensors=tens)
+    site = 3
+    eng.move_center(0, site)
+    mps = eng.get_mps(0)
+    W = TDVPState.start(p, D=1).W
+    L = np.ones((1, 1, 1), complex)
+    for j in range(site):
+        L = env_left(L, mps[j], W[j])
+    R = np.ones((1, 1, 1), complex)
+    for j in range(len(mps) - 1, site, -1):
+        R = env_right(R, mps[j], W[j])
+    C = mps[site]
+    n = C.size
+    assert n == 32
+    H = np.zeros((n, n), complex)
+    for q in range(n):
+        e = np.zeros(n, complex)
+        e[q] = 1.0
+        H[:, q] = heff_apply(L, W[site], R, e.reshape(C.shape)).ravel()
+    ev, U = np.linalg.eigh(0.5 * (H + H.conj().T))
+    tau = x_target / (0.5 * (ev[-1] - ev[0]))     # the phase theta of exp(-i theta H_eff)
+    out, k = eng.debug_expm(0, site, -1j * tau, 1e-12, C)
+    ref = (U @ (np.exp(-1j * tau * ev) * (U.conj().T @ C.ravel()))).reshape(C.shape)
+    assert 1 <= k <= n
+    assert abs(np.linalg.norm(out) - np.linalg.norm(C)) <= 1e-12 * np.linalg.norm(C)
+    assert np.abs(out - ref).max() <= 1e-9 * np.abs(ref).max()
+    eng.close()
 
 
 # ------------------------------------------------------------------ whole time steps
