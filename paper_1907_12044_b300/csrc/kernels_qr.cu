@@ -204,6 +204,17 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
+// 1/sqrt(s) for s in [2^-100, 2^100]: the FP32 estimate refined by two Newton steps
+// y <- y (3 - s y^2) / 2 (each squares the relative error), about 8 FP64 instructions instead of an
+// FP64 square root and division, which matter on a serial chain where every FP64 instruction of a
+// lone warp costs tens of cycles
+__device__ __forceinline__ double rsqrt_nr(double s) {
+  double y = (double)rsqrtf((float)s);
+  y = y * fma(-0.5 * s * y, y, 1.5);
+  y = y * fma(-0.5 * s * y, y, 1.5);
+  return y;
+}
+
 // fixed-order sum of one double per block (every block gets the same value)
 __device__ double sum_over_blocks(const zc* P, int B) {
   const int lane = threadIdx.x % 32;
@@ -224,25 +235,27 @@ struct Scratch {
 
 // ---- rank-deficient tail ----
 // Taken after a dropped row j.  With Q_t (t < J0 = j+1) final, rows J0..n-1 are projected twice
-// onto them (block Gram-Schmidt); a row whose residual is <= thresh/2 is dropped under the exact
-// rule as well, since the exact process tests it against a superset of these Q_t (residuals only
-// shrink) and the rounding differences are O(eps ||x||).  The completions are then built one per group barrier:
+// onto them (block Gram-Schmidt); a row whose residual is <= max(thresh/2, thresh - 1e-10 ||X||_F)
+// is dropped under the exact rule as well, since the exact process tests it against a superset
+// of these Q_t (residuals only shrink) and the two computed residuals differ by rounding only,
+// at most n m eps ||x|| < 1e-10 ||x|| <= 1e-10 ||X||_F for n <= 256, m <= 16384.  The completions are then built one per group barrier:
 // rows are kept unnormalised with their squared norms (so no row another block reads is
 // rewritten) and every block picks the next unit vector itself, scanning forward from the
 // previous one.  A completion is e_p minus its projection with the exact
 // first-pass coefficients conj(Q_t[p]); being at distance >= 1/2 from the span (or the farthest
 // unit vector), one pass leaves it orthogonal to O(eps).  Finally rows are normalised and the
 // R coefficients of the dropped rows against the completions are taken from the backed-up rows.
-// Only the prefix of rows whose residual is <= thresh/2 is finished this way (a later row may
+// Only the prefix of rows that are certainly dropped is finished this way (a later row may
 // be kept); the rows after it are restored and return to the row path.  Returns the number of
 // rows finished (0: none, rows restored), -1 when a group barrier gave up.
 
 constexpr int TAIL_KB = 8;   // completions per group barrier in the tail
 
 __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J0, int j0, int pend, int b, int B,
-                       int gw, int nwarps, int c0, int c1, double thresh, zc* Hs, double* red, double* ens,
-                       int* flag) {
+                       int gw, int nwarps, int c0, int c1, double thresh, double fro, zc* Hs, double* red,
+                       double* ens, int* flag) {
   __shared__ zc Gb[TAIL_KB][TAIL_KB], Lb[TAIL_KB][TAIL_KB], Li[TAIL_KB][TAIL_KB];
+  __shared__ double Ldi[TAIL_KB];                       // 1 / L_kk
   __shared__ zc Yb[QT];
   __shared__ int tflag[TAIL_KB + 1];
   const int n = J.n, m = J.m, Tn = n - J0, lane = threadIdx.x % 32;
@@ -250,7 +263,7 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
   zc* BK = W.qtail;                                     // [n][m] backup of rows J0..n-1
   zc* HT1 = BK + (long long)n * m;                      // [n][n]
   zc* HT2 = HT1 + (long long)n * n;                     // [n][n]
-  double* TPN = reinterpret_cast<double*>(HT2 + (long long)n * n);   // [n][B]
+  double* TPN = reinterpret_cast<double*>(HT2 + (long long)n * n);   // [n][B] residual norms
   for (long long e = threadIdx.x; e < (long long)Tn * (c1 - c0); e += QT) {
     const int j = J0 + (int)(e / (c1 - c0)), c = c0 + (int)(e % (c1 - c0));
     BK[(long long)j * m + c] = X[(long long)j * m + c];
@@ -291,10 +304,13 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
     __shared__ int first_bad;
     if (threadIdx.x == 0) first_bad = Tn;
     __syncthreads();
-    for (int a = threadIdx.x; a < Tn; a += QT) {
+    // certain-drop bound (squared), the same in every block: fro = ||X||_F
+    const double lim = fmax(0.5 * thresh, thresh - 1e-10 * fro), lim2 = lim * lim;
+    for (int a = threadIdx.x / 32; a < Tn; a += NW) {
       double s = 0;
-      for (int bb = 0; bb < B; ++bb) s += __ldcg(TPN + (long long)a * B + bb);
-      if (!(sqrt(s) <= 0.5 * thresh)) atomicMin(&first_bad, a);
+      for (int bb = lane; bb < B; bb += 32) s += __ldcg(TPN + (long long)a * B + bb);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0 && !(s <= lim2)) atomicMin(&first_bad, a);
     }
     __syncthreads();
     Tc = first_bad;
@@ -435,7 +451,8 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
         for (int jj = 0; jj < Kc; ++jj) {
           const double sp = Gb[jj][jj].x;
           if (!(sp >= 0.25)) { kgood = jj; break; }
-          const double d = sqrt(sp), inv = 1.0 / d;
+          const double inv = rsqrt_nr(sp), d = sp * inv;   // sp in [1/4, 1]
+          if (lane == 0) Ldi[jj] = inv;
           for (int i = lane; i < Kc; i += 32)
             Lb[i][jj] = (i < jj) ? zmake(0, 0) : (i == jj ? zmake(d, 0) : zscale(Gb[i][jj], inv));
           __syncwarp();
@@ -454,7 +471,7 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
     if (K >= 2) {
       // Li = L^{-1} (lower triangular), one warp per column
       for (int cc = wid; cc < K; cc += NW) {
-        if (lane == 0) Li[cc][cc] = zmake(1.0 / Lb[cc][cc].x, 0.0);
+        if (lane == 0) Li[cc][cc] = zmake(Ldi[cc], 0.0);
         for (int i = 0; i < cc; ++i) if (lane == 0) Li[i][cc] = zmake(0, 0);
         __syncwarp();
         for (int i = cc + 1; i < K; ++i) {
@@ -464,7 +481,7 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
             s2.x += __shfl_xor_sync(0xffffffffu, s2.x, o);
             s2.y += __shfl_xor_sync(0xffffffffu, s2.y, o);
           }
-          if (lane == 0) Li[i][cc] = zscale(s2, -1.0 / Lb[i][i].x);
+          if (lane == 0) Li[i][cc] = zscale(s2, -Ldi[i]);
           __syncwarp();
         }
       }
@@ -517,11 +534,14 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
   }
   __syncthreads();
   // normalise the completions on the slab, add them to the column sums the row path uses, and
-  // put the rows after them back as they were
-  for (int a = 0; a < Tc; ++a) {
-    const double inv = ens[a] > 0.0 ? 1.0 / sqrt(ens[a]) : 0.0;
+  // put the rows after them back as they were.  The reciprocal norms are computed once per row
+  // (into the second half of ens, whose single-completion scales are no longer needed).
+  for (int a = threadIdx.x; a < Tc; a += QT) ens[QR_NMAX + a] = ens[a] > 0.0 ? 1.0 / sqrt(ens[a]) : 0.0;
+  __syncthreads();
+  for (long long e = threadIdx.x; e < (long long)Tc * (c1 - c0); e += QT) {
+    const int a = (int)(e / (c1 - c0)), c = c0 + (int)(e % (c1 - c0));
     zc* x = X + (long long)(J0 + a) * m;
-    for (int c = c0 + threadIdx.x; c < c1; c += QT) x[c] = zscale(x[c], inv);
+    x[c] = zscale(x[c], ens[QR_NMAX + a]);
   }
   __syncthreads();
   for (int c = c0 + threadIdx.x; c < c1; c += QT) {
@@ -570,6 +590,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
   __shared__ zc L2[PB][PB];
   __shared__ zc Gs[PB][PB];
   __shared__ double Gd[PB];
+  __shared__ double Ldi[PB];            // 1 / L_kk of the current Cholesky factor
   __shared__ zc sdot[NW];
   __shared__ double red[NW];
   __shared__ int flag[2 + 2 * NW];
@@ -655,7 +676,8 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
         for (int jj = 0; jj < nb; ++jj) {
           const double s = Gs[jj][jj].x;            // Schur complement pivot
           if (!(s > 0.0) || (it == 0 && (s <= 1e-10 * Gd[jj] || s <= 100.0 * thresh * thresh))) { bad = it + 1; break; }
-          const double d = sqrt(s), inv = 1.0 / d;
+          const double inv = (s > 1e-30 && s < 1e30) ? rsqrt_nr(s) : 1.0 / sqrt(s), d = s * inv;
+          if (lane == 0) Ldi[jj] = inv;
           for (int i = lane; i < nb; i += 32)
             Lc[i][jj] = (i < jj) ? zmake(0, 0) : (i == jj ? zmake(d, 0) : zscale(Gs[i][jj], inv));
           __syncwarp();
@@ -680,7 +702,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
         for (int rr = 0; rr < nb; ++rr) {
           zc v = X[(long long)(j0 + rr) * m + c];
           for (int k = 0; k < rr; ++k) v = zfms(Lc[rr][k], y[k], v);
-          y[rr] = zscale(v, 1.0 / Lc[rr][rr].x);
+          y[rr] = zscale(v, Ldi[rr]);
         }
         for (int rr = 0; rr < nb; ++rr) X[(long long)(j0 + rr) * m + c] = y[rr];
       }
@@ -764,7 +786,7 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
       }
       if (!group_sync(W, B)) return;
       const double s1 = sum_over_blocks(S.Pn, B);
-      const bool full = sqrt(s1) > thresh;
+      const bool full = s1 > thresh * thresh;
       double en;
       if (full) {
         // (C)
@@ -837,7 +859,8 @@ bqr_kernel(int dir, int site, const SiteDev* __restrict__ sd, const WorkDev* __r
       // after a dropped row, try to finish every later row as a completion in one go
       if (!full && tail_tries < 8 && n - (j + 1) >= 2) {
         ++tail_tries;
-        const int done = qr_tail(J, W, S, j + 1, j0, j0 + nb, b, B, gw, nwarps, c0, c1, thresh, Hs, red, ens, flag);
+        const int done = qr_tail(J, W, S, j + 1, j0, j0 + nb, b, B, gw, nwarps, c0, c1, thresh, sqrt(fro2), Hs, red,
+                                 ens, flag);
         if (done < 0) return;
         if (j + 1 + done >= n) return;
         if (done > 0) {

@@ -1091,6 +1091,8 @@ int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
   if ((rc = dalloc(ctx, H.mps_allocs, &W.qpart, (size_t)3 * 148 * (Dmax + 4)))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.qhp, Dmax))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.colsq, mmax))) return rc;
+  // rank-deficient tail of the QR: row backup, two coefficient tables, residual norms
+  // ([n][blocks] doubles, blocks <= 148)
   if ((rc = dalloc(ctx, H.mps_allocs, &W.qtail, (size_t)(nmax + 2 * Dmax * Dmax + Dmax * 74 + 16)))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.obs, ctx->n_el + 4))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.ks, 1))) return rc;

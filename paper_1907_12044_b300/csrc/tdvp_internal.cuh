@@ -41,9 +41,10 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 #define TDVP_KMAX_HARD 128        // largest Krylov dimension supported
 #define TDVP_KFLAG_DONE (1 << 20) // finished-solve bit of a Krylov flag word: k | notconv << 16 | this
 #define TDVP_VEC_THREADS 256      // threads of the Lanczos vector kernels
-#define TDVP_MAX_VEC_BLOCKS 160   // chunks per vector (bounds the partial-sum table)
-#define TDVP_VEC_CHUNK 256        // elements per chunk before the cap: one per thread, so a
-                                  // 640 x 64 site vector spreads over every SM
+#define TDVP_MAX_VEC_BLOCKS 148   // chunks per vector: at most one block per SM, so that no SM
+                                  // carries two chunks of one vector
+#define TDVP_VEC_CHUNK 32         // elements per chunk before the cap, so that a 64 x 64 bond
+                                  // vector also spreads over 128 SMs
 #define TDVP_QR_THREADS 256
 
 // Learned Krylov controller (kernels_mlp.cu): 8 features -> 64 -> 64 -> 1
