@@ -222,7 +222,7 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
         eng.step(args.dt, 1, precision=PREC[precision], krylov_mode=mode, tol=tol)
         eng.set_profiling(False)
         ps = eng.stats()
-        for k in ("prof_ms", "prof_flops", "prof_launches"):
+        for k in ("prof_ms", "prof_flops", "prof_launches", "prof_bytes"):
             st[k] = {c: v * args.steps for c, v in ps[k].items()}
         st["prof_note"] = "per-kernel breakdown from one launch-by-launch step after the timed ones, x steps"
     eng.close()
@@ -236,9 +236,19 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
 
 
 # kernel and arithmetic of each timed category with algorithmic flop counts
-ROOF_KERNELS = {"qr": ("bqr_kernel (FP64 Gram-Schmidt, gauge shift)", "alu"),
+ROOF_KERNELS = {"qr": ("bqr_kernel / cqr_kernel (FP64 gauge-shift QR, grid or cluster kernel autotuned per shape)",
+                       "alu"),
                 "gemm": ("zgemm_kernel (FP64 complex GEMM)", "alu"),
-                "tc_gemm": ("tc_cgemm_kernel (tcgen05 kind::tf32)", "tensor")}
+                "tc_gemm": ("tc_cgemm_kernel (tcgen05 kind::tf32)", "tensor"),
+                "lanczos_vec": ("lz_start / lz_dots / lz_upd / lz_next / lz_combine (FP64 Lanczos vectors: "
+                                "two Gram-Schmidt passes, next vector, combination)", "hbm")}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
+# kernel in its current form, on the bench's dominant shape; None where no such capture exists
+TRAFFIC = {"qr": (894464 + 256, "ncu --set full of bqr_kernel on the 640 x 64 rank-8 gauge shift "
+                                "(bench.py --kernel-case qr), the shape of 132 of the 152 shifts of a step; "
+                                "profiles/bqr_rank8_640x64.md")}
 
 
 def roofline(args, st, cat):
@@ -251,6 +261,23 @@ def roofline(args, st, cat):
                 "note": "no algorithmic flop count for this category"}
     name, bound = ROOF_KERNELS[cat]
     ms, fl, nl = cat_ms[cat], st["prof_flops"][cat], st["prof_launches"][cat]
+    if bound == "hbm":
+        # algorithmic bytes (counted by the library per finished solve) / summed CUDA-event time
+        by = st.get("prof_bytes", {}).get(cat, 0.0)
+        ach = by / (ms * 1e-3) / 1e9 if ms > 0 and by > 0 else None
+        pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        peak = pk.get("hbm_gbs", 6400.0)
+        src = ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk
+               else "fallback 6.4 TB/s (no MEASURED_PEAKS.json)")
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak if ach else None, "traffic": TRAFFIC.get(cat, (None, None))[0],
+                "traffic_source": TRAFFIC.get(cat, (None, None))[1], "peak_source": src, "launches": nl,
+                "algorithmic_bytes_per_launch": by / max(nl, 1),
+                "avg_launch_us": 1e3 * ms / max(nl, 1), "share_of_step": ms / max(total, 1e-9),
+                "note": "algorithmic bytes: 16 n (2 k (k+1) + 10 k + 5) per Lanczos solve of dimension k on "
+                        "n complex elements (each iteration j reads V_0..V_j for the dot and the update of "
+                        "both Gram-Schmidt passes); the vectors of a solve (<= 7 MB here) stay in L2, so "
+                        "these launches are latency bound, far from the HBM roof"}
     ach = fl / (ms * 1e-3) / 1e12 if ms > 0 else None
     if bound == "tensor":
         pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {"bf16_tflops": 1800.0}
@@ -259,7 +286,8 @@ def roofline(args, st, cat):
     else:
         peak, src = FP64_NOMINAL_TFLOPS, "B300 FP64 nominal 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry)"
     return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak if ach else None, "traffic": None, "peak_source": src, "launches": nl,
+            "frac": ach / peak if ach else None, "traffic": TRAFFIC.get(cat, (None, None))[0],
+            "traffic_source": TRAFFIC.get(cat, (None, None))[1], "peak_source": src, "launches": nl,
             "avg_launch_us": 1e3 * ms / max(nl, 1), "share_of_step": ms / max(total, 1e-9),
             "note": "algorithmic flops: 8 per complex multiply-add of the logical products "
                     "(QR: 2 n^2 m per n x m shift, two Gram-Schmidt passes)"}
@@ -315,6 +343,9 @@ def run_ours(args, rank, world):
         out["roofline"] = roofline(args, st, top)
         if top != "tc_gemm" and args.precision != "fp64":
             out["roofline_tc_gemm"] = roofline(args, st, "tc_gemm")
+        # the other large categories against their own roofs (QR: FP64 ALU, Lanczos vectors: HBM)
+        out["roofline_other"] = {c: roofline(args, st, c) for c in ("qr", "lanczos_vec", "gemm")
+                                 if c != top and cat_ms.get(c, 0) > 0}
         out["kernel_time_ms"] = {k: round(v, 3) for k, v in cat_ms.items()}
         out["dominant_category"] = top
     out["krylov"] = {"mean_dim": st["krylov_dim_sum"] / max(st["krylov_solves"], 1),

@@ -181,11 +181,16 @@ typedef struct {
   long long not_converged;     /* solves that stopped at kmax above tolerance */
   long long tri_evals;         /* tridiagonal exponentials evaluated (convergence tests), all realisations */
   /* filled only while profiling is on: per category, summed CUDA-event time of each launch
-   * (recorded on the context stream right before and after it), launch count, and the
-   * algorithmic real flops of the contraction GEMMs (8 per complex multiply-add). */
+   * (recorded on the context stream right before and after it), launch count, the
+   * algorithmic real flops of the contraction GEMMs (8 per complex multiply-add), and the
+   * algorithmic bytes of the Lanczos vector kernels (TDVP_CAT_LZVEC): per solve of dimension k
+   * on vectors of n complex elements, 16 n (2 k (k+1) + 10 k + 5) -- iteration j reads
+   * V_0..V_j four times (dot and update of each of the two Gram-Schmidt passes) and moves w,
+   * V_{j+1} and x nine times; start and combination add k + 5 vectors. */
   double prof_ms[TDVP_NCAT];
   long long prof_launches[TDVP_NCAT];
   double prof_flops[TDVP_NCAT];
+  double prof_bytes[TDVP_NCAT];
 } tdvp_stats_t;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0).  While on, every kernel launch is

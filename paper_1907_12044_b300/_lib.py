@@ -62,7 +62,7 @@ class StatsC(C.Structure):
                 ("kernel_launches", C.c_longlong), ("not_converged", C.c_longlong),
                 ("tri_evals", C.c_longlong),
                 ("prof_ms", C.c_double * NCAT), ("prof_launches", C.c_longlong * NCAT),
-                ("prof_flops", C.c_double * NCAT)]
+                ("prof_flops", C.c_double * NCAT), ("prof_bytes", C.c_double * NCAT)]
 
 
 def library_path():

@@ -1008,6 +1008,12 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
     const int k = f & 0xffff;
     if ((f >> 16) & 1) { ctx->stats.not_converged++; if (notconv) *notconv = 1; }
     kmaxr = std::max(kmaxr, k);
+    if (ctx->prof) {
+      // algorithmic bytes of this solve's vector kernels (see tdvp_stats_t)
+      const auto& bd = ctx->rh[v.r0 + r].bd;
+      const double nr = kind == 0 ? (double)bd[site] * ctx->d[site] * bd[site + 1] : (double)bd[site + 1] * bd[site + 1];
+      ctx->stats.prof_bytes[TDVP_CAT_LZVEC] += 16.0 * nr * (2.0 * k * (k + 1) + 10.0 * k + 5.0);
+    }
     ctx->stats.krylov_dim_sum += k;
     ctx->stats.krylov_dim_max = std::max(ctx->stats.krylov_dim_max, k);
   }

@@ -36,3 +36,25 @@ def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         L.load_library()
+
+
+def test_stats_struct_layout_matches_the_header(tmp_path):
+    """The ctypes mirror of tdvp_stats_t has the C struct's size and field offsets."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1907_12044_b300._lib import StatsC
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in StatsC._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"tdvp.h\"\nint main(void){\n"
+                   "printf(\"%zu\\n\", sizeof(tdvp_stats_t));\n"
+                   + "".join(f"printf(\"%zu\\n\", offsetof(tdvp_stats_t, {f}));\n" for f in fields)
+                   + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(StatsC)
+    assert out[1:] == [getattr(StatsC, f).offset for f in fields]
