@@ -226,13 +226,27 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
             st[k] = {c: v * args.steps for c, v in ps[k].items()}
         st["prof_note"] = "per-kernel breakdown from one launch-by-launch step after the timed ones, x steps"
     eng.close()
-    ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.sum(times)), world)
     return {"ms": ms, "stats": st, "pops": np.array(pops), "clocks": clk.summary(), "controller": ctl,
             "graph": graph}
+
+
+def max_over_ranks(ms, world):
+    """The slowest rank's time (every rank gets it): all-reduce MAX over the default process group,
+    on the device for NCCL and on the host for gloo."""
+    if world <= 1:
+        return ms
+    import torch
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def site_update_rate(n_sites, steps, world, ms):
+    """Whole-job site updates per second: every rank advances its own trajectory (2N-1 site
+    updates per step each, Eq. ps_trotter) and the job takes the slowest rank's time."""
+    return (2 * n_sites - 1) * steps * world / (ms / 1e3)
 
 
 # kernel and arithmetic of each timed category with algorithmic flop counts
@@ -308,9 +322,8 @@ def run_ours(args, rank, world):
                                                                         flush, prof)
     if run is None:
         run = ref
-    updates = (2 * N - 1) * args.steps * world
-    value = updates / (run["ms"] / 1e3)
-    fp64_value = updates / (ref["ms"] / 1e3)
+    value = site_update_rate(N, args.steps, world, run["ms"])
+    fp64_value = site_update_rate(N, args.steps, world, ref["ms"])
     # population error of the timed arm against the FP64 arm on the same steps (Eq. error)
     t = args.dt * np.arange(len(run["pops"]))
     dP = np.abs(run["pops"] - ref["pops"])
