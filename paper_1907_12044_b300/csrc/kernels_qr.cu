@@ -235,10 +235,11 @@ struct Scratch {
 
 // ---- rank-deficient tail ----
 // Taken after a dropped row j.  With Q_t (t < J0 = j+1) final, rows J0..n-1 are projected twice
-// onto them (block Gram-Schmidt); a row whose residual is <= max(thresh/2, thresh - 1e-10 ||X||_F)
+// onto them (block Gram-Schmidt); a row whose residual is <= max(thresh/2, thresh - 1e-8 ||X||_F)
 // is dropped under the exact rule as well, since the exact process tests it against a superset
-// of these Q_t (residuals only shrink) and the two computed residuals differ by rounding only,
-// at most n m eps ||x|| < 1e-10 ||x|| <= 1e-10 ||X||_F for n <= 256, m <= 16384.  The completions are then built one per group barrier:
+// of these Q_t (residuals only shrink) and the two computed residuals differ by rounding only:
+// each is within ~2 n m eps ||x|| of its exact value (n dot products of length m, two passes),
+// together < 2e-9 ||x|| <= 1e-8 ||X||_F for n <= 256, m <= 16384.  The completions are then built one per group barrier:
 // rows are kept unnormalised with their squared norms (so no row another block reads is
 // rewritten) and every block picks the next unit vector itself, scanning forward from the
 // previous one.  A completion is e_p minus its projection with the exact
@@ -305,7 +306,7 @@ __device__ int qr_tail(const QrJob& J, const WorkDev& W, const Scratch& S, int J
     if (threadIdx.x == 0) first_bad = Tn;
     __syncthreads();
     // certain-drop bound (squared), the same in every block: fro = ||X||_F
-    const double lim = fmax(0.5 * thresh, thresh - 1e-10 * fro), lim2 = lim * lim;
+    const double lim = fmax(0.5 * thresh, thresh - 1e-8 * fro), lim2 = lim * lim;
     for (int a = threadIdx.x / 32; a < Tn; a += NW) {
       double s = 0;
       for (int bb = lane; bb < B; bb += 32) s += __ldcg(TPN + (long long)a * B + bb);
