@@ -259,10 +259,10 @@ ROOF_KERNELS = {"qr": ("bqr_kernel / cqr_kernel (FP64 gauge-shift QR, grid or cl
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel in its current form, on the bench's dominant shape; None where no such capture exists
-TRAFFIC = {"qr": (894464 + 256, "ncu --set full of bqr_kernel on the 640 x 64 rank-8 gauge shift "
-                                "(bench.py --kernel-case qr), the shape of 132 of the 152 shifts of a step; "
-                                "profiles/bqr_rank8_640x64.md")}
+# kernel in its current form, on the bench's dominant shape; None where no such capture exists or
+# the kernel has changed since (bqr_kernel: 0.89 MB per 640 x 64 rank-8 shift at commit 92e9268,
+# profiles/bqr_rank8_640x64.md, before a change of its certain-drop margin)
+TRAFFIC = {}
 
 
 def roofline(args, st, cat):
