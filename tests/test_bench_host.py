@@ -1,0 +1,135 @@
+"""bench.py's host side on CPU: the JSON line assembled around a stand-in engine.
+
+The stand-in replaces only the CUDA library (steps, statistics, populations) and the CUDA timing
+calls; the bench's own arithmetic (rates, population error, rooflines, JSON assembly) runs as it
+does on a GPU, so a change to the bench is checked here before it reaches a GPU.
+"""
+import json
+import sys
+import time
+import types
+
+import numpy as np
+
+import bench
+
+CATS = ["gemm", "wapply", "lanczos_vec", "tridiag", "qr", "other", "tc_gemm"]
+
+
+class FakeEngine:
+    def __init__(self, n_realisations=1, kmax=64, device=0, stream=None):
+        self.t = 0
+        self.prof = False
+        self.precisions = []
+        self._reset()
+
+    def _reset(self):
+        self.s = {"steps": 0, "site_updates": 0, "matvecs": 0, "krylov_solves": 0, "krylov_dim_sum": 0,
+                  "krylov_dim_max": 0, "host_syncs": 0, "kernel_launches": 0, "not_converged": 0,
+                  "tri_evals": 0, "prof_ms": dict.fromkeys(CATS, 0.0), "prof_launches": dict.fromkeys(CATS, 0),
+                  "prof_flops": dict.fromkeys(CATS, 0.0), "prof_bytes": dict.fromkeys(CATS, 0.0)}
+
+    def set_option(self, *a):
+        pass
+
+    def build_mpo(self, r, p):
+        self.n_el = p.n_el
+
+    def init_mps(self, r, D, site):
+        pass
+
+    def autotune(self):
+        pass
+
+    def controller_logging(self, n):
+        pass
+
+    def controller_set_weights(self, w):
+        pass
+
+    def controller_train(self, epochs=20, batch=1024, lr=1e-3):
+        return 0.5
+
+    def reset_stats(self):
+        self._reset()
+
+    def set_profiling(self, on=True):
+        self.prof = on
+
+    def step(self, dt, n_steps=1, precision=0, krylov_mode=0, tol=1e-12):
+        self.t += n_steps
+        self.precisions.append(precision)
+        s = self.s
+        s["steps"] += n_steps
+        s["krylov_solves"] += 305 * n_steps
+        s["krylov_dim_sum"] += 6 * 305 * n_steps
+        s["krylov_dim_max"] = 9
+        s["kernel_launches"] += 19000 * n_steps
+        s["tri_evals"] += 400 * n_steps
+        if self.prof:
+            for i, c in enumerate(CATS):
+                s["prof_ms"][c] += 10.0 * (i + 1)
+                s["prof_launches"][c] += 100 * (i + 1)
+            s["prof_flops"]["qr"] += 6.4e9
+            s["prof_flops"]["tc_gemm"] += 3.7e11
+            s["prof_flops"]["gemm"] += 1e10
+            s["prof_bytes"]["lanczos_vec"] += 1.8e10
+        time.sleep(0.002)
+
+    def stats(self):
+        return json.loads(json.dumps(self.s))
+
+    def observables(self, r=0):
+        P = np.full(self.n_el, 1.0 / self.n_el)
+        P[0] += 1e-9 * self.t * (1 + (2 in self.precisions))
+        return P, 1.0, 1.0
+
+    def close(self):
+        pass
+
+
+class FakeEvent:
+    def __init__(self, enable_timing=True):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = time.perf_counter()
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return max(1e-3, (other.t - self.t) * 1e3)
+
+
+def test_bench_line_is_complete_with_a_stand_in_engine(monkeypatch):
+    import torch
+    import paper_1907_12044_b300 as pkg
+    monkeypatch.setattr(pkg, "Engine", FakeEngine)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: types.SimpleNamespace(cuda_stream=0))
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    real_zeros = torch.zeros
+    monkeypatch.setattr(torch, "zeros", lambda *a, **k: real_zeros(4, dtype=k.get("dtype")))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--batched", "0", "--no-e2e", "--no-cpu-baseline"])
+    args = bench.parse()
+    out, p = bench.run_ours(args, 0, 1)
+    line = json.loads(json.dumps(out))
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "fp64_arm", "speedup_vs_fp64", "pop_error_vs_fp64",
+              "gpu_launches", "clocks", "roofline", "kernel_time_ms", "krylov"):
+        assert k in line, k
+    n = len(p.chain())
+    assert line["value"] > 0 and line["fp64_arm"]["value"] > 0
+    assert abs(line["value"] * line["ms_per_step"] / 1e3 - (2 * n - 1)) < 1e-6 * (2 * n - 1)
+    assert line["config"]["workload"].startswith(p.name)
+    assert line["pop_error_vs_fp64"]["max_abs_dP"] > 0
+    # the stand-in's largest category is tc_gemm (tensor roof); the others keep their own roofs
+    roof = line["roofline"]
+    assert roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s" and 0 < roof["frac"] < 1
+    other = line["roofline_other"]
+    assert other["lanczos_vec"]["bound"] == "hbm" and other["lanczos_vec"]["unit"] == "GB/s"
+    assert abs(other["lanczos_vec"]["achieved"] - 1.8e10 * args.steps / (30.0 * args.steps * 1e-3) / 1e9) < 1e-6
+    assert other["qr"]["bound"] == "alu" and other["qr"]["frac"] > 0
+    assert line["kernel_time_ms"]["tc_gemm"] == 70.0 * args.steps
