@@ -34,6 +34,11 @@ class FakeEngine:
 
     def build_mpo(self, r, p):
         self.n_el = p.n_el
+        self.d = np.asarray(p.phys_dims(), np.int32)
+
+    def chain_info(self, r=0):
+        n = len(self.d)
+        return self.d, np.ones(n + 1, np.int32), np.ones(n + 1, np.int32)
 
     def init_mps(self, r, D, site):
         pass
@@ -133,3 +138,21 @@ def test_bench_line_is_complete_with_a_stand_in_engine(monkeypatch):
     assert abs(other["lanczos_vec"]["achieved"] - 1.8e10 * args.steps / (30.0 * args.steps * 1e-3) / 1e9) < 1e-6
     assert other["qr"]["bound"] == "alu" and other["qr"]["frac"] > 0
     assert line["kernel_time_ms"]["tc_gemm"] == 70.0 * args.steps
+
+
+def test_batched_and_e2e_sections_with_a_stand_in_engine(monkeypatch):
+    import torch
+    import paper_1907_12044_b300 as pkg
+    monkeypatch.setattr(pkg, "Engine", FakeEngine)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: types.SimpleNamespace(cuda_stream=0))
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "2"])
+    args = bench.parse()
+    b = json.loads(json.dumps(bench.run_batched(args, 3)))
+    assert b["realisations"] == 3 and b["value"] > 0 and b["unit"] == bench.UNIT
+    p, _ = bench.workload(args)
+    e = json.loads(json.dumps(bench.run_e2e(args, p)))
+    for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
+        assert k in e, k
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] >= 0 and e["d2h_bytes_per_step"] > 0
