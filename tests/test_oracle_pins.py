@@ -101,6 +101,23 @@ def test_qr_rank_deficient_completion_rule():
     assert np.sum(np.abs(np.diag(R)) > 0) == 4
 
 
+def test_qr_at_bond_dimension_256():
+    """The sizes of a D = 256 sweep: full rank against the phase-normalised library QR, and a
+    rank-64 matrix whose dropped columns are completed (orthonormal Q, C = QR, 64 kept)."""
+    rng = np.random.default_rng(256)
+    C = rng.normal(size=(512, 256)) + 1j * rng.normal(size=(512, 256))
+    Q, R = qr_rr(C)
+    Qn, Rn = np.linalg.qr(C)
+    ph = np.diag(Rn) / np.abs(np.diag(Rn))
+    Qn, Rn = Qn * ph, (Rn.T * ph.conj()).T
+    assert np.abs(Q - Qn).max() < 1e-12 and np.abs(R - Rn).max() < 1e-11 * np.abs(Rn).max()
+    X = (rng.normal(size=(512, 64)) + 1j * rng.normal(size=(512, 64))) @ rng.normal(size=(64, 256))
+    Q, R = qr_rr(X)
+    assert np.abs(Q.conj().T @ Q - np.eye(256)).max() < 1e-12
+    assert np.abs(Q @ R - X).max() < 1e-12 * np.abs(X).max()
+    assert np.sum(np.abs(np.diag(R)) > 0) == 64
+
+
 def test_lq_orthonormal_rows():
     rng = np.random.default_rng(2)
     C = rng.normal(size=(8, 30)) + 1j * rng.normal(size=(8, 30))
@@ -121,6 +138,24 @@ def test_expm_tridiag_matches_dense_expm():
         z = -0.7j
         ref = sla.expm(z * T)[:, 0]
         assert np.allclose(expm_tridiag_e1(a, b, z), ref, atol=1e-13)
+
+
+def test_tridiagonal_exponential_at_wide_exponents():
+    """exp(-i theta T) e_1 for theta ||T|| from 30 to 6000 against the Pade scaling-and-squaring
+    matrix exponential (a different method from the oracle's eigendecomposition), in the regime
+    where a Chebyshev series needs hundreds of terms or substeps; unitary."""
+    rng = np.random.default_rng(7)
+    k = 32
+    a = rng.normal(size=k) * 100
+    b = np.abs(rng.normal(size=k - 1)) * 50 + 1
+    T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+    lam = np.linalg.eigvalsh(T)
+    for x in (30.0, 250.0, 1500.0, 6000.0):
+        theta = x / (0.5 * (lam[-1] - lam[0]))
+        ref = sla.expm(-1j * theta * T)[:, 0]
+        out = expm_tridiag_e1(a, b, -1j * theta)
+        assert np.abs(out - ref).max() < 1e-10
+        assert abs(np.linalg.norm(out) - 1.0) < 1e-12
 
 
 def test_lanczos_matches_dense_expm_and_converges():
