@@ -102,8 +102,10 @@ int tdvp_init_mps(tdvp_ctx* ctx, int r, int D, int exciton_site);   /* 1 <= D <=
 /* Explicit initial tensors for realisation r: bond_dims[0..N] (bond_dims[0] =
  * bond_dims[N] = 1) and re_im = all site tensors concatenated in site order,
  * each in the layout above.  The state is right-canonicalised on the device by
- * LQ from the last site (Eq. QR, "RQ" direction), normalised, and the right
- * environments are built. */
+ * LQ from the last site (Eq. QR, "RQ" direction), the new centre normalised after
+ * each absorbed factor (only the normalised state is kept, and the norm of a product
+ * of generic tensors grows or shrinks geometrically with the chain length), and the
+ * right environments are built.  Tensors need not be canonical or normalised. */
 int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const double* re_im);
 
 /* Advance every realisation by n_steps steps of dt_fs with Eq. ps_trotter.
