@@ -46,8 +46,3 @@ def test_batched_fmo_realisations_match_single_runs(prec, tol):
         assert rel_pop_err(Pb, Ps) <= tol, (r, rel_pop_err(Pb, Ps))
         single.close()
 
-
-def test_ragged_draw_is_seeded_and_in_range():
-    Ds = wl.ragged_bond_dims(256)
-    assert Ds == wl.ragged_bond_dims(256)
-    assert set(Ds) <= {32, 48, 64, 96, 128} and len(set(Ds)) == 5
