@@ -6,6 +6,12 @@ Index conventions: site tensor A[l, s, r]; MPO W[w, w', s', s] (s' is the bra
 index); left environment L[l', w, l] and right environment R[r', w, r] with the
 primed (bra) index first.  L of site i contracts sites < i (h[1:i-1] of
 Eq. tdvp1_h1i), R of site i contracts sites > i (h[i+1:N] of Eq. tdvp1_hiN).
+
+Each contraction below is its definition written as one ``np.einsum``.  numpy's
+default path search refuses any intermediate larger than the largest operand and
+then falls back to the naive loop over all eight indices (hours at D = 64); the
+``_PATH`` setting lifts that cap so the same sum is evaluated pairwise.  The
+pairing changes only the rounding order, not the result.
 """
 from __future__ import annotations
 
@@ -13,44 +19,36 @@ import numpy as np
 
 from .linalg import lq_rr
 
+_PATH = ("greedy", 1e15)
+
 
 def heff_apply(L, W, R, A):
-    """H[i] C of Eq. tdvp2_C with H[i] from Eq. tdvp1_H, contracted stage by stage.
+    """H[i] C of Eq. tdvp2_C with H[i] from Eq. tdvp1_H.
 
-    T1[x,w,s,b] = sum_a L[x,w,a] A[a,s,b]; T2 = sum_{w,s} T1 W[w,v,t,s];
-    out[x,t,y] = sum_{v,b} T2[x,b,v,t] R[y,v,b].
+    out[x,t,y] = sum_{w,v,a,s,b} L[x,w,a] W[w,v,t,s] A[a,s,b] R[y,v,b].
     """
-    T1 = np.tensordot(L, A, axes=(2, 0))                    # [x, w, s, b]
-    T2 = np.tensordot(T1, W, axes=([1, 2], [0, 3]))         # [x, b, v, t]
-    return np.tensordot(T2, R, axes=([1, 2], [2, 1]))       # [x, t, y]
+    return np.einsum("xwa,wvts,asb,yvb->xty", L, W, A, R, optimize=_PATH)
 
 
 def h0_apply(L, R, D):
     """Zero-site Hamiltonian of Eq. tdvp2_D: out[x,y] = sum_{w,a,b} L[x,w,a] D[a,b] R[y,w,b]."""
-    T = np.tensordot(L, D, axes=(2, 0))                     # [x, w, b]
-    return np.tensordot(T, R, axes=([1, 2], [1, 2]))        # [x, y]
+    return np.einsum("xwa,ab,ywb->xy", L, D, R, optimize=_PATH)
 
 
 def env_left(L, A, W):
     """h[1:i] from h[1:i-1] and site i (Eq. tdvp1_h1i with Eq. tdvp1_h).
 
-    Lnew[p,v,q] = sum L[x,w,y] conj(A[x,t,p]) W[w,v,t,s] A[y,s,q].
+    Lnew[p,v,q] = sum_{x,w,y,t,s} L[x,w,y] conj(A[x,t,p]) W[w,v,t,s] A[y,s,q].
     """
-    T1 = np.tensordot(L, A, axes=(2, 0))                    # [x, w, s, q]
-    T2 = np.tensordot(T1, W, axes=([1, 2], [0, 3]))         # [x, q, v, t]
-    out = np.tensordot(A.conj(), T2, axes=([0, 1], [0, 3])) # [p, q, v]
-    return out.transpose(0, 2, 1)
+    return np.einsum("xwy,xtp,wvts,ysq->pvq", L, A.conj(), W, A, optimize=_PATH)
 
 
 def env_right(R, A, W):
     """h[i:N] from h[i+1:N] and site i (Eq. tdvp1_hiN with Eq. tdvp1_h).
 
-    Rnew[p,w,q] = sum conj(A[p,t,x]) W[w,v,t,s] A[q,s,y] R[x,v,y].
+    Rnew[p,w,q] = sum_{t,x,v,s,y} conj(A[p,t,x]) W[w,v,t,s] A[q,s,y] R[x,v,y].
     """
-    T1 = np.tensordot(A, R, axes=(2, 2))                    # [q, s, x, v]
-    T2 = np.tensordot(T1, W, axes=([1, 3], [3, 1]))         # [q, x, w, t]
-    out = np.tensordot(A.conj(), T2, axes=([1, 2], [3, 1])) # [p, q, w]
-    return out.transpose(0, 2, 1)
+    return np.einsum("ptx,wvts,qsy,xvy->pwq", A.conj(), W, A, R, optimize=_PATH)
 
 
 def product_mps(d, bd, occ):
@@ -64,6 +62,15 @@ def product_mps(d, bd, occ):
     first.
     Distinct standard basis rows are orthonormal, so every site is
     right-canonical (Eq. rcanon) and the state is the product state.
+
+    Why r first: one-site TDVP-PS only moves the state inside the tangent space
+    that these completion rows span.  Ordered s first, a site with Dl <= Dr gets
+    only rows whose own level is the occupied one, the exciton-hopping direction is
+    never in that space and the populations stay frozen at their start values;
+    ordered r first, the rows are the single-site excitations that H reaches from
+    the product state.  A CPU test holds the product start on the tiny chain to the
+    exact state vector (max |dP| 1.0e-4 at D = 8, 7.9e-6 at D = 16 over 400 fs;
+    0.53, the full transfer amplitude, with the s-first order).
     """
     mps = []
     for i, di in enumerate(d):

@@ -80,3 +80,52 @@ def test_wrong_time_unit_is_caught(monkeypatch):
     t = 100.0 * 2 * np.pi * 2.99792458e-5
     P1 = 1 - 4 * p.J[0, 1] ** 2 / Om ** 2 * np.sin(Om * t / 2) ** 2
     assert abs(populations(st, p)[0] - P1) > 1e-6
+
+
+
+# ---------------------------------------------------------------- observables: the dense-state pin
+
+def _obs_deviation(**mutated):
+    from test_oracle_pins import _dense_observable_deviation
+    return _dense_observable_deviation(wl.tiny_chain(), 8, 21, **mutated)
+
+
+def _energy_unnormalised(st):
+    """energy() with the division by <Psi|Psi> left out."""
+    E = np.ones((1, 1, 1), dtype=complex)
+    for A, W in zip(st.mps, st.W):
+        E = T.env_left(E, A, W)
+    return float(E[0, 0, 0].real)
+
+
+def _mpo_without_first_coupling(p):
+    W = T.build_mpo(p)
+    W[1] = W[1].copy()
+    W[1][4, 1] = 0.0                          # the g w (b^+ + b) n block of the first mode
+    return W
+
+
+def test_observable_pin_is_quiet_without_a_mistake():
+    assert _obs_deviation() < 1e-12
+
+
+def test_energy_without_normalisation_is_caught():
+    assert _obs_deviation(energy_fn=_energy_unnormalised) > 1e-3
+
+
+def test_energy_with_dropped_mpo_term_is_caught():
+    assert _obs_deviation(mpo_fn=_mpo_without_first_coupling) > 1e-6
+
+
+def test_norm_without_square_root_is_caught():
+    assert _obs_deviation(norm_fn=lambda st: float(abs(T._expect_local(st.mps, {})))) > 1e-3
+
+
+def test_norm_that_is_always_one_is_caught():
+    assert _obs_deviation(norm_fn=lambda st: 1.0) > 1e-3
+
+
+def test_populations_without_normalisation_is_caught():
+    def unnormalised(st, p):
+        return T.populations(st, p) * T._expect_local(st.mps, {}).real
+    assert _obs_deviation(pops_fn=unnormalised) > 1e-3

@@ -365,3 +365,53 @@ def test_mean_cumulative_deviation_closed_form():
     Pref = np.full_like(P, 0.5)
     # sum_n |dP| = 0.02 t/100, integral = 0.01 t^2/100, divided by 2 t
     assert abs(mean_cumulative_deviation(t, P, Pref) - 0.01 * 100 / 100 / 2) < 1e-12
+
+
+# ---------------------------------------------------------------- observables against the dense state
+
+def _dense_observable_deviation(p, D, seed, norm_fn=None, energy_fn=None, pops_fn=None,
+                                mpo_fn=None):
+    """Largest relative deviation of the oracle's norm, energy and populations from the dense
+    state vector of the same (random, non-canonical, unnormalised) MPS: ||psi||,
+    <psi|H|psi>/<psi|psi> with the Kronecker-built H, and <psi|n_m|psi>/<psi|psi>.  The keyword
+    arguments replace an oracle function (planted-mistake tests)."""
+    import types
+    norm_fn, energy_fn = norm_fn or norm, energy_fn or energy
+    pops_fn, mpo_fn = pops_fn or populations, mpo_fn or build_mpo
+    tens = [2.0 * t for t in wl.random_mps_tensors(p.phys_dims(), D, seed=seed)]
+    st = types.SimpleNamespace(mps=tens, W=mpo_fn(p))
+    psi = mps_to_dense(tens)
+    H = hamiltonian_kron(p)
+    n_d = np.linalg.norm(psi)
+    E_d = np.vdot(psi, H @ psi).real / n_d ** 2
+    P_d = populations_dense(psi, p)
+    assert abs(n_d - 1) > 0.1                      # a norm that is always 1 cannot pass
+    return max(abs(norm_fn(st) - n_d) / n_d, abs(energy_fn(st) - E_d) / max(1.0, abs(E_d)),
+               np.abs(pops_fn(st, p) - P_d).max())
+
+
+@pytest.mark.parametrize("maker,D,seed", [(wl.tiny_chain, 8, 21), (wl.tiny_chain, 32, 22),
+                                          (lambda: _small_vibronic(), 3, 23),
+                                          (lambda: _small_vibronic(zpe=True), 4, 24)])
+def test_norm_energy_populations_match_dense_state(maker, D, seed):
+    """norm() = ||psi||, energy() = <psi|H|psi>/<psi|psi> and populations() of Eq. error on
+    random truncated states, against the dense vector and the term-by-term H of Eq. holstein."""
+    assert _dense_observable_deviation(maker(), D, seed) < 1e-12
+
+
+# ---------------------------------------------------------------- product start against exact dynamics
+
+@pytest.mark.slow
+def test_product_start_completion_tracks_exact_dynamics():
+    """The completion rows of the product start (reading of Sec. II.C) span the directions H
+    reaches from the product state: at D = 16 the truncated TDVP-PS follows the exact
+    state-vector populations over 400 fs.  The s-first order freezes them (error 0.53)."""
+    p = wl.tiny_chain()
+    st = TDVPState.start(p, D=16)
+    exact = propagate_exact(hamiltonian_kron(p), product_state(p), 10.0 * np.arange(1, 41))
+    worst = 0.0
+    for s in range(40):
+        tdvp_ps_step(st, 10.0)
+        worst = max(worst, np.abs(populations(st, p) - populations_dense(exact[s], p)).max())
+    assert worst < 2e-5
+    assert np.abs(populations(st, p) - [1.0, 0.0]).max() > 0.1       # population did move
