@@ -218,13 +218,14 @@ void tdvp_reset_stats(tdvp_ctx* ctx);
  * has finished (it synchronises the stream).
  *
  * Limits: 1 <= n <= 256, n <= m <= 16384; anything else returns TDVP_ERR_INVALID_ARG without
- * touching the device.  X must not overlap Q or L.
+ * touching the device.  X, Q and L must not overlap (checked on the host: TDVP_ERR_INVALID_ARG).
  *
  * Memory: the scratch space (partial sums, column norms, barrier words; about 0.9 MB) is one
  * static device array of fixed size in the library, held by every GPU that loads the library
- * until the process exits.  The first call on a device looks up its address
- * (cudaGetSymbolAddress) and the co-resident block count; make that first call before any
- * stream capture.  All calls on a device share that one array, so calls that overlap on the
+ * until the process exits.  The first call on a device (and the first after the device's context
+ * was replaced, e.g. by cudaDeviceReset) looks up its address (cudaGetSymbolAddress) and the
+ * co-resident block count; make that first call before any stream capture.  Every device-side
+ * barrier wait gives up after 1 s of wall-clock time.  All calls on a device share that one array, so calls that overlap on the
  * GPU (other streams, other host threads) race and give wrong results; serialise them.
  * Returns TDVP_ERR_DEVICE_TIMEOUT if a bounded device-side wait gave up. */
 int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* cuda_stream);

@@ -16,7 +16,7 @@ constexpr int NA_BMAX = 64;         // blocks per call
 constexpr int NA_PS = NA_NMAX + 4;  // stride of one block's partial sums
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
-constexpr long long NA_SPIN_LIMIT = 1LL << 24;
+constexpr unsigned long long NA_WAIT_NS = 1000000000ull;   // a barrier wait gives up after 1 s
 
 constexpr size_t NA_OFF_PART = 0;                                            // 3 x [BMAX][PS] complex
 constexpr size_t NA_OFF_COLSQ = NA_OFF_PART + 3ull * NA_BMAX * NA_PS * sizeof(zc);   // [MMAX] double
@@ -45,6 +45,15 @@ __device__ NaView na_view(unsigned char* base) {
   return v;
 }
 
+__device__ __forceinline__ unsigned long long na_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier of the cooperative launch (one arrival word and one generation word).  Every wait
+// is bounded by wall-clock time (NA_WAIT_NS, %globaltimer): past it the block records
+// TDVP_ERR_DEVICE_TIMEOUT and returns false, and so does every block that sees the error word.
 __device__ bool na_sync(const NaView& S, int nblocks) {
   __shared__ int ok;
   __syncthreads();
@@ -61,10 +70,10 @@ __device__ bool na_sync(const NaView& S, int nblocks) {
         __threadfence();
         atomicAdd(S.bar + 1, 1u);
       } else {
-        long long spins = 0;
+        const unsigned long long t0 = na_gtimer();
         while (*gen == g) {
           if (*err != 0) { good = 0; break; }
-          if (++spins > NA_SPIN_LIMIT) { atomicExch(S.err, TDVP_ERR_DEVICE_TIMEOUT); good = 0; break; }
+          if (na_gtimer() - t0 > NA_WAIT_NS) { atomicExch(S.err, TDVP_ERR_DEVICE_TIMEOUT); good = 0; break; }
           __nanosleep(64);
         }
       }
@@ -303,18 +312,50 @@ lq_noalloc_kernel(zc* X, zc* L, int n, int m, int B, double rtol, unsigned char*
   }
 }
 
-// Device address of the scratch array and the co-resident block count, once per device.
+// Device address of the scratch array and the co-resident block count, looked up once per device
+// and again whenever the current context of that device is a different one (after a
+// cudaDeviceReset the module is loaded anew and the array may sit elsewhere).  The context is
+// identified by its driver-assigned unique id, read through the driver entry points the runtime
+// exposes; none of these calls allocates device memory.
 struct NaDevice {
   unsigned char* scratch = nullptr;
   int blocks = 0;
+  unsigned long long ctx_id = 0;
 };
 std::mutex g_na_mu;
 NaDevice g_na_dev[64];
 
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// unique id of the calling thread's current context (0 if the driver cannot tell)
+unsigned long long na_context_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    looked_up = true;
+  }
+  void* c = nullptr;
+  unsigned long long id = 0;
+  if (!get_cur || !get_id || get_cur(&c) != 0 || !c || get_id(c, &id) != 0) return 0;
+  return id;
+}
+
 int na_setup(int dev, NaDevice* out) {
   std::lock_guard<std::mutex> lock(g_na_mu);
   NaDevice& d = g_na_dev[dev];
-  if (!d.scratch) {
+  const unsigned long long id = na_context_id();
+  if (!d.scratch || id != d.ctx_id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_lq_scratch) != cudaSuccess || !p) return TDVP_ERR_CUDA;
     int per_sm = 0, sms = 0;
@@ -323,22 +364,31 @@ int na_setup(int dev, NaDevice* out) {
       return TDVP_ERR_CUDA;
     d.blocks = per_sm * sms;
     d.scratch = static_cast<unsigned char*>(p);
+    d.ctx_id = id;
   }
   *out = d;
   return TDVP_OK;
+}
+
+// true if the byte ranges [a, a + na) and [b, b + nb) share a byte
+bool na_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
 }
 
 }  // namespace
 
 extern "C" int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* cuda_stream) {
   if (n < 1 || m < n || n > NA_NMAX || m > NA_MMAX || !X || !Q || !L) return TDVP_ERR_INVALID_ARG;
+  const size_t xb = sizeof(zc) * (size_t)n * m, lb = sizeof(zc) * (size_t)n * n;
+  if (na_overlap(X, xb, Q, xb) || na_overlap(X, xb, L, lb) || na_overlap(Q, xb, L, lb)) return TDVP_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TDVP_ERR_CUDA;
   NaDevice nd;
   int rc = na_setup(dev, &nd);
   if (rc) return rc;
-  if (cudaMemcpyAsync(Q, X, sizeof(zc) * (size_t)n * m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (cudaMemcpyAsync(Q, X, xb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return TDVP_ERR_CUDA;
   // barrier words and the error word must start at zero; the rest is written before it is read
   if (cudaMemsetAsync(nd.scratch + NA_OFF_WORDS, 0, 256, st) != cudaSuccess) return TDVP_ERR_CUDA;

@@ -1677,8 +1677,13 @@ int tdvp_controller_loss_grad(tdvp_ctx* ctx, const float* X, const float* t, int
     rows[(size_t)b * (MLP_NIN + 1) + MLP_NIN] = t[b];
   }
   float *d_rows = nullptr, *d_grad = nullptr;
-  CK(cudaMalloc(&d_rows, sizeof(float) * rows.size()));
-  CK(cudaMalloc(&d_grad, sizeof(float) * (MLP_NPARAM + 1)));
+  const cudaError_t e1 = cudaMalloc(&d_rows, sizeof(float) * rows.size());
+  const cudaError_t e2 = cudaMalloc(&d_grad, sizeof(float) * (MLP_NPARAM + 1));
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaFree(d_rows);
+    cudaFree(d_grad);
+    return fail(ctx, TDVP_ERR_OOM, "controller: cudaMalloc of the gradient buffers failed");
+  }
   int rc = TDVP_OK;
   if (cudaMemcpyAsync(d_rows, rows.data(), sizeof(float) * rows.size(), cudaMemcpyHostToDevice, ctx->st) != cudaSuccess)
     rc = fail(ctx, TDVP_ERR_CUDA, "controller: upload failed");

@@ -58,3 +58,20 @@ def test_stats_struct_layout_matches_the_header(tmp_path):
     out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert out[0] == ctypes.sizeof(StatsC)
     assert out[1:] == [getattr(StatsC, f).offset for f in fields]
+
+
+def test_noalloc_lq_rejects_overlapping_buffers_before_touching_the_device():
+    """X, Q and L of tdvp_lq_noalloc must be disjoint; the host check runs before any CUDA call,
+    so it needs no GPU (the pointers are never dereferenced)."""
+    n, m = 4, 8
+    xb, lb = 16 * n * m, 16 * n * n
+    base = 1 << 20
+    cases = [(base, base + xb - 16, base + 4 * xb),        # X and Q share 16 bytes
+             (base, base + 2 * xb, base + xb - 16),        # X and L
+             (base, base + 2 * xb, base + 3 * xb - 16),    # Q and L
+             (base, base, base + 4 * xb)]                  # in place
+    for x, q, l in cases:
+        with pytest.raises(pkg.TDVPError) as e:
+            pkg.lq_noalloc(n, m, x, q, l, 0)
+        assert e.value.code == -1
+    assert lb < xb

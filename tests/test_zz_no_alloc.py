@@ -19,6 +19,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_1907_12044_b300 as pkg  # noqa: E402
+from oracle import lq_rr  # noqa: E402
 
 
 def _noalloc(X):
@@ -53,6 +54,36 @@ def test_noalloc_lq_matches_allocating_gauge_shift_twice_in_a_row():
         assert np.abs(Q - Qr).max() < 1e-12
         assert np.abs(L - Lr).max() < 1e-11 * max(1.0, np.abs(Lr).max())
         assert np.abs(Q @ Q.conj().T - np.eye(X.shape[0])).max() < 1e-12
+
+
+def _rank_deficient_in_later_block(rng, n=256, m=16384, rank=250, support=260):
+    """Rank-250 rows supported on the first 260 columns: the 250 kept rows span almost all of
+    those columns (distance of each e_p far below 1/2), so the completions of the 6 dropped rows
+    are e_260..e_265, which lie in the second column slab of the kernel's blocks."""
+    G = rng.normal(size=(n, rank)) + 1j * rng.normal(size=(n, rank))
+    H = np.zeros((rank, m), dtype=complex)
+    H[:, :support] = rng.normal(size=(rank, support)) + 1j * rng.normal(size=(rank, support))
+    return G @ H
+
+
+def test_noalloc_lq_at_its_largest_sizes_matches_the_oracle_twice():
+    """n = 256 rows over m = 16384 columns (the documented limits; the block count is clamped
+    to the kernel's maximum): full rank, and rank deficient with the completion columns in a
+    block other than the first, against the oracle's gauge shift, each called twice in a row."""
+    rng = np.random.default_rng(256)
+    full = rng.normal(size=(256, 16384)) + 1j * rng.normal(size=(256, 16384))
+    deficient = _rank_deficient_in_later_block(rng)
+    for X in (full, deficient):
+        Lo, Qo = lq_rr(X)
+        for _ in range(2):
+            Q, L = _noalloc(X)
+            assert np.abs(Q - Qo).max() < 1e-12
+            assert np.abs(L - Lo).max() < 1e-11 * np.abs(Lo).max()
+            assert np.abs(Q @ Q.conj().T - np.eye(256)).max() < 1e-12
+    kept = np.abs(np.diag(Lo)) > 0
+    assert kept.sum() == 250
+    comp = [int(np.argmax(np.abs(Qo[j]))) for j in np.nonzero(~kept)[0]]
+    assert min(comp) >= 256                       # completions outside block 0's slab
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
