@@ -6,12 +6,18 @@ right-to-left half sweep) of every trajectory held on the GPU.  One site update 
 site evolution with its gauge shift, environment update and backward bond evolution, so a step
 of an N-site chain is 2N-1 site updates per trajectory.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference] [--precision fp64]
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference] [--precision P]
 
-Default workload: the FMO-sized Frenkel-Holstein chain (7 electronic sites x 10 Debye modes with
-10 levels = 77 sites), bond dimension 64, dt = 10 fs, product start (exciton on site 1),
-adaptive Lanczos with tolerance 1e-12.  All inputs are synthetic and seeded.
-With N > 1 (torchrun) every rank advances its own replica; there is no exchange.
+Workload: the FMO-sized Frenkel-Holstein chain (7 electronic sites x 10 Debye modes with 10
+levels = 77 sites), bond dimension 64, dt = 10 fs, product start (exciton on site 1).  All
+inputs are synthetic and seeded.  Three GPU arms run the same W warm-up and K timed steps:
+  - the timed arm (`value`): mixed-precision matvecs, Lanczos tolerance 1e-8, each step replayed
+    as a CUDA graph, learned Krylov controller trained on the warm-up;
+  - `fp64_arm`: the same in every respect except FP64 matvecs (isolates the precision);
+  - `plain_fp64_arm`: the plain method (FP64, tolerance 1e-12, convergence tested at every k,
+    launch by launch), the reference of the population error.
+With N > 1 (torchrun) every rank advances its own replica (a single trajectory is sequential
+along the chain) and the disorder realisations of the batched section are sharded by index.
 """
 from __future__ import annotations
 
@@ -32,33 +38,47 @@ METRIC = "TDVP-PS site-updates/s & % tensor peak, mixed vs FP64 GPU at pop. err 
 UNIT = "site-updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25      # B300 FP64 (no FP64 tensor path); measured DFMA ceiling ~0.95
+TF32_OF_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rate ratio
+
+# arithmetic of the Lanczos matvecs (TDVP_PREC_* of include/tdvp.h); the tensor-core input
+# format decides the peak a contraction is measured against
+PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16": 3, "bf16x3": 4, "tf32_3m": 5, "bf16_3m": 6}
+TENSOR_FMT = {"tf32": "tf32", "tf32x3": "tf32", "tf32_3m": "tf32", "bf16": "bf16", "bf16x3": "bf16",
+              "bf16_3m": "bf16"}
+DTYPE = {"fp64": "f64 (complex128)",
+         "tf32": "tf32 tensor cores, 4M complex products, f32 accumulate; f64 Lanczos/QR",
+         "tf32x3": "tf32x3 split tensor cores, 4M, f32 accumulate; f64 Lanczos/QR",
+         "tf32_3m": "tf32 tensor cores, 3M (Gauss) complex products, f32 accumulate; f64 Lanczos/QR",
+         "bf16": "bf16 tensor cores, 4M, f32 accumulate; f64 Lanczos/QR",
+         "bf16x3": "bf16x3 split tensor cores, 4M, f32 accumulate; f64 Lanczos/QR",
+         "bf16_3m": "bf16 tensor cores, 3M (Gauss), f32 accumulate; f64 Lanczos/QR"}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "tf32x3"],
-                    help="arithmetic of the Lanczos matvecs on the timed arm; FP64 is always timed beside it")
+    ap.add_argument("--precision", default="tf32x3", choices=sorted(PREC),
+                    help="arithmetic of the Lanczos matvecs on the timed arm")
     ap.add_argument("--D", type=int, default=64)
     ap.add_argument("--dt", type=float, default=10.0)
-    ap.add_argument("--tol", type=float, default=1e-12, help="Lanczos tolerance of the FP64 arm")
-    ap.add_argument("--mixed-tol", type=float, default=1e-8,
-                    help="Lanczos tolerance of the mixed-precision arms: the TF32x3 matvecs are accurate to "
-                         "~1e-7 relative, so a tighter tolerance only adds iterations below that noise")
+    ap.add_argument("--tol", type=float, default=1e-8,
+                    help="Lanczos tolerance of the timed arm and of the FP64 arm beside it: the TF32x3 "
+                         "matvecs are accurate to ~1e-7 relative, so a tighter tolerance only adds "
+                         "iterations below that noise")
+    ap.add_argument("--plain-tol", type=float, default=1e-12, help="Lanczos tolerance of the plain FP64 arm")
     ap.add_argument("--rank-rtol", type=float, default=1e-6,
-                    help="rank threshold of the gauge-shift QR, the same on both arms")
+                    help="rank threshold of the gauge-shift QR, the same on every arm")
+    ap.add_argument("--arms", default="mixed,fp64,plain",
+                    help="GPU arms to run (mixed = the timed arm, fp64 = the same with FP64 matvecs, "
+                         "plain = FP64 at --plain-tol, every k tested, launch by launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-prof", action="store_true", help="time without per-launch events")
-    ap.add_argument("--no-learned", action="store_true", help="mixed arm without the learned Krylov controller")
-    ap.add_argument("--only-timed-arm", action="store_true",
-                    help="skip the FP64 reference arm (for profiling captures; no population error then)")
-    ap.add_argument("--no-graph", action="store_true",
-                    help="timed arm launch by launch instead of replaying each step as a CUDA graph "
-                         "(the FP64 arm is always launch by launch: the plain method)")
+    ap.add_argument("--no-prof", action="store_true", help="skip the per-kernel breakdown step")
+    ap.add_argument("--no-learned", action="store_true", help="no learned Krylov controller")
+    ap.add_argument("--no-graph", action="store_true", help="launch by launch instead of CUDA-graph steps")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the step's kernels in plain stream order (no programmatic dependent launch)")
     ap.add_argument("--kernel-case", choices=["heff", "qr"], default=None,
@@ -66,19 +86,22 @@ def parse():
                          "kernel captures): heff = one H_eff matvec at a bath-mode site of a random D-bond "
                          "state, qr = one gauge-shift QR of a rank-8 640 x 64 matrix")
     ap.add_argument("--batched", type=int, default=32,
-                    help="also time R disorder realisations with ragged bond dims in the same launches (0: skip)")
-    return ap.parse_args()
+                    help="also time R disorder realisations with ragged bond dims in the same launches "
+                         "(0: skip); with N ranks each takes the realisations r = rank mod N")
+    ap.add_argument("--batched-steps", type=int, default=None, help="timed steps of the batched section")
+    ap.add_argument("--batched-dmax", type=int, default=128, help="largest ragged bond dimension")
+    ap.add_argument("--long", type=int, default=0,
+                    help="accuracy run instead of the bench line: this many steps of the timed arm and "
+                         "of the plain FP64 arm from the same start, Eq. error and max |dP| every 100 steps")
+    ap.add_argument("--out", default=None, help="also write the JSON line to this file")
+    return ap.parse_args(argv)
 
 
 def workload(args):
     import workloads as wl
     p = wl.fmo_sized()
     return p, {"workload": f"{p.name}: {len(p.chain())} sites, D={args.D}, dt={args.dt} fs, product start",
-               "model": "Frenkel-Holstein (synthetic FMO-sized, Debye bath)",
-               "sites": len(p.chain()), "bond_dim": args.D, "dt_fs": args.dt,
-               "krylov": f"adaptive Lanczos, tol {arm_tol(args, args.precision):g}", "precision": args.precision,
-           "rank_rtol": args.rank_rtol,
-               "realisations_per_gpu": 1}
+               "sites": len(p.chain()), "bond_dim": args.D, "dt_fs": args.dt, "rank_rtol": args.rank_rtol}
 
 
 class ClockSampler:
@@ -140,13 +163,11 @@ def flush_l2(buf):
     buf.add_(1)          # 256 MiB read+write through L2 (126 MB), on the current stream
 
 
-PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2}
-TF32_OF_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rate ratio
-
-
-def arm_tol(args, precision):
-    """Lanczos tolerance of an arm: --tol for FP64, --mixed-tol (else --tol) for TF32 / TF32x3."""
-    return args.mixed_tol if (precision != "fp64" and args.mixed_tol is not None and args.mixed_tol > 0) else args.tol
+def sig(x, n=4):
+    """x rounded to n significant digits (keeps the JSON line short)."""
+    if x is None or not np.isfinite(x) or x == 0:
+        return x
+    return float(f"{x:.{n}g}")
 
 
 def train_controller(eng, seed=0):
@@ -156,44 +177,56 @@ def train_controller(eng, seed=0):
     return eng.controller_train(epochs=150, batch=256, lr=3e-3)
 
 
-def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned=False):
+ARMS = {
+    # name: (precision, tolerance attribute, graph, learned, test every k)
+    "mixed": (None, "tol", True, True, False),
+    "fp64": ("fp64", "tol", True, True, False),
+    "plain": ("fp64", "plain_tol", False, False, True),
+}
+
+
+def arm_setup(args, name):
+    prec, tol_attr, graph, learned, every = ARMS[name]
+    prec = prec or args.precision
+    graph = graph and not args.no_graph and args.warmup >= 1
+    learned = learned and not args.no_learned
+    return prec, getattr(args, tol_attr), graph, learned, every
+
+
+def timed_run(args, p, name, world, dev, stream, flush):
     """W warm-up steps, then K timed steps (L2 flushed before each); returns timing and populations.
 
-    The plain method tests Lanczos convergence at every k.  With ``learned`` the warm-up steps
-    log their solves, the controller is trained on them and the timed steps use it.  A mixed arm
-    replays each step as a CUDA graph (unless --no-graph): the last warm-up step captures it, and
-    since per-launch events are not available inside a graph, one more step after the timed ones
-    runs launch by launch with CUDA-event timing for the per-kernel breakdown."""
+    With the learned controller the warm-up steps log their solves and the controller is trained
+    on them.  A graph arm captures its step in the last warm-up step.  After the timed steps one
+    more step runs launch by launch with per-launch CUDA events for the per-kernel breakdown."""
     import torch
     import paper_1907_12044_b300 as pkg
-    graph = precision != "fp64" and not args.no_graph and args.warmup >= 1
-    tol = arm_tol(args, precision)
+    prec, tol, graph, learned, every = arm_setup(args, name)
+    P = PREC[prec]
     eng = pkg.Engine(n_realisations=1, stream=stream.cuda_stream)
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
-    eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
+    eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1 if every else 0)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
-    eng.autotune()          # QR launch shape per gauge-shift shape (both arms)
+    eng.autotune()          # QR launch shape per gauge-shift shape
     pops = [eng.observables(0)[0]]
     if learned:
         eng.controller_logging(1 << 20)
     for _ in range(args.warmup - (1 if graph else 0)):
-        eng.step(args.dt, 1, precision=PREC[precision], tol=tol)
+        eng.step(args.dt, 1, precision=P, tol=tol)
         pops.append(eng.observables(0)[0])
     ctl = None
     if learned:
         nlog = eng.stats()["krylov_solves"]
         eng.controller_logging(0)
-        ctl = {"train_loss": train_controller(eng), "samples": int(nlog)}
+        ctl = {"train_loss": sig(train_controller(eng)), "samples": int(nlog)}
     mode = pkg.KRYLOV_LEARNED if learned else pkg.KRYLOV_ADAPTIVE
     if graph:
         eng.set_option(pkg.OPT_GRAPH, 1)
-        eng.step(args.dt, 1, precision=PREC[precision], krylov_mode=mode, tol=tol)   # capture
+        eng.step(args.dt, 1, precision=P, krylov_mode=mode, tol=tol)   # capture
         pops.append(eng.observables(0)[0])
     torch.cuda.synchronize()
     eng.reset_stats()
-    if prof and not graph:
-        eng.set_profiling(True)
     times = []
     if world > 1:
         torch.distributed.barrier()
@@ -204,7 +237,7 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            eng.step(args.dt, 1, precision=PREC[precision], krylov_mode=mode, tol=tol)
+            eng.step(args.dt, 1, precision=P, krylov_mode=mode, tol=tol)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -213,22 +246,19 @@ def timed_run(args, p, precision, rank, world, dev, stream, flush, prof, learned
     if world > 1:
         torch.distributed.barrier()
     st = eng.stats()
-    eng.set_profiling(False)
-    if prof and graph:
+    prof = None
+    if not args.no_prof:
         # per-kernel CUDA-event breakdown of one more (untimed) step, launch by launch
         eng.set_option(pkg.OPT_GRAPH, 0)
         eng.reset_stats()
         eng.set_profiling(True)
-        eng.step(args.dt, 1, precision=PREC[precision], krylov_mode=mode, tol=tol)
+        eng.step(args.dt, 1, precision=P, krylov_mode=mode, tol=tol)
         eng.set_profiling(False)
-        ps = eng.stats()
-        for k in ("prof_ms", "prof_flops", "prof_launches", "prof_bytes"):
-            st[k] = {c: v * args.steps for c, v in ps[k].items()}
-        st["prof_note"] = "per-kernel breakdown from one launch-by-launch step after the timed ones, x steps"
+        prof = eng.stats()
     eng.close()
     ms = max_over_ranks(float(np.sum(times)), world)
-    return {"ms": ms, "stats": st, "pops": np.array(pops), "clocks": clk.summary(), "controller": ctl,
-            "graph": graph}
+    return {"ms": ms, "stats": st, "prof": prof, "pops": np.array(pops), "clocks": clk.summary(),
+            "controller": ctl, "graph": graph, "prec": prec, "tol": tol, "learned": learned, "every": every}
 
 
 def max_over_ranks(ms, world):
@@ -249,62 +279,92 @@ def site_update_rate(n_sites, steps, world, ms):
     return (2 * n_sites - 1) * steps * world / (ms / 1e3)
 
 
-# kernel and arithmetic of each timed category with algorithmic flop counts
-ROOF_KERNELS = {"qr": ("bqr_kernel / cqr_kernel (FP64 gauge-shift QR, grid or cluster kernel autotuned per shape)",
-                       "alu"),
-                "gemm": ("zgemm_kernel (FP64 complex GEMM)", "alu"),
-                "tc_gemm": ("tc_cgemm_kernel (tcgen05 kind::tf32)", "tensor"),
-                "lanczos_vec": ("lz_start / lz_dots / lz_upd / lz_next / lz_combine (FP64 Lanczos vectors: "
-                                "two Gram-Schmidt passes, next vector, combination)", "hbm")}
+def pop_error(dt, pops, ref):
+    """Eq. error at the last compared time (trapezoid in time) and max |dP|, against `ref`."""
+    n = min(len(pops), len(ref))
+    t = dt * np.arange(n)
+    dP = np.abs(np.asarray(pops[:n]) - np.asarray(ref[:n]))
+    if n < 2:
+        return 0.0, float(dP.max()) if dP.size else 0.0
+    s = dP.sum(1)
+    err = float(np.sum(0.5 * (s[1:] + s[:-1]) * np.diff(t)) / (dP.shape[1] * t[-1]))
+    return err, float(dP.max())
 
+
+# kernel and roof of each timed category
+ROOF_KERNELS = {"qr": ("bqr_kernel/cqr_kernel (FP64 gauge-shift QR)", "alu"),
+                "gemm": ("zgemm_kernel (FP64 complex GEMM)", "alu"),
+                "tc_gemm": ("tc_cgemm_kernel (tcgen05)", "tensor"),
+                "lanczos_vec": ("lz_* (FP64 Lanczos vectors)", "hbm")}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel in its current form, on the bench's dominant shape; None where no such capture exists or
-# the kernel has changed since (bqr_kernel: 0.89 MB per 640 x 64 rank-8 shift at commit 92e9268,
-# profiles/bqr_rank8_640x64.md, before a change of its certain-drop margin)
+# kernel as it is built now, on the bench's shapes: (bytes, capture).  A kernel missing here has no
+# capture of its current form, and its `traffic` is null.
 TRAFFIC = {}
 
 
-def roofline(args, st, cat):
-    """Achieved vs peak for one timed category: algorithmic flops / summed CUDA-event time."""
-    cat_ms = st["prof_ms"]
-    total = sum(cat_ms.values())
-    if cat not in ROOF_KERNELS:
-        return {"kernel": cat, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None, "share_of_step": cat_ms[cat] / max(total, 1e-9),
-                "note": "no algorithmic flop count for this category"}
+def peaks():
+    return json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+
+
+def tensor_peak(fmt):
+    pk = peaks()
+    bf16 = pk.get("bf16_tflops")
+    src = "measured bf16 burst" if bf16 else "fallback 1800 TFLOP/s bf16"
+    bf16 = bf16 or 1800.0
+    if fmt == "tf32":
+        return bf16 * TF32_OF_BF16, src + " x nominal tf32/bf16 1.1/2.25"
+    return bf16, src
+
+
+def roofline(prof, cat, prec):
+    """Achieved vs peak for one category of the profiled step: algorithmic work / summed
+    CUDA-event time of its launches.  Lanczos vectors: Sec. 8(d)'s count of k^2/2 vectors of
+    16 n bytes per solve (each iteration j reads V_0..V_j once); `bytes_4pass` is the count of the
+    kernels as written (four reads per iteration: dot and update of both Gram-Schmidt passes)."""
+    ms, nl = prof["prof_ms"][cat], prof["prof_launches"][cat]
     name, bound = ROOF_KERNELS[cat]
-    ms, fl, nl = cat_ms[cat], st["prof_flops"][cat], st["prof_launches"][cat]
+    base = {"kernel": name, "bound": bound, "launches": nl, "avg_launch_us": sig(1e3 * ms / max(nl, 1)),
+            "traffic": TRAFFIC.get(cat, (None, None))[0]}
     if bound == "hbm":
-        # algorithmic bytes (counted by the library per finished solve) / summed CUDA-event time
-        by = st.get("prof_bytes", {}).get(cat, 0.0)
-        ach = by / (ms * 1e-3) / 1e9 if ms > 0 and by > 0 else None
-        pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        by = prof.get("prof_bytes", {}).get(cat, 0.0)          # library count, 4 passes
+        by_alg = prof.get("lz_alg_bytes", 0.0)
+        pk = peaks()
         peak = pk.get("hbm_gbs", 6400.0)
-        src = ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk
-               else "fallback 6.4 TB/s (no MEASURED_PEAKS.json)")
-        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak if ach else None, "traffic": TRAFFIC.get(cat, (None, None))[0],
-                "traffic_source": TRAFFIC.get(cat, (None, None))[1], "peak_source": src, "launches": nl,
-                "algorithmic_bytes_per_launch": by / max(nl, 1),
-                "avg_launch_us": 1e3 * ms / max(nl, 1), "share_of_step": ms / max(total, 1e-9),
-                "note": "algorithmic bytes: 16 n (2 k (k+1) + 10 k + 5) per Lanczos solve of dimension k on "
-                        "n complex elements (each iteration j reads V_0..V_j for the dot and the update of "
-                        "both Gram-Schmidt passes); the vectors of a solve (<= 7 MB here) stay in L2, so "
-                        "these launches are latency bound, far from the HBM roof"}
+        ach = by_alg / (ms * 1e-3) / 1e9 if ms > 0 else None
+        return dict(base, achieved=sig(ach), peak=peak, unit="GB/s", frac=sig(ach / peak) if ach else None,
+                    bytes_per_launch=sig(by_alg / max(nl, 1)), frac_4pass=sig(by / (ms * 1e-3) / 1e9 / peak) if ms else None,
+                    peak_source="measured" if "hbm_gbs" in pk else "fallback")
+    fl = prof["prof_flops"][cat]
     ach = fl / (ms * 1e-3) / 1e12 if ms > 0 else None
     if bound == "tensor":
-        pk = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {"bf16_tflops": 1800.0}
-        peak = pk["bf16_tflops"] * TF32_OF_BF16
-        src = "measured bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25"
+        peak, src = tensor_peak(TENSOR_FMT.get(prec, "tf32"))
     else:
-        peak, src = FP64_NOMINAL_TFLOPS, "B300 FP64 nominal 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry)"
-    return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak if ach else None, "traffic": TRAFFIC.get(cat, (None, None))[0],
-            "traffic_source": TRAFFIC.get(cat, (None, None))[1], "peak_source": src, "launches": nl,
-            "avg_launch_us": 1e3 * ms / max(nl, 1), "share_of_step": ms / max(total, 1e-9),
-            "note": "algorithmic flops: 8 per complex multiply-add of the logical products "
-                    "(QR: 2 n^2 m per n x m shift, two Gram-Schmidt passes)"}
+        peak, src = FP64_NOMINAL_TFLOPS, "FP64 nominal (no FP64 entry measured)"
+    return dict(base, achieved=sig(ach), peak=sig(peak), unit="TFLOP/s", frac=sig(ach / peak) if ach else None,
+                flops_per_launch=sig(fl / max(nl, 1)), peak_source=src)
+
+
+def lz_alg_bytes(st):
+    """Sec. 8(d)'s algorithmic bytes of the Lanczos vectors of the profiled step: k(k+1)/2 reads of
+    a 16 n-byte vector per solve, from the library's 4-pass count 16 n (2k(k+1) + 10k + 5) summed
+    over solves, taking k at the mean Krylov dimension."""
+    k = st["krylov_dim_sum"] / max(st["krylov_solves"], 1)
+    by4 = st["prof_bytes"]["lanczos_vec"]
+    return by4 * (0.5 * k * (k + 1)) / (2 * k * (k + 1) + 10 * k + 5) if k > 0 else 0.0
+
+
+def arm_summary(args, run, N, world):
+    st = run["stats"]
+    out = {"value": sig(site_update_rate(N, args.steps, world, run["ms"])), "unit": UNIT,
+           "ms_per_step": sig(run["ms"] / args.steps), "precision": run["prec"], "tol": run["tol"],
+           "graph": run["graph"], "learned": run["learned"], "every_k": run["every"],
+           "krylov_mean": sig(st["krylov_dim_sum"] / max(st["krylov_solves"], 1), 3),
+           "tri_evals_per_step": sig(st["tri_evals"] / args.steps, 4),
+           "launches_per_step": int(st["kernel_launches"] / max(args.steps, 1))}
+    if run["prof"]:
+        out["phase_ms"] = {k: sig(v, 3) for k, v in run["prof"]["prof_phase_ms"].items() if v > 0}
+    return out
 
 
 def run_ours(args, rank, world):
@@ -315,129 +375,157 @@ def run_ours(args, rank, world):
     N = len(p.chain())
     stream = torch.cuda.current_stream()
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    prof = not args.no_prof
-    run = None if args.precision == "fp64" else timed_run(args, p, args.precision, rank, world, dev, stream, flush, prof,
-                                                          learned=not args.no_learned)
-    ref = run if args.only_timed_arm and run is not None else timed_run(args, p, "fp64", rank, world, dev, stream,
-                                                                        flush, prof)
-    if run is None:
-        run = ref
-    value = site_update_rate(N, args.steps, world, run["ms"])
-    fp64_value = site_update_rate(N, args.steps, world, ref["ms"])
-    # population error of the timed arm against the FP64 arm on the same steps (Eq. error)
-    t = args.dt * np.arange(len(run["pops"]))
-    dP = np.abs(run["pops"] - ref["pops"])
-    err = float(np.sum(0.5 * (dP.sum(1)[1:] + dP.sum(1)[:-1]) * np.diff(t)) / (p.n_el * t[-1])) if len(t) > 1 else 0.0
-    st = run["stats"]
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": run["ms"] / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None,
-           "dtype": {"fp64": "f64 (complex128)", "tf32": "tf32 tensor cores, f32 accumulate; f64 Lanczos/QR",
-                     "tf32x3": "tf32x3 split tensor cores, f32 accumulate; f64 Lanczos/QR"}[args.precision],
-           "data": "synthetic (seeded FMO-sized Frenkel-Holstein chain)",
-           "config": dict(cfg, precision=args.precision,
-                          execution=("each step replayed as one CUDA graph (a conditional while node per "
-                                     "Lanczos exponential)") if run["graph"] else "launch by launch",
+    names = [a for a in args.arms.split(",") if a]
+    runs = {a: timed_run(args, p, a, world, dev, stream, flush) for a in names}
+    main = runs.get("mixed") or runs[names[0]]
+    st = main["stats"]
+    out = {"metric": METRIC, "value": sig(site_update_rate(N, args.steps, world, main["ms"]), 5), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sig(main["ms"] / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": DTYPE[main["prec"]], "data": "synthetic (seeded FMO-sized FH chain)",
+           "config": dict(cfg, precision=main["prec"], tol=main["tol"],
+                          krylov="learned controller" if main["learned"] else "adaptive",
+                          execution="CUDA-graph steps" if main["graph"] else "launch by launch",
                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                           l2="flushed between timed steps (256 MiB write)"),
-           "fp64_arm": {"value": fp64_value, "unit": UNIT, "ms_per_step": ref["ms"] / args.steps,
-                        "krylov": f"adaptive, convergence tested at every k, tol {args.tol:g}",
-                        "tri_evals_per_step": ref["stats"]["tri_evals"] / args.steps,
-                        "kernel_time_ms": {k: round(v, 3) for k, v in ref["stats"]["prof_ms"].items()}},
-           "learned_controller": run["controller"],
-           "tri_evals_per_step": run["stats"]["tri_evals"] / args.steps,
-           "speedup_vs_fp64": value / fp64_value,
-           "pop_error_vs_fp64": {"eq_error_final": err, "max_abs_dP": float(dP.max()),
-                                 "steps_compared": len(t) - 1},
-           "gpu_launches": int(st["kernel_launches"]), "clocks": run["clocks"]}
-    if prof:
-        cat_ms = st["prof_ms"]
-        top = max(cat_ms, key=cat_ms.get)
-        out["roofline"] = roofline(args, st, top)
-        if top != "tc_gemm" and args.precision != "fp64":
-            out["roofline_tc_gemm"] = roofline(args, st, "tc_gemm")
-        # the other large categories against their own roofs (QR: FP64 ALU, Lanczos vectors: HBM)
-        out["roofline_other"] = {c: roofline(args, st, c) for c in ("qr", "lanczos_vec", "gemm")
-                                 if c != top and cat_ms.get(c, 0) > 0}
-        out["kernel_time_ms"] = {k: round(v, 3) for k, v in cat_ms.items()}
-        out["dominant_category"] = top
-    out["krylov"] = {"mean_dim": st["krylov_dim_sum"] / max(st["krylov_solves"], 1),
-                     "max_dim": st["krylov_dim_max"], "host_syncs": st["host_syncs"]}
+           "gpu_launches": int(st["kernel_launches"]), "clocks": main["clocks"]}
+    if "fp64" in runs and main is not runs["fp64"]:
+        out["speedup_vs_fp64"] = sig(runs["fp64"]["ms"] / main["ms"])
+    if "plain" in runs and main is not runs["plain"]:
+        out["speedup_vs_plain_fp64"] = sig(runs["plain"]["ms"] / main["ms"])
+        e, m = pop_error(args.dt, main["pops"], runs["plain"]["pops"])
+        out["pop_error_vs_fp64"] = {"eq_error": sig(e, 3), "max_abs_dP": sig(m, 3),
+                                    "steps": len(main["pops"]) - 1, "against": "plain_fp64_arm"}
+    if "fp64" in runs and main is not runs["fp64"]:
+        e, m = pop_error(args.dt, main["pops"], runs["fp64"]["pops"])
+        out["pop_error_vs_fp64_arm"] = {"eq_error": sig(e, 3), "max_abs_dP": sig(m, 3)}
+    out["arms"] = {("timed" if r is main else a): arm_summary(args, r, N, world) for a, r in runs.items()}
+    if main["controller"]:
+        out["learned_controller"] = main["controller"]
+    if main["prof"]:
+        pr = main["prof"]
+        pr["lz_alg_bytes"] = lz_alg_bytes(pr)
+        cat_ms = pr["prof_ms"]
+        ranked = sorted((c for c in ROOF_KERNELS if cat_ms.get(c, 0) > 0), key=lambda c: -cat_ms[c])
+        if ranked:
+            out["roofline"] = roofline(pr, ranked[0], main["prec"])
+            out["roofline"]["category"] = ranked[0]
+            out["roofline_other"] = {c: {k: v for k, v in roofline(pr, c, main["prec"]).items()
+                                         if k in ("achieved", "peak", "unit", "frac", "avg_launch_us", "bound")}
+                                     for c in ranked[1:]}
+        tot = sum(cat_ms.values())
+        out["kernel_share"] = {c: sig(v / tot, 3) for c, v in cat_ms.items() if v > 0}
     return out, p
 
 
-def run_batched(args, R):
+def shard(R, rank, world):
+    """Realisation indices of one rank: r = rank, rank + world, ... (no exchange during the run)."""
+    return list(range(rank, R, world))
+
+
+def run_batched(args, R, rank=0, world=1):
     """R static-disorder realisations of the FMO-sized chain with bond dims drawn from
-    {32,48,64,96,128}, advanced together; total site updates per second."""
+    {32,48,64,96,128}, sharded by index over the ranks; each rank advances its share in the same
+    launches.  Returns this rank's share, its timing and its final populations."""
     import torch
     import workloads as wl
     import paper_1907_12044_b300 as pkg
     base = wl.fmo_sized()
-    Ds = wl.ragged_bond_dims(R)
-    eng = pkg.Engine(n_realisations=R)
+    choices = tuple(c for c in (32, 48, 64, 96, 128) if c <= args.batched_dmax)
+    Ds = wl.ragged_bond_dims(R, choices=choices)
+    mine = shard(R, rank, world)
+    steps = args.batched_steps or args.steps
+    tol = args.tol
+    P = PREC[args.precision]
+    eng = pkg.Engine(n_realisations=len(mine))
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
-    for r in range(R):
-        q = wl.disorder_realisation(base, r)
-        eng.build_mpo(r, q)
-        eng.init_mps(r, Ds[r], q.exciton_site)
+    for q, r in enumerate(mine):
+        p = wl.disorder_realisation(base, r)
+        eng.build_mpo(q, p)
+        eng.init_mps(q, Ds[r], p.exciton_site)
     eng.autotune()
-    eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
     graph = not args.no_graph and args.warmup >= 1
-    if not args.no_learned:
+    learned = not args.no_learned
+    if learned:
         eng.controller_logging(1 << 22)
     for _ in range(args.warmup - (1 if graph else 0)):
-        eng.step(args.dt, 1, precision=PREC[args.precision], tol=arm_tol(args, args.precision))
+        eng.step(args.dt, 1, precision=P, tol=tol)
     mode = pkg.KRYLOV_ADAPTIVE
-    if not args.no_learned:
+    if learned:
         eng.controller_logging(0)
         train_controller(eng)
         mode = pkg.KRYLOV_LEARNED
     if graph:
         eng.set_option(pkg.OPT_GRAPH, 1)
-        eng.step(args.dt, 1, precision=PREC[args.precision], krylov_mode=mode, tol=arm_tol(args, args.precision))   # capture
+        eng.step(args.dt, 1, precision=P, krylov_mode=mode, tol=tol)   # capture
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     eng.reset_stats()
     e0.record(stream)
-    eng.step(args.dt, args.steps, precision=PREC[args.precision], krylov_mode=mode, tol=arm_tol(args, args.precision))
+    eng.step(args.dt, steps, precision=P, krylov_mode=mode, tol=tol)
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     st = eng.stats()
+    pops = {r: eng.observables(q)[0].tolist() for q, r in enumerate(mine)}
     eng.close()
+    ms_max = max_over_ranks(ms, world)
     N = len(base.chain())
-    return {"realisations": R, "bond_dims": "ragged from {32,48,64,96,128} (seed 12044)",
-            "precision": args.precision, "value": (2 * N - 1) * R * args.steps / (ms / 1e3),
-            "unit": UNIT, "ms_per_step": ms / args.steps, "gpu_launches": int(st["kernel_launches"]),
-            "qr_blocks": "autotuned", "krylov": "learned controller" if not args.no_learned else "adaptive",
-            "execution": "each step of all realisations replayed as one CUDA graph" if graph else "launch by launch"}
+    return {"realisations": R, "per_rank": len(mine), "bond_dims": f"ragged from {list(choices)} (seed 12044)",
+            "precision": args.precision, "steps": steps,
+            "value": sig((2 * N - 1) * R * steps / (ms_max / 1e3)), "unit": UNIT,
+            "ms_per_step": sig(ms_max / steps), "gpu_launches": int(st["kernel_launches"]),
+            "krylov": "learned controller" if learned else "adaptive",
+            "execution": "CUDA-graph steps" if graph else "launch by launch",
+            "sharding": f"realisation r on rank r mod {world}" if world > 1 else "one GPU"}, pops
+
+
+def gather_pops(pops, rank, world):
+    """Final populations of every realisation on rank 0, over a host (gloo) group: the only
+    exchange of the sharded batched run, after the timed region."""
+    if world <= 1:
+        return pops
+    import torch.distributed as dist
+    grp = dist.new_group(backend="gloo")
+    allp = [None] * world if rank == 0 else None
+    dist.gather_object(pops, allp, dst=0, group=grp)
+    if rank != 0:
+        return None
+    out = {}
+    for d in allp:
+        out.update(d)
+    return out
 
 
 def run_e2e(args, p):
-    """The timed arm's workload end to end through the public API, on the host clock: the same
-    options, warm-up steps and controller training (untimed), then --steps steps, each followed
-    by a device->host read of that step's populations, energy and norm.  The MPO parameters and
-    the initial state go host->device once, before the warm-up; the state stays resident."""
+    """The timed arm end to end through the public API on the host clock: build_mpo from host
+    parameters, init_mps, autotune, the warm-up steps with their solve log, controller training,
+    then the timed steps, each followed by a device->host read of populations, energy and norm.
+    The value counts the site updates of every step (warm-up included) over that whole time."""
     import torch
     import paper_1907_12044_b300 as pkg
     N = len(p.chain())
+    prec, tol, graph, learned, every = arm_setup(args, "mixed")
+    P = PREC[prec]
+    d = np.asarray(p.phys_dims())
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     eng = pkg.Engine(n_realisations=1)
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
-    eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
-    torch.cuda.synchronize()
-    upload_s = time.perf_counter() - t0
     eng.autotune()
-    learned = args.precision != "fp64" and not args.no_learned
-    graph = args.precision != "fp64" and not args.no_graph and args.warmup >= 1
     if learned:
         eng.controller_logging(1 << 20)
+    nsteps = 0
     for _ in range(args.warmup - (1 if graph else 0)):
-        eng.step(args.dt, 1, precision=PREC[args.precision], tol=arm_tol(args, args.precision))
+        eng.step(args.dt, 1, precision=P, tol=tol)
+        eng.observables(0)
+        nsteps += 1
     mode = pkg.KRYLOV_ADAPTIVE
     if learned:
         eng.controller_logging(0)
@@ -445,40 +533,147 @@ def run_e2e(args, p):
         mode = pkg.KRYLOV_LEARNED
     if graph:
         eng.set_option(pkg.OPT_GRAPH, 1)
-        eng.step(args.dt, 1, precision=PREC[args.precision], krylov_mode=mode, tol=arm_tol(args, args.precision))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        eng.step(args.dt, 1, precision=PREC[args.precision], krylov_mode=mode, tol=arm_tol(args, args.precision))
+    for _ in range(args.steps + (1 if graph else 0)):
+        eng.step(args.dt, 1, precision=P, krylov_mode=mode, tol=tol)
         pops, E, nrm = eng.observables(0)
+        nsteps += 1
     dt = time.perf_counter() - t0
-    d, bd, w = eng.chain_info(0)
     f = p.flat()
-    h2d_once = sum(np.asarray(v).nbytes for v in f.values()) + sum(
-        16 * int(bd[i]) * int(d[i]) * int(bd[i + 1]) for i in range(N))
+    h2d = sum(np.asarray(v).nbytes for v in f.values())
     eng.close()
-    return {"value": (2 * N - 1) * args.steps / dt, "unit": UNIT,
-            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * (p.n_el + 2),
-            "includes": "steps through Engine.step and a populations/energy/norm readback after each; "
-                        "state resident on the device between steps",
-            "h2d_bytes_once": h2d_once, "upload_and_build_s": upload_s}
+    return {"value": sig(site_update_rate(N, nsteps, 1, 1e3 * dt)), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d / nsteps), "d2h_bytes_per_step": 8 * (p.n_el + 2),
+            "steps": nsteps, "seconds": sig(dt),
+            "includes": "engine, build_mpo (host params), init_mps, autotune, warm-up + controller training, "
+                        "graph capture, steps with a populations/energy/norm read after each"}
 
 
-def oracle_rate(p, args, n_steps=1):
-    """The CPU oracle as it stands on the same workload; returns (site-updates/s, threads, seconds)."""
-    from oracle import TDVPState, tdvp_ps_step
+def oracle_threads():
     try:
         from threadpoolctl import threadpool_info
-        threads = max([x.get("num_threads", 1) for x in threadpool_info()] or [1])
+        return max([x.get("num_threads", 1) for x in threadpool_info()] or [1])
     except Exception:
-        threads = os.cpu_count()
+        return os.cpu_count()
+
+
+def oracle_run(p, args, warmup, steps, budget_s=None, threads=None):
+    """The CPU oracle as it stands on the same workload and the same steps as the GPU arms: the
+    product start, `warmup` untimed steps, then up to `steps` timed ones (fewer if `budget_s`
+    runs out).  Same Lanczos tolerance and rank threshold as the timed arm.  Returns
+    (site-updates/s, threads, timed steps, seconds)."""
+    from oracle import TDVPState, tdvp_ps_step
     st = TDVPState.start(p, D=args.D)
-    N = len(p.chain())
-    t0 = time.perf_counter()
-    for _ in range(n_steps):
+    for _ in range(warmup):
         tdvp_ps_step(st, args.dt, tol=args.tol, rank_rtol=args.rank_rtol)
-    dt = time.perf_counter() - t0
-    return (2 * N - 1) * n_steps / dt, threads, dt
+    N = len(p.chain())
+
+    def timed():
+        t0 = time.perf_counter()
+        n = 0
+        while n < steps:
+            tdvp_ps_step(st, args.dt, tol=args.tol, rank_rtol=args.rank_rtol)
+            n += 1
+            if budget_s is not None and time.perf_counter() - t0 > budget_s:
+                break
+        return n, time.perf_counter() - t0
+
+    if threads is not None:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=threads):
+            n, dt = timed()
+    else:
+        threads = oracle_threads()
+        n, dt = timed()
+    return (2 * N - 1) * n / dt, threads, n, dt
+
+
+def cpu_baseline(p, args):
+    """The oracle on the host cores at all threads and at 1 thread: one step each after the
+    warm-up steps (steps W+1 and W+2 of the same trajectory)."""
+    from oracle import TDVPState, tdvp_ps_step
+    N = len(p.chain())
+    st = TDVPState.start(p, D=args.D)
+    for _ in range(args.warmup):
+        tdvp_ps_step(st, args.dt, tol=args.tol, rank_rtol=args.rank_rtol)
+    t0 = time.perf_counter()
+    tdvp_ps_step(st, args.dt, tol=args.tol, rank_rtol=args.rank_rtol)
+    t_all = time.perf_counter() - t0
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(limits=1):
+        t0 = time.perf_counter()
+        tdvp_ps_step(st, args.dt, tol=args.tol, rank_rtol=args.rank_rtol)
+        t_one = time.perf_counter() - t0
+    cores = oracle_threads()
+    return {"value": sig((2 * N - 1) / t_all), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1thread": sig((2 * N - 1) / t_one), "host_cpus": os.cpu_count(),
+            "sample": f"step {args.warmup + 1} (all {cores} threads, {t_all:.1f} s) and step {args.warmup + 2} "
+                      f"(1 thread, {t_one:.1f} s) after {args.warmup} untimed steps, tol {args.tol:g}"}
+
+
+def run_reference(args, world):
+    """The reference arm: the CPU oracle, as it stands, on the timed arm's workload, tolerance and
+    rank threshold, timing steps W+1.. of the same trajectory (bounded to ~150 s)."""
+    p, cfg = workload(args)
+    value, thr, n, secs = oracle_run(p, args, args.warmup, args.steps, budget_s=150.0)
+    out = {"metric": METRIC, "value": sig(value), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": sig(1e3 * secs / n), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128 numpy/scipy)",
+           "data": "synthetic (seeded FMO-sized FH chain)",
+           "config": dict(cfg, precision="complex128", tol=args.tol, krylov="adaptive",
+                          parallelism="CPU oracle (numpy/scipy, OpenBLAS threads)"),
+           "impl": "reference",
+           "cpu_baseline": {"kind": "oracle", "cores": thr, "value": sig(value), "unit": UNIT,
+                            "sample": f"steps {args.warmup + 1}..{args.warmup + n} of the trajectory "
+                                      f"({n} of the {args.steps} asked, 150 s budget), {secs:.1f} s"},
+           "e2e": {"value": sig(value), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return out
+
+
+def run_long(args):
+    """Accuracy of the timed arm over a long run: `--long` steps of the timed arm and of the plain
+    FP64 arm from the same product start, Eq. error and max |dP| every 100 steps (no timing)."""
+    import torch
+    import paper_1907_12044_b300 as pkg
+    p, cfg = workload(args)
+    torch.cuda.set_device(0)
+    res = {}
+    for name in ("mixed", "plain"):
+        prec, tol, graph, learned, every = arm_setup(args, name)
+        eng = pkg.Engine(n_realisations=1)
+        eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
+        eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1 if every else 0)
+        eng.build_mpo(0, p)
+        eng.init_mps(0, args.D, p.exciton_site)
+        eng.autotune()
+        pops = [eng.observables(0)[0]]
+        if learned:
+            eng.controller_logging(1 << 20)
+        for _ in range(args.warmup):
+            eng.step(args.dt, 1, precision=PREC[prec], tol=tol)
+            pops.append(eng.observables(0)[0])
+        mode = pkg.KRYLOV_ADAPTIVE
+        if learned:
+            eng.controller_logging(0)
+            train_controller(eng)
+            mode = pkg.KRYLOV_LEARNED
+        if graph:
+            eng.set_option(pkg.OPT_GRAPH, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while len(pops) <= args.long:
+            eng.step(args.dt, 1, precision=PREC[prec], krylov_mode=mode, tol=tol)
+            pops.append(eng.observables(0)[0])
+        res[name] = (np.array(pops), time.perf_counter() - t0, eng.stats())
+        eng.close()
+    P, Pref = res["mixed"][0], res["plain"][0]
+    rows = []
+    for s in list(range(100, args.long + 1, 100)) or [args.long]:
+        e, m = pop_error(args.dt, P[:s + 1], Pref[:s + 1])
+        rows.append({"step": s, "t_fs": s * args.dt, "eq_error": sig(e, 3), "max_abs_dP": sig(m, 3)})
+    return {"long_run": args.long, "config": cfg, "precision": args.precision, "tol": args.tol,
+            "plain_tol": args.plain_tol, "host_seconds": {k: sig(v[1]) for k, v in res.items()},
+            "errors": rows, "final_pops_mixed": [sig(x, 6) for x in P[-1]],
+            "final_pops_fp64": [sig(x, 6) for x in Pref[-1]]}
 
 
 def run_kernel_case(args):
@@ -519,6 +714,14 @@ def run_kernel_case(args):
                       "device_ms_per_call": dev_ms, "launches_per_call": st["kernel_launches"] / args.steps}))
 
 
+def emit(out, args):
+    line = json.dumps(out, ensure_ascii=False)
+    print(line, flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(line + "\n")
+
+
 def main():
     args = parse()
     if args.no_pdl:
@@ -529,41 +732,31 @@ def main():
     if args.kernel_case:
         run_kernel_case(args)
         return
+    if args.long:
+        emit(run_long(args), args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
-        if rank != 0:
-            return
-        p, cfg = workload(args)
-        vals = []
-        for _ in range(args.steps):
-            v, thr, secs = oracle_rate(p, args, 1)
-            vals.append(secs)
-        N = len(p.chain())
-        value = (2 * N - 1) * args.steps / sum(vals)
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": 1e3 * sum(vals) / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
-               "config": dict(cfg, parallelism="CPU oracle (numpy/scipy, OpenBLAS threads)"), "impl": "reference",
-               "cpu_baseline": {"kind": "oracle", "cores": thr, "value": value, "unit": UNIT,
-                                "sample": f"{args.steps} full TDVP-PS step(s) of the bench workload from the product start"},
-               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(out))
+        if rank == 0:
+            emit(run_reference(args, world), args)
         return
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
     out, p = run_ours(args, rank, world)
+    if args.batched > 0:
+        b, pops = run_batched(args, args.batched, rank, world)
+        allp = gather_pops(pops, rank, world)
+        if rank == 0:
+            b["gathered_realisations"] = len(allp)
+            out["batched"] = b
     if rank == 0:
-        if args.batched > 0:
-            out["batched"] = run_batched(args, args.batched)
         if not args.no_e2e:
             out["e2e"] = run_e2e(args, p)
         if not args.no_cpu_baseline and world == 1:
-            v, thr, secs = oracle_rate(p, args, 1)
-            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-                                   "sample": f"one full TDVP-PS step of the bench workload from the product start ({secs:.1f} s)"}
-        print(json.dumps(out))
+            out["cpu_baseline"] = cpu_baseline(p, args)
+        emit(out, args)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

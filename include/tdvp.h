@@ -171,6 +171,21 @@ int tdvp_debug_expm(tdvp_ctx* ctx, int r, int i, double z_re, double z_im, doubl
 #define TDVP_CAT_TC      6   /* tcgen05 complex GEMMs of the mixed-precision matvecs */
 #define TDVP_NCAT        7
 
+/* Sub-steps of a TDVP-PS step under the paper's own time-cost labels (Sec. III.B, Fig. of the
+ * time cost per sub-step), for the per-launch timing: every launch of a step is booked under
+ * the sub-step it serves. */
+#define TDVP_PH_DERIV_FWD 0   /* "Deriv-Forward": H_eff.C matvecs of the forward site exponentials
+                                 (Eq. tdvp2_C, Eq. tdvp1_H) and their operand packing */
+#define TDVP_PH_DERIV_BWD 1   /* "Deriv-Backward": H0.D matvecs of the backward bond exponentials
+                                 (Eq. tdvp2_D) and their operand packing */
+#define TDVP_PH_KRYLOV    2   /* "Krylov": Lanczos vectors, tridiagonal exponential, combination */
+#define TDVP_PH_QR        3   /* "QR": gauge-shift QR / LQ (Eq. QR) */
+#define TDVP_PH_MATMUL_QR 4   /* "MatMul-QR": absorption of the bond factor into the neighbour,
+                                 C_{i+1} = D_i R_{i+1} */
+#define TDVP_PH_GET_ENV   5   /* "Get Env": environment updates (Eq. tdvp1_h1i, tdvp1_hiN) */
+#define TDVP_PH_OTHER     6   /* observables and set-up */
+#define TDVP_NPHASE       7
+
 typedef struct {
   long long steps;             /* completed time steps (per realisation) */
   long long site_updates;      /* forward site evolutions, all realisations (2N-1 per step each) */
@@ -193,6 +208,9 @@ typedef struct {
   long long prof_launches[TDVP_NCAT];
   double prof_flops[TDVP_NCAT];
   double prof_bytes[TDVP_NCAT];
+  /* the same per-launch times booked by sub-step (TDVP_PH_*) */
+  double prof_phase_ms[TDVP_NPHASE];
+  long long prof_phase_launches[TDVP_NPHASE];
 } tdvp_stats_t;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0).  While on, every kernel launch is

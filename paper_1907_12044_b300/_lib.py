@@ -48,6 +48,9 @@ class FHParamsC(C.Structure):
 
 NCAT = 7
 CATEGORIES = ["gemm", "wapply", "lanczos_vec", "tridiag", "qr", "other", "tc_gemm"]
+# the paper's sub-step labels of the time cost of a step (Sec. III.B), in TDVP_PH_* order
+NPHASE = 7
+PHASES = ["Deriv-Forward", "Deriv-Backward", "Krylov", "QR", "MatMul-QR", "Get Env", "other"]
 OPT_RANK_RTOL = 1
 OPT_KRYLOV_CHECK_ALL = 2
 OPT_QR_KERNEL = 3
@@ -62,7 +65,8 @@ class StatsC(C.Structure):
                 ("kernel_launches", C.c_longlong), ("not_converged", C.c_longlong),
                 ("tri_evals", C.c_longlong),
                 ("prof_ms", C.c_double * NCAT), ("prof_launches", C.c_longlong * NCAT),
-                ("prof_flops", C.c_double * NCAT), ("prof_bytes", C.c_double * NCAT)]
+                ("prof_flops", C.c_double * NCAT), ("prof_bytes", C.c_double * NCAT),
+                ("prof_phase_ms", C.c_double * NPHASE), ("prof_phase_launches", C.c_longlong * NPHASE)]
 
 
 def library_path():
@@ -267,7 +271,12 @@ class Engine:
         out = {}
         for k, _ in StatsC._fields_:
             v = getattr(s, k)
-            out[k] = {c: v[i] for i, c in enumerate(CATEGORIES)} if k.startswith("prof_") else v
+            if k.startswith("prof_phase"):
+                out[k] = {c: v[i] for i, c in enumerate(PHASES)}
+            elif k.startswith("prof_"):
+                out[k] = {c: v[i] for i, c in enumerate(CATEGORIES)}
+            else:
+                out[k] = v
         return out
 
     # -- learned Krylov controller ------------------------------------------------------------

@@ -90,6 +90,8 @@ struct tdvp_ctx {
   int graph_nc = 0;                    // a replayed solve stopped at kmax above the tolerance
   std::vector<cudaEvent_t> ev;   // pairs
   std::vector<int> ev_cat;
+  std::vector<int> ev_phase;
+  int phase = TDVP_PH_OTHER;     // sub-step the launches being enqueued serve (TDVP_PH_*)
   size_t ev_used = 0;
   std::string err;
   tdvp_stats_t stats{};
@@ -146,8 +148,10 @@ int prof_begin(tdvp_ctx* ctx, int cat) {
       ctx->ev.push_back(e);
     }
     ctx->ev_cat.resize(ctx->ev.size() / 2);
+    ctx->ev_phase.resize(ctx->ev.size() / 2);
   }
   ctx->ev_cat[ctx->ev_used / 2] = cat;
+  ctx->ev_phase[ctx->ev_used / 2] = ctx->phase;
   CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->st));
   return TDVP_OK;
 }
@@ -168,10 +172,22 @@ int prof_collect(tdvp_ctx* ctx) {
     const int cat = ctx->ev_cat[q / 2];
     ctx->stats.prof_ms[cat] += ms;
     ctx->stats.prof_launches[cat]++;
+    const int ph = ctx->ev_phase[q / 2];
+    ctx->stats.prof_phase_ms[ph] += ms;
+    ctx->stats.prof_phase_launches[ph]++;
   }
   ctx->ev_used = 0;
   return TDVP_OK;
 }
+
+// Books the launches enqueued while it lives under one sub-step (TDVP_PH_*), then restores the
+// previous one.
+struct PhaseScope {
+  tdvp_ctx* ctx;
+  int saved;
+  PhaseScope(tdvp_ctx* c, int ph) : ctx(c), saved(c->phase) { c->phase = ph; }
+  ~PhaseScope() { ctx->phase = saved; }
+};
 
 // ---------------------------------------------------------------------------------------------
 // MPO of Eq. holstein as a finite-state machine (Eq. mpo).  Channel 0 of a cut = nothing placed,
@@ -716,6 +732,7 @@ int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int sp
 
 // clear the per-solve tensor-core operands (their geometry changes from solve to solve)
 int prepare_tc_solve(tdvp_ctx* ctx, const Views& v, int kind, int site, int split) {
+  PhaseScope ps(ctx, kind == 0 ? TDVP_PH_DERIV_FWD : TDVP_PH_DERIV_BWD);
   int rc;
   if (kind == 0) {
     if ((rc = ensure_env_packs(ctx, v, site, site, split))) return rc;
@@ -769,6 +786,7 @@ int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int split);
 // Left environment of site i+1 from site i (Eq. tdvp1_h1i); FP64, or TF32 / TF32x3 on the
 // tensor cores in the mixed-precision sweep.
 int env_left(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
+  PhaseScope ps(ctx, TDVP_PH_GET_ENV);
   if (P != TDVP_PREC_FP64) return env_left_tc(ctx, v, i, P == TDVP_PREC_TF32X3 ? 1 : 0);
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
@@ -781,6 +799,7 @@ int env_left(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
 
 // Right environment of site i-1 from site i (Eq. tdvp1_hiN); FP64 or on the tensor cores.
 int env_right(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
+  PhaseScope ps(ctx, TDVP_PH_GET_ENV);
   if (P != TDVP_PREC_FP64) return env_right_tc(ctx, v, i, P == TDVP_PREC_TF32X3 ? 1 : 0);
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
@@ -846,6 +865,7 @@ int run_qr_timed(tdvp_ctx* ctx, int cat, const Views& v, int dir, int i, int m, 
 
 // dir 0: C_i = L_i D (left-to-right), dir 1: C_i = D R_i (right-to-left); D lands in `bond`
 int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
+  PhaseScope ps(ctx, TDVP_PH_QR);
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i];
   const int mm = dir == 0 ? m.Dl * d : d * m.Dr, nn = dir == 0 ? m.Dr : m.Dl;
@@ -873,6 +893,7 @@ int nblk_for(long long n) {
 // `dst` (1 = site tensor, 2 = bond, 3 = w).  Returns TDVP_OK or an error; sets *notconv.
 // The matvec of one Lanczos iteration (site or bond, FP64 or tensor cores).
 int lanczos_matvec(tdvp_ctx* ctx, const Views& v, int kind, int site, int prec, int split) {
+  PhaseScope ps(ctx, kind == 0 ? TDVP_PH_DERIV_FWD : TDVP_PH_DERIV_BWD);
   if (prec != TDVP_PREC_FP64) {
     if (kind == 0) return matvec_site_tc(ctx, v, site, split);
     return matvec_bond_tc(ctx, v, site, split);
@@ -953,6 +974,7 @@ int expm_graph(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int d
 
 int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
          int* notconv, int prec = TDVP_PREC_FP64) {
+  PhaseScope ps(ctx, TDVP_PH_KRYLOV);
   if (ctx->capturing) return expm_graph(ctx, v, kind, site, src, dst, theta, tol, prec);
   const Dims m = maxdims(ctx, site, v);
   const long long n = kind == 0 ? (long long)m.Dl * ctx->d[site] * m.Dr : (long long)m.Dr * m.Dr;
@@ -979,14 +1001,7 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
   bool all_done = false;
   while (j < ctx->kmax && !all_done) {
     for (int q = 0; q < batch && j < ctx->kmax; ++q, ++j) {
-      if (prec != TDVP_PREC_FP64) {
-        if (kind == 0) { if ((rc = matvec_site_tc(ctx, v, site, split))) return rc; }
-        else if ((rc = matvec_bond_tc(ctx, v, site, split))) return rc;
-      } else if (kind == 0) {
-        if ((rc = matvec_site(ctx, v, site, OP_MV1))) return rc;
-      } else if ((rc = matvec_bond(ctx, v, site))) {
-        return rc;
-      }
+      if ((rc = lanczos_matvec(ctx, v, kind, site, prec, split))) return rc;
       LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));      // three kernels (tridiagonal step inside)
       LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_post(a, j, ctx->st));     // next vector
       ctx->stats.kernel_launches += 2;
@@ -1165,6 +1180,7 @@ int enqueue_step(tdvp_ctx* ctx, const Views& v, double tau, double tol, int P, i
     if ((rc = env_left(ctx, v, i, P))) return rc;
     if ((rc = expm(ctx, v, 1, i, 2, 2, 0.5 * tau, tol, nc, P))) return rc;
     const Dims m = maxdims(ctx, i + 1, v);
+    PhaseScope ps(ctx, TDVP_PH_MATMUL_QR);
     if ((rc = g_op(ctx, v, OP_ABS_L, i, m.Dl, ctx->d[i + 1] * m.Dr, 1))) return rc;
   }
   if ((rc = expm(ctx, v, 0, N - 1, 0, 1, -tau, tol, nc, P))) return rc;
@@ -1173,7 +1189,10 @@ int enqueue_step(tdvp_ctx* ctx, const Views& v, double tau, double tol, int P, i
     if ((rc = env_right(ctx, v, i, P))) return rc;
     if ((rc = expm(ctx, v, 1, i - 1, 2, 2, 0.5 * tau, tol, nc, P))) return rc;
     const Dims m = maxdims(ctx, i - 1, v);
-    if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
+    {
+      PhaseScope ps(ctx, TDVP_PH_MATMUL_QR);
+      if ((rc = g_op(ctx, v, OP_ABS_R, i, m.Dl * ctx->d[i - 1], m.Dr, 1))) return rc;
+    }
     if ((rc = expm(ctx, v, 0, i - 1, 0, 1, -0.5 * tau, tol, nc, P))) return rc;
   }
   return TDVP_OK;
@@ -1452,6 +1471,7 @@ int tdvp_move_center(tdvp_ctx* ctx, int r, int site) {
     if ((rc = gauge_qr(ctx, v, i, 0))) return rc;
     if ((rc = env_left(ctx, v, i))) return rc;
     const Dims m = maxdims(ctx, i + 1, v);
+    PhaseScope ps(ctx, TDVP_PH_MATMUL_QR);
     if ((rc = g_op(ctx, v, OP_ABS_L, i, m.Dl, ctx->d[i + 1] * m.Dr, 1))) return rc;
     LAUNCH(launch_copy_vec(1, i + 1, v.sd, v.wk, 1, ctx->N, m.Dl * ctx->d[i + 1] * m.Dr, ctx->st));
   }

@@ -3,7 +3,9 @@
 Under torchrun every rank advances its own trajectory (replicas: a single TDVP-PS trajectory is
 sequential along the chain, Eq. ps_trotter) and there is no data-path collective; the only
 exchange is the all-reduce MAX of the timed region, so that the whole-job rate is taken over
-the slowest rank.  The reference arm runs on rank 0 only; the other ranks exit without work.
+the slowest rank.  Disorder realisations are independent: each rank takes the realisations
+r = rank mod N, and rank 0 gathers the final populations over a host (gloo) group after the
+timed region.  The reference arm runs on rank 0 only; the other ranks exit without work.
 """
 import os
 import socket
@@ -35,6 +37,54 @@ def _worker(rank, world, port, q):
         dist.barrier()
     finally:
         dist.destroy_process_group()
+
+
+def _batched_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    for d in (ROOT, os.path.join(ROOT, "tests")):
+        if d not in sys.path:
+            sys.path.insert(0, d)
+    import types
+    import torch
+    import torch.distributed as dist
+    import bench
+    import paper_1907_12044_b300 as pkg
+    from test_bench_host import FakeEngine, FakeEvent
+    pkg.Engine = FakeEngine
+    torch.cuda.synchronize = lambda *a: None
+    torch.cuda.current_stream = lambda *a: types.SimpleNamespace(cuda_stream=0)
+    torch.cuda.Event = FakeEvent
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        args = bench.parse(["--steps", "1", "--warmup", "2"])
+        b, pops = bench.run_batched(args, 5, rank, world)
+        allp = bench.gather_pops(pops, rank, world)
+        q.put((rank, sorted(pops), None if allp is None else sorted(allp), b["per_rank"], b["value"]))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_realisations_and_gather_populations():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batched_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = sorted(q.get(timeout=180) for _ in range(2))
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert [p.exitcode for p in procs] == [0, 0]
+    assert res[0][1] == [0, 2, 4] and res[1][1] == [1, 3]       # r on rank r mod 2
+    assert res[0][2] == [0, 1, 2, 3, 4] and res[1][2] is None   # every realisation gathered on rank 0
+    assert (res[0][3], res[1][3]) == (3, 2)
+    assert res[0][4] == res[1][4] > 0                           # whole-job rate over the slowest rank
 
 
 def test_two_gloo_ranks_report_the_slowest_rank():
