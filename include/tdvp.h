@@ -66,12 +66,22 @@ typedef struct {
 #define TDVP_ERR_NAN                  -6  /* a non-finite norm was met */
 #define TDVP_ERR_STATE                -7  /* call out of order (e.g. step before init) */
 
-/* Arithmetic of the Lanczos matvecs H_eff.A (Eq. tdvp2_C) and H0.D (Eq. tdvp2_D).  The
- * environments, the Lanczos orthogonalisation, the tridiagonal exponential and the gauge-shift
- * QR are FP64 in every mode. */
-#define TDVP_PREC_FP64   0   /* complex double on the FP64 pipe */
-#define TDVP_PREC_TF32   1   /* tcgen05 kind::tf32, 4 real products per complex product, FP32 accumulation */
-#define TDVP_PREC_TF32X3 2   /* as TF32 with hi/lo split operands, hi*hi + hi*lo + lo*hi (FP32-level products) */
+/* Arithmetic of the contractions of a step: the Lanczos matvecs H_eff.A (Eq. tdvp2_C) and H0.D
+ * (Eq. tdvp2_D) and, in the mixed precisions, the environment updates (Eq. tdvp1_h1i,
+ * tdvp1_hiN).  The Lanczos orthogonalisation, the tridiagonal exponential, the gauge-shift QR and
+ * the absorption are FP64 in every mode.  Every mixed mode accumulates in FP32 on the tcgen05
+ * tensor cores.  "4M": a complex product as 4 real products (re re - im im, re im + im re);
+ * "3M" (Gauss): as 3 real products re re, im im, (re + im)(re + im), combined in FP32; "x3": each
+ * operand split into a rounded high part and the rounded remainder, the terms hi hi + hi lo +
+ * lo hi of the 4M form accumulated (compensated products). */
+#define TDVP_PREC_FP64    0   /* complex double on the FP64 pipe */
+#define TDVP_PREC_TF32    1   /* kind::tf32, TF32 operands (11 significant bits), 4M */
+#define TDVP_PREC_TF32X3  2   /* TF32 hi/lo split, 4M, x3 (~FP32-level products) */
+#define TDVP_PREC_BF16    3   /* kind::f16, BF16 operands (8 significant bits), 4M */
+#define TDVP_PREC_BF16X3  4   /* BF16 hi/lo split, 4M, x3 (~16 significant bits) */
+#define TDVP_PREC_TF32_3M 5   /* TF32 operands, 3M */
+#define TDVP_PREC_BF16_3M 6   /* BF16 operands, 3M */
+#define TDVP_PREC_LAST    6
 
 /* Krylov dimension control. */
 #define TDVP_KRYLOV_ADAPTIVE 0   /* grow k until the a-posteriori estimate meets the tolerance */
@@ -297,12 +307,23 @@ int tdvp_autotune(tdvp_ctx* ctx);
  *     by launch, one host flag read per exponential.
  *   TDVP_OPT_PDL: 1 (default) = kernels of the step are launched as programmatic dependents of
  *     their predecessor (they start while it finishes and wait for it before touching memory);
- *     0 = plain stream order.  Process-wide: it applies to every context. */
+ *     0 = plain stream order.  Process-wide: it applies to every context.
+ *   TDVP_OPT_FUSED_LANCZOS: 1 (default) = each Lanczos iteration after the matvec (dots, both
+ *     Gram-Schmidt passes, tridiagonal step, next vector) is one cooperative launch whose phases
+ *     are separated by bounded group barriers, whenever the vector chunks of every realisation fit
+ *     co-resident on the GPU; 0 = four launches per iteration.  Both give bit-identical results.
+ *   TDVP_OPT_STALL_TEST: for testing the failure path only.  A value t in (0, 1] (seconds) makes
+ *     the first group barrier of every fused Lanczos iteration wait for one block more than the
+ *     launch has (a participant that never arrives) and limits every wait of that kernel to t, so
+ *     the waits run out and the step returns TDVP_ERR_DEVICE_TIMEOUT (nothing faults or hangs; the
+ *     context stays usable, the state must be initialised again).  0 (default) = off. */
 #define TDVP_OPT_RANK_RTOL         1
 #define TDVP_OPT_KRYLOV_CHECK_ALL  2
 #define TDVP_OPT_QR_KERNEL         3
 #define TDVP_OPT_GRAPH             4
 #define TDVP_OPT_PDL               5
+#define TDVP_OPT_FUSED_LANCZOS     6
+#define TDVP_OPT_STALL_TEST        7
 int tdvp_set_option(tdvp_ctx* ctx, int option, double value);
 
 const char* tdvp_last_error(const tdvp_ctx* ctx);

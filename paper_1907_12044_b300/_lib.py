@@ -11,6 +11,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PREC_FP64 = 0
 PREC_TF32 = 1
 PREC_TF32X3 = 2
+PREC_BF16 = 3
+PREC_BF16X3 = 4
+PREC_TF32_3M = 5
+PREC_BF16_3M = 6
+MIXED_PRECISIONS = (PREC_TF32, PREC_TF32X3, PREC_BF16, PREC_BF16X3, PREC_TF32_3M, PREC_BF16_3M)
 KRYLOV_ADAPTIVE = 0
 KRYLOV_LEARNED = 1
 MLP_NPARAM = 4801
@@ -56,6 +61,8 @@ OPT_KRYLOV_CHECK_ALL = 2
 OPT_QR_KERNEL = 3
 OPT_GRAPH = 4
 OPT_PDL = 5
+OPT_FUSED_LANCZOS = 6
+OPT_STALL_TEST = 7
 
 
 class StatsC(C.Structure):

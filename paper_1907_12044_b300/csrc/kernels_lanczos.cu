@@ -14,6 +14,7 @@
 // the host may enqueue more iterations than needed.  Reductions are two-level with a fixed
 // order, so results are bit-reproducible run to run.
 #include "tdvp_internal.cuh"
+#include "tc_pack.cuh"
 #include <cmath>
 
 namespace {
@@ -45,11 +46,13 @@ __device__ __forceinline__ long long vec_len(const SiteDev* sdr, int site, int k
   return kind == 0 ? (long long)s.Dl * s.d * s.Dr : (long long)s.Dr * s.Dr;
 }
 
-__device__ __forceinline__ VecGeom geom(long long n, int b) {
+// chunking of a vector of n elements: ceil(n / 32) chunks, at most `cap` (<= 148); every kernel of
+// one solve uses the same cap, so a block owns the same elements and partial-sum slots throughout
+__device__ __forceinline__ VecGeom geom(long long n, int b, int cap) {
   VecGeom g;
   g.n = n;
   long long nb = (n + TDVP_VEC_CHUNK - 1) / TDVP_VEC_CHUNK;
-  if (nb > TDVP_MAX_VEC_BLOCKS) nb = TDVP_MAX_VEC_BLOCKS;
+  if (nb > cap) nb = cap;
   if (nb < 1) nb = 1;
   g.nblk = (int)nb;
   const long long ch = (n + nb - 1) / nb;
@@ -89,7 +92,7 @@ __device__ void reduce_partials(const WorkDev& W, int tab, int nblk, int j, zc* 
   const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
   for (int t = wid; t <= j; t += NT / 32) {
     zc s = zmake(0, 0);
-    for (int b = lane; b < nblk; b += 32) s = zadd(s, *P(W, tab, b, t));
+    for (int b = lane; b < nblk; b += 32) s = zadd(s, __ldcg(P(W, tab, b, t)));
     for (int o = 16; o > 0; o >>= 1) {
       s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
       s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
@@ -156,13 +159,24 @@ __device__ void chunk_dots(const WorkDev& W, const VecGeom& g, int j, int tab, i
   }
 }
 
+// Element e of the Krylov vector of (site, kind) as the packed B operand of the next tensor-core
+// matvec: site vectors x[a][(s b)] give row (s b), k = a; bond vectors D[l][r] give row r, k = l.
+__device__ __forceinline__ void pack_krylov(const LzArgs& a, const SiteDev* sdr, const WorkDev& W, long long e,
+                                            zc v) {
+  const SiteDev& s = sdr[a.site];
+  const int Nn = a.kind == 0 ? s.d * s.Dr : s.Dr;
+  const int Kd = a.kind == 0 ? s.Dl : s.Dr;
+  const int k = (int)(e / Nn), n = (int)(e % Nn);
+  tcpack::pk_store(W.tc_x, tcpack::BN, (Kd + tcpack::BK - 1) / tcpack::BK, n, k, v.x, v.y, a.pack_pm);
+}
+
 __global__ void __launch_bounds__(NT) lz_start1(LzArgs a) {
   pdl_enter();
   __shared__ double red[2 * 8 * NT / 32];
   const int r = blockIdx.y, b = blockIdx.x;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const WorkDev& W = a.wk[r];
-  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
   if (b >= g.nblk) return;
   const zc* src = src_ptr(W, sdr, a.site, a.src);
   zc acc = zmake(0, 0);
@@ -177,7 +191,7 @@ __global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
   const int r = blockIdx.y, b = blockIdx.x;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const WorkDev& W = a.wk[r];
-  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
   if (b >= g.nblk) return;
   reduce_partials(W, 2, g.nblk, 0, h);
   const double nrm = sqrt(h[0].x);
@@ -187,8 +201,11 @@ __global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
     const zc v = zscale(src[e], inv);
     W.V[e] = v;
     W.x[e] = v;
+    if (a.pack_pm >= 0) pack_krylov(a, sdr, W, e, v);
   }
   if (b == 0 && threadIdx.x == 0) {
+    W.lzc[0] = 0u;          // last-block counter and barrier word of the fused iteration kernel
+    W.lzc[1] = 0u;
     KState* ks = W.ks;
     ks->nrm = nrm;
     ks->k = 0;
@@ -218,7 +235,7 @@ __global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
   if (W.ks->done) return;
   if (a.devj) j = W.ks->jcur;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
-  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
   if (b >= g.nblk) return;
   chunk_dots(W, g, j, 0, b, red);
 }
@@ -237,7 +254,7 @@ __global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
   if (W.ks->done) return;
   if (a.devj) j = W.ks->jcur;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
-  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
   if (b >= g.nblk) return;
   reduce_partials(W, pass == 1 ? 0 : 1, g.nblk, j, h);
   double nn = 0;
@@ -546,7 +563,7 @@ __device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, doubl
   const WorkDev& W = a.wk[r];
   KState* ks = W.ks;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
-  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), 0);
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), 0, a.bcap);
   if (threadIdx.x < 32) {
     double s = 0;
     for (int b = threadIdx.x; b < g.nblk; b += 32) s += __ldcg(&P(W, 2, b, 0)->x);
@@ -647,7 +664,7 @@ __global__ void __launch_bounds__(NT) lz_next(LzArgs a, int j) {
   if (W.ks->done) return;
   if (a.devj) j = W.ks->jcur;
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
-  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
   if (b >= g.nblk) return;
   const double ib = W.ks->inv_beta;
   zc* Vn = W.V + (j + 1) * W.ldV;
@@ -655,6 +672,119 @@ __global__ void __launch_bounds__(NT) lz_next(LzArgs a, int j) {
     const zc v = zscale(W.w[e], ib);
     Vn[e] = v;
     W.x[e] = v;
+    if (a.pack_pm >= 0) pack_krylov(a, sdr, W, e, v);
+  }
+}
+
+__device__ __forceinline__ unsigned long long lz_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded barrier over the nblocks blocks of one realisation on the word W.lzc[1], whose low 31
+// bits are zero between barriers: block 0 adds 2^31 - (nblocks - 1), every other block 1, so the
+// top bit flips exactly when the last block arrives; a block waits until the top bit differs from
+// the value it read at its arrival.  Gives up after wait_ns of wall-clock time (1 s unless a test
+// shortens it; error word -5, TDVP_ERR_DEVICE_TIMEOUT) or when another block has given up; returns
+// false then.
+__device__ bool lz_group_sync(const WorkDev& W, int nblocks, int b, unsigned long long wait_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* err = W.err;
+    int good = (*err == 0);
+    if (good && nblocks > 1) {
+      const unsigned inc = (b == 0) ? (0x80000000u - (unsigned)(nblocks - 1)) : 1u;
+      volatile unsigned* word = W.lzc + 1;
+      __threadfence();
+      const unsigned old = atomicAdd(W.lzc + 1, inc);
+      const unsigned long long t0 = lz_gtimer();
+      while (((old ^ *word) & 0x80000000u) == 0u) {
+        if (*err != 0) { good = 0; break; }
+        if (lz_gtimer() - t0 > wait_ns) { atomicExch(W.err, -5); good = 0; break; }
+      }
+      __threadfence();
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// One Lanczos iteration j in one launch (the grid is cooperative, so the blocks of a realisation
+// are co-resident and can wait for each other):
+//   1. partial dots p_t = <V_t, w>, t <= j                                   | group barrier
+//   2. h1 = sum p; w -= V h1; alpha_j = Re h1_j; partial dots of the second pass | group barrier
+//   3. h2 = sum; w -= V h2; alpha_j += Re h2_j; |w|^2 partials; the block that finishes last
+//      takes the tridiagonal step (beta_j, exp(i theta T) e_1, convergence)  | group barrier
+//   4. unless the solve is done: V_{j+1} = x = w / beta_j (and its packed tensor-core operand)
+// The arithmetic and its order are those of lz_dots, lz_upd (both passes) and lz_next.
+__global__ void __launch_bounds__(NT) lz_iter(LzArgs a, int j) {
+  __shared__ double red[2 * 8 * NT / 32];
+  __shared__ zc h[TDVP_KMAX_HARD];
+  __shared__ int last;
+  __shared__ double sh[TRI_SH];
+  __shared__ zc c[TRI_THREADS];
+  __shared__ double al[TDVP_KMAX_HARD], be[TDVP_KMAX_HARD], betaj_s;
+  pdl_wait();
+  const int r = blockIdx.y, b = blockIdx.x;
+  const WorkDev& W = a.wk[r];
+  if (W.ks->done) return;
+  if (a.devj) j = W.ks->jcur;
+  const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
+  if (b >= g.nblk) return;
+  chunk_dots(W, g, j, 0, b, red);
+  // failure-path test: the first barrier counts one block more than the launch has, a participant
+  // that never arrives, so every block's bounded wait runs out
+  if (!lz_group_sync(W, a.stall ? g.nblk + 1 : g.nblk, b, a.wait_ns)) return;
+  // first Gram-Schmidt pass
+  reduce_partials(W, 0, g.nblk, j, h);
+  for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) {
+    zc we = W.w[e];
+    for (int t = 0; t <= j; ++t) we = zfms(h[t], W.V[t * W.ldV + e], we);
+    W.w[e] = we;
+  }
+  __syncthreads();
+  chunk_dots(W, g, j, 1, b, red);
+  if (b == 0 && threadIdx.x == 0) W.ks->alpha[j] = h[j].x;
+  if (!lz_group_sync(W, g.nblk, b, a.wait_ns)) return;
+  // second pass and the norm partials
+  reduce_partials(W, 1, g.nblk, j, h);
+  double nn = 0;
+  for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) {
+    zc we = W.w[e];
+    for (int t = 0; t <= j; ++t) we = zfms(h[t], W.V[t * W.ldV + e], we);
+    W.w[e] = we;
+    nn += zabs2(we);
+  }
+  const zc s = block_zsum(zmake(nn, 0), red);
+  if (threadIdx.x == 0) *P(W, 2, b, 0) = s;
+  if (b == 0 && threadIdx.x == 0) W.ks->alpha[j] += h[j].x;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned old = atomicAdd(W.lzc, 1u);
+    last = old == (unsigned)(g.nblk - 1);
+    if (last) W.lzc[0] = 0u;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    tri_step(a, r, j, sh, c, al, be, &betaj_s);
+  }
+  if (!lz_group_sync(W, g.nblk, b, a.wait_ns)) return;
+  // next Krylov vector (values of the tridiagonal step read through L2)
+  KState* ks = W.ks;
+  if (__ldcg(&ks->done)) return;
+  const double ib = __ldcg(&ks->inv_beta);
+  zc* Vn = W.V + (j + 1) * W.ldV;
+  for (long long e = g.c0 + threadIdx.x; e < g.c1; e += NT) {
+    const zc v = zscale(W.w[e], ib);
+    Vn[e] = v;
+    W.x[e] = v;
+    if (a.pack_pm >= 0) pack_krylov(a, sdr, W, e, v);
   }
 }
 
@@ -664,7 +794,7 @@ __global__ void __launch_bounds__(NT) lz_combine(LzArgs a) {
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
-  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b);
+  const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
   if (b >= g.nblk) return;
   const int k = W.ks->k;
   for (int t = threadIdx.x; t < k; t += NT) cf[t] = W.ks->coef[t];
@@ -690,7 +820,7 @@ __global__ void lz_loop_ctl(LzArgs a, int which) {
         // cannot happen while the tridiagonal kernel stops every solve at its cap; it bounds the
         // device loop even so
         ks->done = 1;
-        atomicExch(a.wk[r].err, -7);
+        atomicCAS(a.wk[r].err, 0, -7);    // an earlier error (e.g. a timed-out wait) stays reported
       } else {
         active = 1;
       }
@@ -729,6 +859,30 @@ cudaError_t launch_lz_iter_post(const LzArgs& a, int j, cudaStream_t st) {
   dim3 grid(a.nblk, a.R);
   { const cudaError_t e_ = launch_pdl(lz_next, grid, NT, 0, st, a, j); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
+}
+
+cudaError_t launch_lz_iter(const LzArgs& a, int j, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.gridDim = dim3(a.nblk, a.R);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, lz_iter, a, j);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// co-resident blocks of lz_iter on the whole device (0 if the query fails)
+int lz_iter_capacity(int device) {
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lz_iter, NT, 0) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  return per_sm * sms;
 }
 
 cudaError_t launch_lz_combine(const LzArgs& a, cudaStream_t st) {

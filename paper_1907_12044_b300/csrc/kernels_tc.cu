@@ -1,17 +1,21 @@
 // Mixed-precision contractions of the Lanczos matvecs on the 5th-generation tensor cores.
 //
 // H[i] C (Eq. tdvp2_C) and the zero-site H0 D (Eq. tdvp2_D) are complex GEMMs.  Each runs as real
-// TF32 products on tcgen05 with FP32 accumulation in tensor memory:
-//   Dr += Ar Br - Ai Bi,   Di += Ai Br + Ar Bi        (4 real products, the A-negate bit gives -Ai)
-// and, in the compensated mode, every operand is split a = a_hi + a_lo (a_hi = TF32 rounding of a)
-// and the three terms hi*hi + hi*lo + lo*hi are accumulated (FP32-level products).
+// products on tcgen05 (kind::tf32 with TF32 operands, or kind::f16 with BF16 operands) with FP32
+// accumulation in tensor memory.  A precision mode word selects the form (TC_PM_* bits):
+//   4M:    Dr += Ar Br - Ai Bi,   Di += Ai Br + Ar Bi      (4 real products; A-negate gives -Ai)
+//   3M:    P1 += Ar Br,  P2 += Ai Bi,  P3 += (Ar + Ai)(Br + Bi),  Dr = P1 - P2,  Di = P3 - P1 - P2
+//          (Gauss: 3 real products; the sum planes are formed in FP64 and rounded once)
+//   split: every operand a = a_hi + a_lo (a_hi = a rounded to the operand format) and the terms
+//          hi*hi + hi*lo + lo*hi of the 4M form are accumulated (compensated products)
 //
 // Operands are produced by the pack kernels below directly in the tensor-core tile layout: a
 // matrix with R rows (R = 128 for the A operand, 64 for B) and K columns is cut into R x 32 tiles,
 // each stored contiguously in K-major "no swizzle" core-matrix order (8 rows x 16 bytes per core
-// matrix; core matrices adjacent in K are 128 bytes apart, 8-row groups 1024 bytes apart), planes
-// re_hi, im_hi, re_lo, im_lo one after another.  Padding rows/columns are zero.  A whole tile is
-// therefore one contiguous block that a 1-D bulk TMA copy moves into shared memory.
+// matrix; core matrices adjacent in K are 128 bytes apart, 8-row groups 1024 bytes apart for TF32
+// and 512 for BF16), planes re_hi, im_hi, re_lo, im_lo (3M: re, im, re + im) one after another in
+// slots of the TF32 tile size.  Padding rows/columns are zero.  A whole tile is therefore one
+// contiguous block that a 1-D bulk TMA copy moves into shared memory.
 //
 // GEMM kernel: 160 threads per CTA and S CTAs per 128 x 64 output tile, each over its own range
 // of K tiles (split-K; S = 1 when the output alone fills the GPU).  One thread of warp 4 issues
@@ -27,14 +31,22 @@
 // Every wait is bounded: on timeout the CTA records an error, drains its copies and MMAs with
 // bounded waits, still takes part in the cluster barriers, frees its tensor memory and returns.
 #include "tdvp_internal.cuh"
+#include "tc_pack.cuh"
 #include <cstdint>
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 32;
+using tcpack::BM;
+using tcpack::BN;
+using tcpack::BK;
+using tcpack::NPL;
+using tcpack::pm_split;
+using tcpack::pm_bf16;
+using tcpack::pm_gauss;
+using tcpack::pm_planes;
+using tcpack::pk_store;
 constexpr int A_TILE = BM * BK * 4;     // 16 KB per plane
 constexpr int B_TILE = BN * BK * 4;     //  8 KB per plane
-constexpr int NPL = 4;                  // planes: re_hi, im_hi, re_lo, im_lo
 constexpr int STAGE_BYTES = NPL * (A_TILE + B_TILE);   // 96 KB
 constexpr int STAGES = 2;
 constexpr int TC_EPI = 128;             // warps 0-3: accumulator drains and epilogue (one TMEM lane each)
@@ -112,6 +124,19 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// one real product of the selected operand format
+__device__ __forceinline__ void mma_fmt(bool bf16, uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (bf16) mma_bf16(d, a, b, idesc, acc);
+  else mma_tf32(d, a, b, idesc, acc);
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
@@ -148,43 +173,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // shared-memory matrix descriptor: K-major, no swizzle, LBO = 128 B (next core matrix in K),
-// SBO = 1024 B (next 8-row group); bits 46-48 = 0b001.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+// SBO = next 8-row group (1024 B for a 32-column TF32 tile, 512 B for BF16); bits 46-48 = 0b001.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo = 1024) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((128 >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
-// instruction descriptor: kind::tf32, D = F32, A = B = TF32, K-major, M = 128, N = 64
+// instruction descriptor, D = F32, K-major, M = 128, N = 64: kind::tf32 with A = B = TF32 (format
+// 2), or kind::f16 with A = B = BF16 (format 1)
 __device__ __forceinline__ uint32_t idesc_tf32(bool negA) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(BN >> 3) << 17) |
          ((uint32_t)(BM >> 4) << 24);
 }
-
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// byte offset of element (row, k) in a packed operand with RT-row tiles and nkt K-tiles
-__device__ __forceinline__ long long pk_off(int RT, int nkt, int row, int k, int plane) {
-  const int rt = row / RT, r = row % RT, kt = k / BK, kk = k % BK;
-  const long long tile = ((long long)(rt * nkt + kt) * NPL + plane) * (RT * BK * 4);
-  return tile + (r / 8) * 1024 + (kk / 4) * 128 + (r % 8) * 16 + (kk % 4) * 4;
-}
-
-// store a complex value into the packed planes (hi/lo split when split != 0)
-__device__ __forceinline__ void pk_store(char* base, int RT, int nkt, int row, int k, double re, double im, int split) {
-  const float rh = tf32_round((float)re), ih = tf32_round((float)im);
-  *reinterpret_cast<float*>(base + pk_off(RT, nkt, row, k, 0)) = rh;
-  *reinterpret_cast<float*>(base + pk_off(RT, nkt, row, k, 1)) = ih;
-  if (split) {
-    *reinterpret_cast<float*>(base + pk_off(RT, nkt, row, k, 2)) = (float)(re - (double)rh);
-    *reinterpret_cast<float*>(base + pk_off(RT, nkt, row, k, 3)) = (float)(im - (double)ih);
-  }
+__device__ __forceinline__ uint32_t idesc_bf16(bool negA) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
 }
 
 __device__ __forceinline__ int cdivd(int a, int b) { return (a + b - 1) / b; }
@@ -261,9 +267,13 @@ constexpr int PART_LD = BN + 1;       // partial tile row stride in floats (conf
 constexpr int MAX_SPLIT = 8;
 static_assert(2 * BM * PART_LD * 4 <= STAGE_BYTES, "partial tile must fit in the first stage");
 
+// PM: precision mode word (TC_PM_* bits), a template parameter so that every mode gets its own
+// register allocation
+template <int PM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk, int N_sites,
-                int split, int S) {
+                int S) {
+  constexpr int pm = PM;
   pdl_enter();
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ TcDesc g;
@@ -304,8 +314,12 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
   const int kt0 = (int)((long long)nkt_all * sidx / S);
   const int nkt = (int)((long long)nkt_all * (sidx + 1) / S) - kt0;
   const int mt = blockIdx.y, nt = blockIdx.x;
-  const int npl = split ? 4 : 2;
-  const uint32_t stage_tx = (uint32_t)npl * (A_TILE + B_TILE);
+  constexpr bool split = pm_split(pm), bf = pm_bf16(pm), gauss = pm_gauss(pm);
+  constexpr int npl = pm_planes(pm);
+  const uint32_t plane_a = bf ? A_TILE / 2 : A_TILE, plane_b = bf ? B_TILE / 2 : B_TILE;
+  const uint32_t stage_tx = (uint32_t)npl * (plane_a + plane_b);
+  // main accumulators: 4M Dr, Di (2 x BN columns); 3M P1, P2, P3 (3 x BN), at b * bstride
+  const uint32_t bstride = gauss ? 3 * BN : 2 * BN;
   // The tensor cores add into an FP32 accumulator with truncation, so a long sum of same-signed
   // terms (the diagonal of an environment, sum_k |A_k|^2 weighted by the MPO) loses about half an
   // ulp per addition, always downward.  The main products of each K tile therefore go into a fresh
@@ -322,13 +336,17 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
         unsigned char* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full_bar[s], stage_tx);
         for (int p = 0; p < npl; ++p) {
-          bulk_load(st + p * A_TILE, g.A + ((long long)(mt * nkt_all + kt0 + kt) * NPL + p) * A_TILE, A_TILE,
+          bulk_load(st + p * A_TILE, g.A + ((long long)(mt * nkt_all + kt0 + kt) * NPL + p) * A_TILE, plane_a,
                     &full_bar[s]);
           bulk_load(st + NPL * A_TILE + p * B_TILE, g.B + ((long long)(nt * nkt_all + kt0 + kt) * NPL + p) * B_TILE,
-                    B_TILE, &full_bar[s]);
+                    plane_b, &full_bar[s]);
         }
       };
-      const uint32_t id_pos = idesc_tf32(false), id_neg = idesc_tf32(true);
+      const uint32_t id_pos = bf ? idesc_bf16(false) : idesc_tf32(false);
+      const uint32_t id_neg = bf ? idesc_bf16(true) : idesc_tf32(true);
+      const uint32_t sbo = bf ? 512u : 1024u;
+      // one instruction covers 32 bytes of K per row (8 TF32 or 16 BF16 = 2 core matrices)
+      constexpr int ksteps = bf ? BK / 16 : BK / 8;
       const uint32_t sr = tmem + ACC_SMALL, si = sr + BN;
       int issued = 0;
       for (; issued < STAGES && issued < nkt; ++issued) issue(issued);
@@ -342,31 +360,39 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
           break;
         }
         tc_after();
-        const uint32_t dr = tmem + (uint32_t)b * (2 * BN), di = dr + BN;
+        const uint32_t dr = tmem + (uint32_t)b * bstride, di = dr + BN, d3 = dr + 2 * BN;
         const uint32_t abase = su32(smem + s * STAGE_BYTES);
         const uint32_t bbase = abase + NPL * A_TILE;
 #pragma unroll
-        for (int ks = 0; ks < BK / 8; ++ks) {
-          const uint32_t ko = ks * 256;   // 8 TF32 = 2 core matrices of 128 B
-          const uint64_t arh = sdesc(abase + 0 * A_TILE + ko), aih = sdesc(abase + 1 * A_TILE + ko);
-          const uint64_t brh = sdesc(bbase + 0 * B_TILE + ko), bih = sdesc(bbase + 1 * B_TILE + ko);
+        for (int ks = 0; ks < ksteps; ++ks) {
+          const uint32_t ko = ks * 256;   // 32 bytes of K per row = 2 core matrices of 128 B
+          const uint64_t arh = sdesc(abase + 0 * A_TILE + ko, sbo), aih = sdesc(abase + 1 * A_TILE + ko, sbo);
+          const uint64_t brh = sdesc(bbase + 0 * B_TILE + ko, sbo), bih = sdesc(bbase + 1 * B_TILE + ko, sbo);
           const uint32_t acc = ks > 0 ? 1u : 0u;
-          mma_tf32(dr, arh, brh, id_pos, acc);
-          mma_tf32(dr, aih, bih, id_neg, 1u);
-          mma_tf32(di, aih, brh, id_pos, acc);
-          mma_tf32(di, arh, bih, id_pos, 1u);
-          if (split) {
+          if constexpr (gauss) {
+            // P1 = Ar Br, P2 = Ai Bi, P3 = (Ar + Ai)(Br + Bi)
+            const uint64_t as = sdesc(abase + 2 * A_TILE + ko, sbo), bs = sdesc(bbase + 2 * B_TILE + ko, sbo);
+            mma_fmt(bf, dr, arh, brh, id_pos, acc);
+            mma_fmt(bf, di, aih, bih, id_pos, acc);
+            mma_fmt(bf, d3, as, bs, id_pos, acc);
+          } else {
+          mma_fmt(bf, dr, arh, brh, id_pos, acc);
+          mma_fmt(bf, dr, aih, bih, id_neg, 1u);
+          mma_fmt(bf, di, aih, brh, id_pos, acc);
+          mma_fmt(bf, di, arh, bih, id_pos, 1u);
+          }
+          if constexpr (split) {
             const uint32_t accs = (kt > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t arl = sdesc(abase + 2 * A_TILE + ko), ail = sdesc(abase + 3 * A_TILE + ko);
-            const uint64_t brl = sdesc(bbase + 2 * B_TILE + ko), bil = sdesc(bbase + 3 * B_TILE + ko);
-            mma_tf32(sr, arh, brl, id_pos, accs);
-            mma_tf32(sr, arl, brh, id_pos, 1u);
-            mma_tf32(sr, aih, bil, id_neg, 1u);
-            mma_tf32(sr, ail, bih, id_neg, 1u);
-            mma_tf32(si, aih, brl, id_pos, accs);
-            mma_tf32(si, ail, brh, id_pos, 1u);
-            mma_tf32(si, arh, bil, id_pos, 1u);
-            mma_tf32(si, arl, bih, id_pos, 1u);
+            const uint64_t arl = sdesc(abase + 2 * A_TILE + ko, sbo), ail = sdesc(abase + 3 * A_TILE + ko, sbo);
+            const uint64_t brl = sdesc(bbase + 2 * B_TILE + ko, sbo), bil = sdesc(bbase + 3 * B_TILE + ko, sbo);
+            mma_fmt(bf, sr, arh, brl, id_pos, accs);
+            mma_fmt(bf, sr, arl, brh, id_pos, 1u);
+            mma_fmt(bf, sr, aih, bil, id_neg, 1u);
+            mma_fmt(bf, sr, ail, bih, id_neg, 1u);
+            mma_fmt(bf, si, aih, brl, id_pos, accs);
+            mma_fmt(bf, si, ail, brh, id_pos, 1u);
+            mma_fmt(bf, si, arh, bil, id_pos, 1u);
+            mma_fmt(bf, si, arl, bih, id_pos, 1u);
           }
         }
         mma_commit(&done_bar[s]);
@@ -400,15 +426,31 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
       const bool got = mbar_wait_or(&acc_full[b], (uint32_t)((kt >> 1) & 1), &abort_flag);
       if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
       tc_after();
+      if constexpr (gauss) {
+        // Dr += P1 - P2, Di += P3 - P1 - P2 (in FP32 registers, round to nearest)
 #pragma unroll
-      for (int cb = 0; cb < BN; cb += 16) {
-        float v[16];
-        tmem_ld16(lane_addr + (uint32_t)b * (2 * BN) + cb, v);
+        for (int cb = 0; cb < BN; cb += 16) {
+          float v1[16], v2[16], v3[16];
+          tmem_ld16(lane_addr + (uint32_t)b * bstride + cb, v1);
+          tmem_ld16(lane_addr + (uint32_t)b * bstride + BN + cb, v2);
+          tmem_ld16(lane_addr + (uint32_t)b * bstride + 2 * BN + cb, v3);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) ar[cb + q] += v[q];
-        tmem_ld16(lane_addr + (uint32_t)b * (2 * BN) + BN + cb, v);
+          for (int q = 0; q < 16; ++q) {
+            ar[cb + q] += v1[q] - v2[q];
+            ai[cb + q] += v3[q] - v1[q] - v2[q];
+          }
+        }
+      } else {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) ai[cb + q] += v[q];
+        for (int cb = 0; cb < BN; cb += 16) {
+          float v[16];
+          tmem_ld16(lane_addr + (uint32_t)b * bstride + cb, v);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) ar[cb + q] += v[q];
+          tmem_ld16(lane_addr + (uint32_t)b * bstride + BN + cb, v);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) ai[cb + q] += v[q];
+        }
       }
       tc_before();
       mbar_arrive(&acc_free[b]);
@@ -486,7 +528,7 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
           g.C64[((long long)w * Dc + row) * Dc + c] = zmake((double)vr, (double)vi);
         } else {
           const int w = row / g.pDb, lp = row % g.pDb;
-          pk_store(g.P, BM, g.pnkt, lp, w * g.pDb + gcol, (double)vr, (double)vi, split);
+          pk_store(g.P, BM, g.pnkt, lp, w * g.pDb + gcol, (double)vr, (double)vi, pm);
         }
       }
     }
@@ -501,7 +543,7 @@ tc_cgemm_kernel(int op, int site, const SiteDev* __restrict__ sd, const WorkDev*
 
 // Lenv[site] stacked as the A operand: row = w*Dl + a', k = a
 __global__ void pack_env_l_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
-                                  int N_sites, int split) {
+                                  int N_sites, int pm) {
   pdl_enter();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -511,12 +553,12 @@ __global__ void pack_env_l_kernel(int site, const SiteDev* __restrict__ sd, cons
   if (e >= (long long)M * K) return;
   const int row = (int)(e / K), k = (int)(e % K);
   const zc v = s.Lenv[e];          // [w][a'][a] row-major = [(w a')][a]
-  pk_store(W.tc_l, BM, nkt, row, k, v.x, v.y, split);
+  pk_store(W.tc_l, BM, nkt, row, k, v.x, v.y, pm);
 }
 
 // Renv[site] as the B operand: row = b', k = w*Dr + b
 __global__ void pack_env_r_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
-                                  int N_sites, int split) {
+                                  int N_sites, int pm) {
   pdl_enter();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -527,12 +569,12 @@ __global__ void pack_env_r_kernel(int site, const SiteDev* __restrict__ sd, cons
   const int w = (int)(e / ((long long)Dr * Dr)), rem = (int)(e % ((long long)Dr * Dr));
   const int bp = rem / Dr, b = rem % Dr;
   const zc v = s.Renv[e];          // [w][b'][b]
-  pk_store(W.tc_r, BN, nkt, bp, w * Dr + b, v.x, v.y, split);
+  pk_store(W.tc_r, BN, nkt, bp, w * Dr + b, v.x, v.y, pm);
 }
 
 // x as the B operand.  kind 0 (site): row = (s b), k = a;  kind 1 (bond D[l][r]): row = r, k = l
 __global__ void pack_x_kernel(int kind, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
-                              int N_sites, int split) {
+                              int N_sites, int pm) {
   pdl_enter();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -545,13 +587,13 @@ __global__ void pack_x_kernel(int kind, int site, const SiteDev* __restrict__ sd
   if (e >= (long long)Kd * Nn) return;
   const int k = (int)(e / Nn), n = (int)(e % Nn);
   const zc v = W.x[e];
-  pk_store(W.tc_x, BN, nkt, n, k, v.x, v.y, split);
+  pk_store(W.tc_x, BN, nkt, n, k, v.x, v.y, pm);
 }
 
 // Sparse MPO middle stage from the planar FP32 T1 into the packed A operand of the third GEMM:
 // T2[(a' s')][(w' b)] = sum_e val * T1[(w a')][(s b)]  over the CSR row (w', s').
 __global__ void wapply_tc_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
-                                 int N_sites, int split) {
+                                 int N_sites, int pm) {
   pdl_wait();
   const int r = blockIdx.z;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -574,14 +616,14 @@ __global__ void wapply_tc_kernel(int site, const SiteDev* __restrict__ sd, const
     ai += s.fw.val[e] * (double)T1i[off];
   }
   const int nkt = cdivd(s.Wr * Dr, BK);
-  pk_store(W.tc_t2, BM, nkt, ap * d + sp, wp * Dr + b, ar, ai, split);
+  pk_store(W.tc_t2, BM, nkt, ap * d + sp, wp * Dr + b, ar, ai, pm);
 }
 
 // Site tensor of an environment update as a packed operand; the grid covers the padded tiles.
 //   kind 0: A^H as A operand, row r', k (l s);    kind 1: A as A operand, row (l s), k r
 //   kind 2: conj(A) as A operand, row l', k (s r); kind 3: A as B operand, row (s r), k l
 __global__ void pack_site_kernel(int kind, int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
-                                 int N_sites, int split) {
+                                 int N_sites, int pm) {
   pdl_wait();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -608,12 +650,12 @@ __global__ void pack_site_kernel(int kind, int site, const SiteDev* __restrict__
       default: v = s.A[(long long)k * d * Dr + row]; break;
     }
   }
-  pk_store(dst, RT, cdivd(K, BK), row, k, v.x, v.y, split);
+  pk_store(dst, RT, cdivd(K, BK), row, k, v.x, v.y, pm);
 }
 
 // Renv[site] as the B operand of the right-update first stage: row (w' r'), k r.
 __global__ void pack_renv_rows_kernel(int site, const SiteDev* __restrict__ sd, const WorkDev* __restrict__ wk,
-                                      int N_sites, int split) {
+                                      int N_sites, int pm) {
   pdl_wait();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -624,7 +666,7 @@ __global__ void pack_renv_rows_kernel(int site, const SiteDev* __restrict__ sd, 
   if (e >= (long long)rp * kp) return;
   const int row = (int)(e / kp), k = (int)(e % kp);
   const zc v = (row < rows && k < K) ? s.Renv[(long long)row * Dr + k] : zmake(0, 0);
-  pk_store(W.tc_e2, BN, cdivd(K, BK), row, k, v.x, v.y, split);
+  pk_store(W.tc_e2, BN, cdivd(K, BK), row, k, v.x, v.y, pm);
 }
 
 // Sparse MPO stage of an environment update from the planar FP32 first-stage output, written as
@@ -634,7 +676,7 @@ __global__ void pack_renv_rows_kernel(int site, const SiteDev* __restrict__ sd, 
 //   which 1 (right): T2[w][(l s')][r'] = sum_e val T1[(l s)][(w' r')] over the backward CSR row
 //                    (w, s'); B row (w l), k (s' r').
 __global__ void wapply_env_kernel(int which, int site, const SiteDev* __restrict__ sd,
-                                  const WorkDev* __restrict__ wk, int N_sites, int split) {
+                                  const WorkDev* __restrict__ wk, int N_sites, int pm) {
   pdl_wait();
   const int r = blockIdx.y;
   const SiteDev& s = sd[(long long)r * N_sites + site];
@@ -670,7 +712,7 @@ __global__ void wapply_env_kernel(int which, int site, const SiteDev* __restrict
       }
     }
   }
-  pk_store(W.tc_e2, BN, cdivd(K, BK), row, k, ar, ai, split);
+  pk_store(W.tc_e2, BN, cdivd(K, BK), row, k, ar, ai, pm);
 }
 
 inline int cdivh(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -682,7 +724,21 @@ long long tc_pack_bytes(int rows_tile, long long rows, long long K) {
 }
 
 cudaError_t tc_setup() {
-  return cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGES * STAGE_BYTES);
+  const int smem = STAGES * STAGE_BYTES;
+  cudaError_t e = cudaFuncSetAttribute(tc_cgemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_cgemm_kernel<TC_PM_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_cgemm_kernel<TC_PM_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_cgemm_kernel<TC_PM_BF16 | TC_PM_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_cgemm_kernel<TC_PM_GAUSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_cgemm_kernel<TC_PM_BF16 | TC_PM_GAUSS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+  return e;
 }
 
 // K splits per output tile: the largest power of two <= 8 that keeps at least two K tiles per
@@ -695,7 +751,7 @@ int tc_splits(int tiles, int R, int maxK) {
 }
 
 cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
-                           int maxN, int maxK, int split, cudaStream_t st) {
+                           int maxN, int maxK, int pm, cudaStream_t st) {
   const int tn = cdivh(maxN, BN), tm = cdivh(maxM, BM);
   const int S = tc_splits(tn * tm, R, maxK);
   cudaLaunchConfig_t cfg = {};
@@ -715,52 +771,62 @@ cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* w
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = (S > 1 || g_tdvp_pdl) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel, op, site, sd, wk, N_sites, split, S);
+  switch (pm) {
+    case 0: return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel<0>, op, site, sd, wk, N_sites, S);
+    case TC_PM_SPLIT: return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel<TC_PM_SPLIT>, op, site, sd, wk, N_sites, S);
+    case TC_PM_BF16: return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel<TC_PM_BF16>, op, site, sd, wk, N_sites, S);
+    case TC_PM_BF16 | TC_PM_SPLIT:
+      return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel<TC_PM_BF16 | TC_PM_SPLIT>, op, site, sd, wk, N_sites, S);
+    case TC_PM_GAUSS: return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel<TC_PM_GAUSS>, op, site, sd, wk, N_sites, S);
+    case TC_PM_BF16 | TC_PM_GAUSS:
+      return cudaLaunchKernelEx(&cfg, tc_cgemm_kernel<TC_PM_BF16 | TC_PM_GAUSS>, op, site, sd, wk, N_sites, S);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                            long long max_elems, int split, cudaStream_t st) {
+                            long long max_elems, int pm, cudaStream_t st) {
   dim3 grid(cdivh(max_elems, 256), R);
-  if (which == 0) { const cudaError_t e_ = launch_pdl(pack_env_l_kernel, grid, 256, 0, st, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
-  else { const cudaError_t e_ = launch_pdl(pack_env_r_kernel, grid, 256, 0, st, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
+  if (which == 0) { const cudaError_t e_ = launch_pdl(pack_env_l_kernel, grid, 256, 0, st, site, sd, wk, N_sites, pm); if (e_ != cudaSuccess) return e_; }
+  else { const cudaError_t e_ = launch_pdl(pack_env_r_kernel, grid, 256, 0, st, site, sd, wk, N_sites, pm); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                          long long max_elems, int split, cudaStream_t st) {
+                          long long max_elems, int pm, cudaStream_t st) {
   dim3 grid(cdivh(max_elems, 256), R);
-  { const cudaError_t e_ = launch_pdl(pack_x_kernel, grid, 256, 0, st, kind, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_pdl(pack_x_kernel, grid, 256, 0, st, kind, site, sd, wk, N_sites, pm); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_site(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                             long long max_rows, long long max_k, int split, cudaStream_t st) {
+                             long long max_rows, long long max_k, int pm, cudaStream_t st) {
   const int RT = kind == 3 ? BN : BM;
   const long long total = (long long)cdivh(max_rows, RT) * RT * cdivh(max_k, BK) * BK;
   dim3 grid(cdivh(total, 256), R);
-  { const cudaError_t e_ = launch_pdl(pack_site_kernel, grid, 256, 0, st, kind, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_pdl(pack_site_kernel, grid, 256, 0, st, kind, site, sd, wk, N_sites, pm); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_renv_rows(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                                  long long max_rows, long long max_k, int split, cudaStream_t st) {
+                                  long long max_rows, long long max_k, int pm, cudaStream_t st) {
   const long long total = (long long)cdivh(max_rows, BN) * BN * cdivh(max_k, BK) * BK;
   dim3 grid(cdivh(total, 256), R);
-  { const cudaError_t e_ = launch_pdl(pack_renv_rows_kernel, grid, 256, 0, st, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_pdl(pack_renv_rows_kernel, grid, 256, 0, st, site, sd, wk, N_sites, pm); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_wapply_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                              long long max_rows, long long max_k, int split, cudaStream_t st) {
+                              long long max_rows, long long max_k, int pm, cudaStream_t st) {
   const long long total = (long long)cdivh(max_rows, BN) * BN * cdivh(max_k, BK) * BK;
   dim3 grid(cdivh(total, 256), R);
-  { const cudaError_t e_ = launch_pdl(wapply_env_kernel, grid, 256, 0, st, which, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_pdl(wapply_env_kernel, grid, 256, 0, st, which, site, sd, wk, N_sites, pm); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }
 
 cudaError_t launch_wapply_tc(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int max_xy,
-                             int n_rows, int split, cudaStream_t st) {
+                             int n_rows, int pm, cudaStream_t st) {
   dim3 grid(cdivh(max_xy, 256), n_rows, R);
-  { const cudaError_t e_ = launch_pdl(wapply_tc_kernel, grid, 256, 0, st, site, sd, wk, N_sites, split); if (e_ != cudaSuccess) return e_; }
+  { const cudaError_t e_ = launch_pdl(wapply_tc_kernel, grid, 256, 0, st, site, sd, wk, N_sites, pm); if (e_ != cudaSuccess) return e_; }
   return cudaGetLastError();
 }

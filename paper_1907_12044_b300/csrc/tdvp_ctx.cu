@@ -60,6 +60,9 @@ struct tdvp_ctx {
   int qr_force = -1;          // TDVP_OPT_QR_KERNEL
   bool cqr_ok[17] = {};       // cluster size launchable with the largest shared-memory slab
   int check_every = 0;        // 1: test Lanczos convergence at every k (else from the last k - 2 on)
+  int fused_lz = 1;           // TDVP_OPT_FUSED_LANCZOS: one cooperative launch per Lanczos iteration
+  double stall_test = 0.0;    // TDVP_OPT_STALL_TEST: > 0 = failure-path test with this wait limit (s)
+  int lz_cap = 0;             // co-resident blocks of the fused iteration kernel
   // per-launch timing
   // learned Krylov controller
   float* d_mlp = nullptr;           // weights (MLP_NPARAM)
@@ -72,7 +75,7 @@ struct tdvp_ctx {
   long long log_cap = 0;
   int logging = 0;
   int l_site = -1, r_site = -1;     // site whose environment is packed in tc_l / tc_r
-  int l_split = -1, r_split = -1;
+  int l_pm = -1, r_pm = -1;
   int prof = 0;
   int krylov_mode = TDVP_KRYLOV_ADAPTIVE;
   // CUDA-graph execution of whole steps (TDVP_OPT_GRAPH)
@@ -270,6 +273,7 @@ int tdvp_create(tdvp_ctx** out, int device, void* cuda_stream, int n_realisation
   ctx->h_work.assign(ctx->R, WorkDev{});
   ctx->ws_cap.assign(ctx->R, 0);
   ctx->qr_cap = qr_max_coresident_blocks(device);
+  ctx->lz_cap = lz_iter_capacity(device);
   if (tc_setup() != cudaSuccess) { tdvp_destroy(ctx); return TDVP_ERR_CUDA; }
   if (cqr_setup(device) != cudaSuccess) { tdvp_destroy(ctx); return TDVP_ERR_CUDA; }
   for (int C : {1, 2, 4, 8, 16}) ctx->cqr_ok[C] = cqr_max_clusters(C, TDVP_CQR_SMEM_MAX) >= 1;
@@ -542,6 +546,18 @@ Views one_view(tdvp_ctx* ctx, int r) {
   return Views{ctx->d_sites + (size_t)r * ctx->N, ctx->d_work + r, 1, ctx->d_flags + r, r};
 }
 
+// tensor-core precision mode word (TC_PM_* bits) of a TDVP_PREC_* value (mixed precisions only)
+int tc_mode(int P) {
+  switch (P) {
+    case TDVP_PREC_TF32X3: return TC_PM_SPLIT;
+    case TDVP_PREC_BF16: return TC_PM_BF16;
+    case TDVP_PREC_BF16X3: return TC_PM_BF16 | TC_PM_SPLIT;
+    case TDVP_PREC_TF32_3M: return TC_PM_GAUSS;
+    case TDVP_PREC_BF16_3M: return TC_PM_BF16 | TC_PM_GAUSS;
+    default: return 0;   // TDVP_PREC_TF32
+  }
+}
+
 // algorithmic real flops of one batched GEMM launch (8 per complex multiply-add)
 double gemm_flops(tdvp_ctx* ctx, const Views& v, int op, int site) {
   double f = 0;
@@ -645,33 +661,33 @@ int memset_tc(tdvp_ctx* ctx, const Views& v, int field, int which, int site) {
   return TDVP_OK;
 }
 
-int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int split);
+int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int pm);
 
 // the left environment of `site` packed in tc_l (kept while it stays valid)
-int ensure_l_pack(tdvp_ctx* ctx, const Views& v, int site, int split) {
-  if (ctx->l_site == site && ctx->l_split == split) return TDVP_OK;
+int ensure_l_pack(tdvp_ctx* ctx, const Views& v, int site, int pm) {
+  if (ctx->l_site == site && ctx->l_pm == pm) return TDVP_OK;
   int rc = memset_tc(ctx, v, 0, 0, site);
   if (rc) return rc;
   const Dims m = maxdims(ctx, site, v);
-  LAUNCH(launch_pack_env(0, site, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[site] * m.Dl * m.Dl, split, ctx->st));
+  LAUNCH(launch_pack_env(0, site, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[site] * m.Dl * m.Dl, pm, ctx->st));
   ctx->l_site = site;
-  ctx->l_split = split;
+  ctx->l_pm = pm;
   return TDVP_OK;
 }
 
 // Left update on the tensor cores: T1 = L A (stage 1, as the matvec's), the MPO stage written as
 // the B operand of the last stage, Lenv(i+1) = A^H T2.
-int env_left_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
+int env_left_tc(tdvp_ctx* ctx, const Views& v, int i, int pm) {
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
-  if ((rc = ensure_l_pack(ctx, v, i, split))) return rc;
-  LAUNCH(launch_pack_site(3, i, v.sd, v.wk, v.R, ctx->N, (long long)d * m.Dr, m.Dl, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_EL1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, m.Dl, split, ctx->st));
+  if ((rc = ensure_l_pack(ctx, v, i, pm))) return rc;
+  LAUNCH(launch_pack_site(3, i, v.sd, v.wk, v.R, ctx->N, (long long)d * m.Dr, m.Dl, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_EL1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, m.Dl, pm, ctx->st));
   LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_env(0, i, v.sd, v.wk, v.R, ctx->N, (long long)Wr * m.Dr, (long long)m.Dl * d,
-                                             split, ctx->st));
-  LAUNCH(launch_pack_site(0, i, v.sd, v.wk, v.R, ctx->N, m.Dr, (long long)m.Dl * d, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_EL3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, Wr * m.Dr, m.Dl * d, split, ctx->st));
+                                             pm, ctx->st));
+  LAUNCH(launch_pack_site(0, i, v.sd, v.wk, v.R, ctx->N, m.Dr, (long long)m.Dl * d, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_EL3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, Wr * m.Dr, m.Dl * d, pm, ctx->st));
   if (ctx->l_site == i + 1) ctx->l_site = -1;
   if (ctx->prof) {
     double f = 0;
@@ -687,16 +703,16 @@ int env_left_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
 
 // Right update on the tensor cores: T1 = A R^T (all w' at once), the backward MPO stage written as
 // the B operand of the last stage, Renv(i-1) = conj(A) T2^T.
-int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
+int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int pm) {
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
-  LAUNCH(launch_pack_site(1, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dl * d, m.Dr, split, ctx->st));
-  LAUNCH(launch_pack_renv_rows(i, v.sd, v.wk, v.R, ctx->N, (long long)Wr * m.Dr, m.Dr, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_ER1, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, Wr * m.Dr, m.Dr, split, ctx->st));
+  LAUNCH(launch_pack_site(1, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dl * d, m.Dr, pm, ctx->st));
+  LAUNCH(launch_pack_renv_rows(i, v.sd, v.wk, v.R, ctx->N, (long long)Wr * m.Dr, m.Dr, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_ER1, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, Wr * m.Dr, m.Dr, pm, ctx->st));
   LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_env(1, i, v.sd, v.wk, v.R, ctx->N, (long long)Wl * m.Dl, (long long)d * m.Dr,
-                                             split, ctx->st));
-  LAUNCH(launch_pack_site(2, i, v.sd, v.wk, v.R, ctx->N, m.Dl, (long long)d * m.Dr, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_ER3, i, v.sd, v.wk, v.R, ctx->N, m.Dl, Wl * m.Dl, d * m.Dr, split, ctx->st));
+                                             pm, ctx->st));
+  LAUNCH(launch_pack_site(2, i, v.sd, v.wk, v.R, ctx->N, m.Dl, (long long)d * m.Dr, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_ER3, i, v.sd, v.wk, v.R, ctx->N, m.Dl, Wl * m.Dl, d * m.Dr, pm, ctx->st));
   if (ctx->r_site == i - 1) ctx->r_site = -1;
   if (ctx->prof) {
     double f = 0;
@@ -710,47 +726,48 @@ int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
   return TDVP_OK;
 }
 
-int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int split) {
-  if (ctx->l_site != lsite || ctx->l_split != split) {
+int ensure_env_packs(tdvp_ctx* ctx, const Views& v, int lsite, int rsite, int pm) {
+  if (ctx->l_site != lsite || ctx->l_pm != pm) {
     int rc = memset_tc(ctx, v, 0, 0, lsite);
     if (rc) return rc;
     const Dims m = maxdims(ctx, lsite, v);
-    LAUNCH(launch_pack_env(0, lsite, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[lsite] * m.Dl * m.Dl, split, ctx->st));
+    LAUNCH(launch_pack_env(0, lsite, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[lsite] * m.Dl * m.Dl, pm, ctx->st));
     ctx->l_site = lsite;
-    ctx->l_split = split;
+    ctx->l_pm = pm;
   }
-  if (ctx->r_site != rsite || ctx->r_split != split) {
+  if (ctx->r_site != rsite || ctx->r_pm != pm) {
     int rc = memset_tc(ctx, v, 1, 1, rsite);
     if (rc) return rc;
     const Dims m = maxdims(ctx, rsite, v);
-    LAUNCH(launch_pack_env(1, rsite, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[rsite + 1] * m.Dr * m.Dr, split, ctx->st));
+    LAUNCH(launch_pack_env(1, rsite, v.sd, v.wk, v.R, ctx->N, (long long)ctx->Wb[rsite + 1] * m.Dr * m.Dr, pm, ctx->st));
     ctx->r_site = rsite;
-    ctx->r_split = split;
+    ctx->r_pm = pm;
   }
   return TDVP_OK;
 }
 
 // clear the per-solve tensor-core operands (their geometry changes from solve to solve)
-int prepare_tc_solve(tdvp_ctx* ctx, const Views& v, int kind, int site, int split) {
+int prepare_tc_solve(tdvp_ctx* ctx, const Views& v, int kind, int site, int pm) {
   PhaseScope ps(ctx, kind == 0 ? TDVP_PH_DERIV_FWD : TDVP_PH_DERIV_BWD);
   int rc;
   if (kind == 0) {
-    if ((rc = ensure_env_packs(ctx, v, site, site, split))) return rc;
+    if ((rc = ensure_env_packs(ctx, v, site, site, pm))) return rc;
     if ((rc = memset_tc(ctx, v, 2, 2, site))) return rc;
     return memset_tc(ctx, v, 3, 4, site);
   }
-  if ((rc = ensure_env_packs(ctx, v, site + 1, site, split))) return rc;
+  if ((rc = ensure_env_packs(ctx, v, site + 1, site, pm))) return rc;
   if ((rc = memset_tc(ctx, v, 2, 3, site))) return rc;
   return memset_tc(ctx, v, 3, 5, site);
 }
 
-int matvec_site_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
+// prepacked: the Lanczos kernels have already written x as the packed B operand
+int matvec_site_tc(tdvp_ctx* ctx, const Views& v, int i, int pm, bool prepacked = false) {
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
-  LAUNCH(launch_pack_x(0, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dl * d * m.Dr, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, m.Dl, split, ctx->st));
-  LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_tc(i, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wr * d, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV3, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, Wr * m.Dr, split, ctx->st));
+  if (!prepacked) LAUNCH(launch_pack_x(0, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dl * d * m.Dr, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, m.Dl, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_tc(i, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wr * d, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV3, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, Wr * m.Dr, pm, ctx->st));
   if (ctx->prof) {
     double f = 0;
     for (int r = v.r0; r < v.r0 + v.R; ++r) {
@@ -763,12 +780,12 @@ int matvec_site_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
   return TDVP_OK;
 }
 
-int matvec_bond_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
+int matvec_bond_tc(tdvp_ctx* ctx, const Views& v, int i, int pm, bool prepacked = false) {
   const Dims m = maxdims(ctx, i, v);
   const int Wb = ctx->Wb[i + 1];
-  LAUNCH(launch_pack_x(1, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dr * m.Dr, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z1, i, v.sd, v.wk, v.R, ctx->N, Wb * m.Dr, m.Dr, m.Dr, split, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, m.Dr, Wb * m.Dr, split, ctx->st));
+  if (!prepacked) LAUNCH(launch_pack_x(1, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dr * m.Dr, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z1, i, v.sd, v.wk, v.R, ctx->N, Wb * m.Dr, m.Dr, m.Dr, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, m.Dr, Wb * m.Dr, pm, ctx->st));
   if (ctx->prof) {
     double f = 0;
     for (int r = v.r0; r < v.r0 + v.R; ++r) {
@@ -780,14 +797,14 @@ int matvec_bond_tc(tdvp_ctx* ctx, const Views& v, int i, int split) {
   return TDVP_OK;
 }
 
-int env_left_tc(tdvp_ctx* ctx, const Views& v, int i, int split);
-int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int split);
+int env_left_tc(tdvp_ctx* ctx, const Views& v, int i, int pm);
+int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int pm);
 
 // Left environment of site i+1 from site i (Eq. tdvp1_h1i); FP64, or TF32 / TF32x3 on the
 // tensor cores in the mixed-precision sweep.
 int env_left(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
   PhaseScope ps(ctx, TDVP_PH_GET_ENV);
-  if (P != TDVP_PREC_FP64) return env_left_tc(ctx, v, i, P == TDVP_PREC_TF32X3 ? 1 : 0);
+  if (P != TDVP_PREC_FP64) return env_left_tc(ctx, v, i, tc_mode(P));
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
@@ -800,7 +817,7 @@ int env_left(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
 // Right environment of site i-1 from site i (Eq. tdvp1_hiN); FP64 or on the tensor cores.
 int env_right(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
   PhaseScope ps(ctx, TDVP_PH_GET_ENV);
-  if (P != TDVP_PREC_FP64) return env_right_tc(ctx, v, i, P == TDVP_PREC_TF32X3 ? 1 : 0);
+  if (P != TDVP_PREC_FP64) return env_right_tc(ctx, v, i, tc_mode(P));
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
@@ -883,20 +900,45 @@ int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
   return run_qr_timed(ctx, TDVP_CAT_QR, v, dir, i, mm, nn, qr_mode(ctx, v.R, mm, nn), ctx->rank_rtol, 0, 0);
 }
 
-int nblk_for(long long n) {
+int nblk_for(long long n, int cap) {
   long long nb = (n + TDVP_VEC_CHUNK - 1) / TDVP_VEC_CHUNK;
-  return (int)std::max(1LL, std::min<long long>(nb, TDVP_MAX_VEC_BLOCKS));
+  return (int)std::max(1LL, std::min<long long>(nb, cap));
+}
+
+// Lanczos arguments shared by the launch-by-launch and the graph-captured exponential.  The fused
+// iteration kernel runs when every realisation's chunks fit co-resident (the chunk count per
+// vector is capped at capacity / R for that); the mixed precisions let the Lanczos kernels write
+// each new Krylov vector as the packed tensor-core operand of the next matvec.
+LzArgs lz_args(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
+               int prec, bool* fused) {
+  const Dims m = maxdims(ctx, site, v);
+  const long long n = kind == 0 ? (long long)m.Dl * ctx->d[site] * m.Dr : (long long)m.Dr * m.Dr;
+  LzArgs a{};
+  a.sd = v.sd; a.wk = v.wk; a.R = v.R; a.N_sites = ctx->N; a.site = site; a.kind = kind;
+  a.src = src; a.dst = dst; a.theta = theta; a.tol = tol; a.kmax = ctx->kmax;
+  *fused = ctx->fused_lz && ctx->lz_cap >= v.R;
+  a.bcap = *fused ? std::min(TDVP_MAX_VEC_BLOCKS, ctx->lz_cap / v.R) : TDVP_MAX_VEC_BLOCKS;
+  a.nblk = nblk_for(n, a.bcap);
+  a.pack_pm = prec != TDVP_PREC_FP64 ? tc_mode(prec) : -1;
+  a.stall = ctx->stall_test > 0.0 ? 1 : 0;
+  a.wait_ns = a.stall ? (unsigned long long)(ctx->stall_test * 1e9) : 1000000000ull;
+  a.flags = v.flags;
+  a.mlp = (ctx->krylov_mode == TDVP_KRYLOV_LEARNED && ctx->mlp_ready) ? ctx->d_mlp : nullptr;
+  a.log = ctx->logging ? ctx->d_log : nullptr;
+  a.log_count = ctx->d_log_count;
+  a.log_cap = ctx->log_cap;
+  return a;
 }
 
 // exp(i theta H) applied to the start vector `src` (0 = x, 1 = site tensor, 2 = bond) with
 // H = H[site] (kind 0) or the zero-site H0 of bond (site, site+1) (kind 1); the result goes to
 // `dst` (1 = site tensor, 2 = bond, 3 = w).  Returns TDVP_OK or an error; sets *notconv.
 // The matvec of one Lanczos iteration (site or bond, FP64 or tensor cores).
-int lanczos_matvec(tdvp_ctx* ctx, const Views& v, int kind, int site, int prec, int split) {
+int lanczos_matvec(tdvp_ctx* ctx, const Views& v, int kind, int site, int prec, int pm) {
   PhaseScope ps(ctx, kind == 0 ? TDVP_PH_DERIV_FWD : TDVP_PH_DERIV_BWD);
   if (prec != TDVP_PREC_FP64) {
-    if (kind == 0) return matvec_site_tc(ctx, v, site, split);
-    return matvec_bond_tc(ctx, v, site, split);
+    if (kind == 0) return matvec_site_tc(ctx, v, site, pm, true);
+    return matvec_bond_tc(ctx, v, site, pm, true);
   }
   if (kind == 0) return matvec_site(ctx, v, site, OP_MV1);
   return matvec_bond(ctx, v, site);
@@ -910,25 +952,17 @@ int lanczos_matvec(tdvp_ctx* ctx, const Views& v, int kind, int site, int prec, 
 // host reads them after the replays.
 int expm_graph(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
                int prec) {
-  const Dims m = maxdims(ctx, site, v);
-  const long long n = kind == 0 ? (long long)m.Dl * ctx->d[site] * m.Dr : (long long)m.Dr * m.Dr;
   if (ctx->loop_n >= ctx->loop_cap) return fail(ctx, TDVP_ERR_STATE, "graph capture: too many Lanczos loops");
-  LzArgs a{};
-  a.sd = v.sd; a.wk = v.wk; a.R = v.R; a.N_sites = ctx->N; a.site = site; a.kind = kind;
-  a.src = src; a.dst = dst; a.theta = theta; a.tol = tol; a.kmax = ctx->kmax;
-  a.nblk = nblk_for(n); a.flags = v.flags;
-  a.mlp = (ctx->krylov_mode == TDVP_KRYLOV_LEARNED && ctx->mlp_ready) ? ctx->d_mlp : nullptr;
-  a.log = ctx->logging ? ctx->d_log : nullptr;
-  a.log_count = ctx->d_log_count;
-  a.log_cap = ctx->log_cap;
+  bool fused = false;
+  LzArgs a = lz_args(ctx, v, kind, site, src, dst, theta, tol, prec, &fused);
   a.jcheck = ctx->check_every ? 1 : 0;
   a.devj = 1;
   a.loop_iters = ctx->d_loop_iters;
   a.loop_id = ctx->loop_n++;
   CK(cudaMemsetAsync(v.flags, 0, sizeof(int) * v.R, ctx->st));
-  const int split = prec == TDVP_PREC_TF32X3 ? 1 : 0;
+  const int pm = tc_mode(prec);
   int rc;
-  if (prec != TDVP_PREC_FP64 && (rc = prepare_tc_solve(ctx, v, kind, site, split))) return rc;
+  if (prec != TDVP_PREC_FP64 && (rc = prepare_tc_solve(ctx, v, kind, site, pm))) return rc;
   LAUNCHC(TDVP_CAT_LZVEC, launch_lz_start(a, ctx->st));
   ctx->stats.kernel_launches++;     // two kernels
   cudaStreamCaptureStatus cs;
@@ -952,10 +986,15 @@ int expm_graph(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int d
   const cudaStream_t main_st = ctx->st;
   const long long before = ctx->stats.kernel_launches;
   ctx->st = ctx->body_st;
-  rc = lanczos_matvec(ctx, v, kind, site, prec, split);
+  rc = lanczos_matvec(ctx, v, kind, site, prec, pm);
   if (!rc) {
-    cudaError_t e = launch_lz_iter_pre(a, 0, ctx->st);
-    if (e == cudaSuccess) e = launch_lz_iter_post(a, 0, ctx->st);
+    cudaError_t e = cudaSuccess;
+    if (fused) {
+      e = launch_lz_iter(a, 0, ctx->st);
+    } else {
+      e = launch_lz_iter_pre(a, 0, ctx->st);
+      if (e == cudaSuccess) e = launch_lz_iter_post(a, 0, ctx->st);
+    }
     if (e == cudaSuccess) e = launch_lz_loop_ctl(a, 1, ctx->st);
     if (e != cudaSuccess) rc = fail(ctx, TDVP_ERR_CUDA, cudaGetErrorString(e));
   }
@@ -964,35 +1003,29 @@ int expm_graph(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int d
   const cudaError_t ee = cudaStreamEndCapture(ctx->body_st, &tmp);
   if (rc) return rc;
   if (ee != cudaSuccess) return fail(ctx, TDVP_ERR_CUDA, cudaGetErrorString(ee));
-  // kernels of one body run: the matvec's (counted while capturing) + dots, two passes (the
-  // tridiagonal step inside the second), next vector, loop control
-  ctx->loop_body_launches.push_back((int)(ctx->stats.kernel_launches - before) + 5);
+  // kernels of one body run: the matvec's (counted while capturing) + the fused iteration, or
+  // dots, two passes (the tridiagonal step inside the second) and next vector; loop control
+  ctx->loop_body_launches.push_back((int)(ctx->stats.kernel_launches - before) + (fused ? 2 : 5));
   ctx->stats.kernel_launches = before;
   LAUNCHC(TDVP_CAT_LZVEC, launch_lz_combine(a, ctx->st));
   return TDVP_OK;
 }
 
+int check_device_errors(tdvp_ctx* ctx);
+
 int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
          int* notconv, int prec = TDVP_PREC_FP64) {
   PhaseScope ps(ctx, TDVP_PH_KRYLOV);
   if (ctx->capturing) return expm_graph(ctx, v, kind, site, src, dst, theta, tol, prec);
-  const Dims m = maxdims(ctx, site, v);
-  const long long n = kind == 0 ? (long long)m.Dl * ctx->d[site] * m.Dr : (long long)m.Dr * m.Dr;
-  LzArgs a{};
-  a.sd = v.sd; a.wk = v.wk; a.R = v.R; a.N_sites = ctx->N; a.site = site; a.kind = kind;
-  a.src = src; a.dst = dst; a.theta = theta; a.tol = tol; a.kmax = ctx->kmax;
-  a.nblk = nblk_for(n); a.flags = v.flags;
-  a.mlp = (ctx->krylov_mode == TDVP_KRYLOV_LEARNED && ctx->mlp_ready) ? ctx->d_mlp : nullptr;
-  a.log = ctx->logging ? ctx->d_log : nullptr;
-  a.log_count = ctx->d_log_count;
-  a.log_cap = ctx->log_cap;
+  bool fused = false;
+  LzArgs a = lz_args(ctx, v, kind, site, src, dst, theta, tol, prec, &fused);
   int& kh = ctx->khist[2 * site + kind];
   const int guess = kh > 0 ? kh : 6;
   a.jcheck = ctx->check_every ? 1 : std::max(1, guess - 2);
   CK(cudaMemsetAsync(v.flags, 0, sizeof(int) * v.R, ctx->st));
-  const int split = prec == TDVP_PREC_TF32X3 ? 1 : 0;
+  const int pm = tc_mode(prec);
   if (prec != TDVP_PREC_FP64) {
-    int rc0 = prepare_tc_solve(ctx, v, kind, site, split);
+    int rc0 = prepare_tc_solve(ctx, v, kind, site, pm);
     if (rc0) return rc0;
   }
   LAUNCHC(TDVP_CAT_LZVEC, launch_lz_start(a, ctx->st));
@@ -1001,10 +1034,14 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
   bool all_done = false;
   while (j < ctx->kmax && !all_done) {
     for (int q = 0; q < batch && j < ctx->kmax; ++q, ++j) {
-      if ((rc = lanczos_matvec(ctx, v, kind, site, prec, split))) return rc;
-      LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));      // three kernels (tridiagonal step inside)
-      LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_post(a, j, ctx->st));     // next vector
-      ctx->stats.kernel_launches += 2;
+      if ((rc = lanczos_matvec(ctx, v, kind, site, prec, pm))) return rc;
+      if (fused) {
+        LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter(a, j, ctx->st));        // the whole iteration
+      } else {
+        LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_pre(a, j, ctx->st));    // three kernels (tridiagonal step inside)
+        LAUNCHC(TDVP_CAT_LZVEC, launch_lz_iter_post(a, j, ctx->st));   // next vector
+        ctx->stats.kernel_launches += 2;
+      }
       ctx->stats.matvecs += v.R;
     }
     CK(cudaMemcpyAsync(ctx->h_flags + v.r0, v.flags, sizeof(int) * v.R, cudaMemcpyDeviceToHost, ctx->st));
@@ -1019,7 +1056,11 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
   for (int r = 0; r < v.R; ++r) {
     const int f = ctx->h_flags[v.r0 + r];
     if (f < 0) return fail(ctx, TDVP_ERR_NAN, "Lanczos: non-finite value or unsupported exponent");
-    if (f == 0) return fail(ctx, TDVP_ERR_KRYLOV_NOT_CONVERGED, "Lanczos: solve did not finish");
+    if (f == 0) {
+      const int de = check_device_errors(ctx);     // a timed-out wait leaves the solve unfinished
+      if (de) return de;
+      return fail(ctx, TDVP_ERR_KRYLOV_NOT_CONVERGED, "Lanczos: solve did not finish");
+    }
     const int k = f & 0xffff;
     if ((f >> 16) & 1) { ctx->stats.not_converged++; if (notconv) *notconv = 1; }
     kmaxr = std::max(kmaxr, k);
@@ -1143,8 +1184,8 @@ int alloc_realisation(tdvp_ctx* ctx, int r, const std::vector<int>& bd) {
   if ((rc = dalloc(ctx, H.mps_allocs, &W.bar, 2 + 16))) return rc;   // root, generation, group counters
   if ((rc = dalloc(ctx, H.mps_allocs, &W.kprev, 2 * N))) return rc;
   if ((rc = dalloc(ctx, H.mps_allocs, &W.tri_count, 1))) return rc;
-  if ((rc = dalloc(ctx, H.mps_allocs, &W.lzc, 1))) return rc;
-  CK(cudaMemsetAsync(W.lzc, 0, sizeof(unsigned), ctx->st));
+  if ((rc = dalloc(ctx, H.mps_allocs, &W.lzc, 2))) return rc;   // last-block counter, fused-iteration barrier
+  CK(cudaMemsetAsync(W.lzc, 0, 2 * sizeof(unsigned), ctx->st));
   W.err = ctx->d_err + r;
   // boundary environments are the scalar 1
   const zc one = zmake(1.0, 0.0);
@@ -1351,7 +1392,8 @@ int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const doub
     LAUNCH(launch_copy_vec(1, i - 1, v.sd, v.wk, v.R, N, m.Dl * ctx->d[i - 1] * m.Dr, ctx->st));
     LzArgs a{};
     a.sd = v.sd; a.wk = v.wk; a.R = 1; a.N_sites = N; a.site = i - 1; a.kind = 0; a.src = 1; a.dst = 1;
-    a.kmax = ctx->kmax; a.nblk = nblk_for((long long)m.Dl * ctx->d[i - 1] * m.Dr); a.flags = v.flags;
+    a.kmax = ctx->kmax; a.bcap = TDVP_MAX_VEC_BLOCKS; a.pack_pm = -1;
+    a.nblk = nblk_for((long long)m.Dl * ctx->d[i - 1] * m.Dr, a.bcap); a.flags = v.flags;
     LAUNCH(launch_lz_start(a, ctx->st));
     ctx->stats.kernel_launches++;
     LAUNCH(launch_copy_vec(1, i - 1, v.sd, v.wk, 1, N, m.Dl * ctx->d[i - 1] * m.Dr, ctx->st));
@@ -1360,7 +1402,8 @@ int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const doub
     LzArgs a{};
     const Dims m = maxdims(ctx, 0, v);
     a.sd = v.sd; a.wk = v.wk; a.R = 1; a.N_sites = N; a.site = 0; a.kind = 0; a.src = 1; a.dst = 1;
-    a.kmax = ctx->kmax; a.nblk = nblk_for((long long)m.Dl * ctx->d[0] * m.Dr); a.flags = v.flags;
+    a.kmax = ctx->kmax; a.bcap = TDVP_MAX_VEC_BLOCKS; a.pack_pm = -1;
+    a.nblk = nblk_for((long long)m.Dl * ctx->d[0] * m.Dr, a.bcap); a.flags = v.flags;
     LAUNCH(launch_lz_start(a, ctx->st));
     ctx->stats.kernel_launches++;
     LAUNCH(launch_copy_vec(1, 0, v.sd, v.wk, 1, N, m.Dl * ctx->d[0] * m.Dr, ctx->st));
@@ -1375,7 +1418,7 @@ int tdvp_init_mps_tensors(tdvp_ctx* ctx, int r, const int* bond_dims, const doub
 int tdvp_ps_step(tdvp_ctx* ctx, double dt_fs, int n_steps, int precision, int krylov_mode, double krylov_tol) {
   if (!ctx) return TDVP_ERR_INVALID_ARG;
   if (n_steps < 0 || !(krylov_tol >= 0) || !std::isfinite(dt_fs)) return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: bad args");
-  if (precision != TDVP_PREC_FP64 && precision != TDVP_PREC_TF32 && precision != TDVP_PREC_TF32X3)
+  if (precision < TDVP_PREC_FP64 || precision > TDVP_PREC_LAST)
     return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported precision");
   if (krylov_mode != TDVP_KRYLOV_ADAPTIVE && krylov_mode != TDVP_KRYLOV_LEARNED)
     return fail(ctx, TDVP_ERR_INVALID_ARG, "ps_step: unsupported krylov mode");
@@ -1499,7 +1542,7 @@ int tdvp_center_to_zero(tdvp_ctx* ctx, int r) {
 int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, int precision, const double* x, double* y) {
   if (!ctx || r < 0 || r >= ctx->R || !x || !y) return TDVP_ERR_INVALID_ARG;
   if (!ctx->rh[r].mps || i < 0 || i >= ctx->N) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_heff: bad site");
-  if (precision < TDVP_PREC_FP64 || precision > TDVP_PREC_TF32X3) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_heff: precision");
+  if (precision < TDVP_PREC_FP64 || precision > TDVP_PREC_LAST) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_heff: precision");
   CK(cudaSetDevice(ctx->dev));
   const Views v = one_view(ctx, r);
   const SiteDev& S = ctx->h_sites[(size_t)r * ctx->N + i];
@@ -1511,8 +1554,8 @@ int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, int precision, const double* x,
     if ((rc = matvec_site(ctx, v, i, OP_MV1))) return rc;
   } else {
     ctx->l_site = ctx->r_site = -1;
-    if ((rc = prepare_tc_solve(ctx, v, 0, i, precision == TDVP_PREC_TF32X3))) return rc;
-    if ((rc = matvec_site_tc(ctx, v, i, precision == TDVP_PREC_TF32X3))) return rc;
+    if ((rc = prepare_tc_solve(ctx, v, 0, i, tc_mode(precision)))) return rc;
+    if ((rc = matvec_site_tc(ctx, v, i, tc_mode(precision)))) return rc;
   }
   CK(cudaMemcpyAsync(y, ctx->h_work[r].w, n * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -1522,7 +1565,7 @@ int tdvp_apply_heff(tdvp_ctx* ctx, int r, int i, int precision, const double* x,
 int tdvp_apply_h0(tdvp_ctx* ctx, int r, int i, int precision, const double* x, double* y) {
   if (!ctx || r < 0 || r >= ctx->R || !x || !y) return TDVP_ERR_INVALID_ARG;
   if (!ctx->rh[r].mps || i < 0 || i >= ctx->N - 1) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_h0: bad bond");
-  if (precision < TDVP_PREC_FP64 || precision > TDVP_PREC_TF32X3) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_h0: precision");
+  if (precision < TDVP_PREC_FP64 || precision > TDVP_PREC_LAST) return fail(ctx, TDVP_ERR_INVALID_ARG, "apply_h0: precision");
   CK(cudaSetDevice(ctx->dev));
   const Views v = one_view(ctx, r);
   const int Db = ctx->rh[r].bd[i + 1];
@@ -1534,8 +1577,8 @@ int tdvp_apply_h0(tdvp_ctx* ctx, int r, int i, int precision, const double* x, d
     if ((rc = matvec_bond(ctx, v, i))) return rc;
   } else {
     ctx->l_site = ctx->r_site = -1;
-    if ((rc = prepare_tc_solve(ctx, v, 1, i, precision == TDVP_PREC_TF32X3))) return rc;
-    if ((rc = matvec_bond_tc(ctx, v, i, precision == TDVP_PREC_TF32X3))) return rc;
+    if ((rc = prepare_tc_solve(ctx, v, 1, i, tc_mode(precision)))) return rc;
+    if ((rc = matvec_bond_tc(ctx, v, i, tc_mode(precision)))) return rc;
   }
   CK(cudaMemcpyAsync(y, ctx->h_work[r].w, n * sizeof(zc), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -1855,6 +1898,15 @@ int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
       return TDVP_OK;
     case TDVP_OPT_PDL:
       g_tdvp_pdl = value != 0.0 ? 1 : 0;
+      return TDVP_OK;
+    case TDVP_OPT_FUSED_LANCZOS:
+      graph_reset(ctx);
+      ctx->fused_lz = value != 0.0 ? 1 : 0;
+      return TDVP_OK;
+    case TDVP_OPT_STALL_TEST:
+      if (!(value >= 0.0 && value <= 1.0)) return fail(ctx, TDVP_ERR_INVALID_ARG, "stall test: wait limit in [0, 1] s");
+      graph_reset(ctx);
+      ctx->stall_test = value;
       return TDVP_OK;
     case TDVP_OPT_QR_KERNEL: {
       const int c = (int)value;

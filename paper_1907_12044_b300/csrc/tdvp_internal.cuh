@@ -157,7 +157,8 @@ struct WorkDev {
   long long tc_t1_plane;
   int* kprev;   // [2*N] last Krylov dimension per (site, kind)
   int* tri_count; // tridiagonal exponentials evaluated (convergence tests)
-  unsigned* lzc;  // blocks of the second orthogonalisation pass that have finished (reset by the last)
+  unsigned* lzc;  // [0] blocks of the second orthogonalisation pass that have finished (reset by the
+                  // last), [1] group-barrier word of the fused iteration kernel (both reset per solve)
   unsigned* bar;// [0]=count, [1]=generation of the QR group barrier
   int* err;     // device-side error flag of this realisation
 };
@@ -178,6 +179,13 @@ enum GemmOp {
   OP_TR3,       // E' = A^H T1
   OP_HX1,       // T1[w] = L_w A  with x = site tensor (energy: H_eff C)
 };
+
+// Precision mode word of the tensor-core path (kernels_tc.cu): bit 0 hi/lo split operands
+// (compensated products), bit 1 BF16 operands (kind::f16; else TF32, kind::tf32), bit 2 the
+// three-product (Gauss, "3M") complex form.
+#define TC_PM_SPLIT 1
+#define TC_PM_BF16 2
+#define TC_PM_GAUSS 4
 
 // Tensor-core GEMMs of the mixed-precision matvecs.
 // Tensor-core GEMMs: the Lanczos matvec stages (skipped once the solve is done) and the
@@ -219,6 +227,12 @@ struct LzArgs {
   int kmax;
   int jcheck;       // convergence is tested only once k >= jcheck
   int nblk;         // chunks per vector (max over realisations)
+  int bcap;         // at most this many chunks per vector (<= TDVP_MAX_VEC_BLOCKS)
+  int pack_pm;      // >= 0: also write each new Krylov vector as the packed tensor-core B operand
+                    // of the next matvec (TC_PM_* mode word), so no separate pack launch is needed
+  unsigned long long wait_ns;   // group-barrier wait limit of the fused iteration kernel
+  int stall;        // test of the failure path: the first barrier of the fused iteration waits for
+                    // one more block than the launch has, so every block's bounded wait runs out
   int* flags;       // [R] device: k | notconv << 16 | TDVP_KFLAG_DONE once a solve is done, -1 on failure
   const float* mlp; // learned controller weights (null: tests start at jcheck)
   float* log;       // solve log rows [8 features, k] (null: no logging)
@@ -267,6 +281,11 @@ cudaError_t launch_lz_start(const LzArgs& a, cudaStream_t st);
 cudaError_t launch_lz_iter_pre(const LzArgs& a, int j, cudaStream_t st);   // orthogonalisation
 cudaError_t launch_lz_iter_post(const LzArgs& a, int j, cudaStream_t st);  // tridiagonal exp, next vector
 cudaError_t launch_lz_combine(const LzArgs& a, cudaStream_t st);
+// One whole Lanczos iteration in one cooperative launch (dots, both Gram-Schmidt passes, the
+// tridiagonal step, the next vector), with bounded group barriers between its phases; every block
+// of a realisation must be co-resident, so a.nblk * a.R <= lz_iter_capacity().
+cudaError_t launch_lz_iter(const LzArgs& a, int j, cudaStream_t st);
+int lz_iter_capacity(int device);
 // loop control of a device-driven solve: which = 0 before the loop (condition = some solve not
 // done), 1 at the end of the body (advance the iteration index of unfinished solves, count the
 // body execution, condition = some solve not done)
@@ -309,11 +328,11 @@ cudaError_t tc_setup();
 // a thread-block cluster (tc_splits)
 int tc_splits(int tiles, int R, int maxK);
 cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
-                           int maxN, int maxK, int split, cudaStream_t st);
+                           int maxN, int maxK, int pm, cudaStream_t st);
 cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                            long long max_elems, int split, cudaStream_t st);
+                            long long max_elems, int pm, cudaStream_t st);
 cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                          long long max_elems, int split, cudaStream_t st);
+                          long long max_elems, int pm, cudaStream_t st);
 // Environment updates on the tensor cores (kernels_tc.cu).  which = 0: left (site i -> Lenv of
 // i+1), 1: right (site i -> Renv of i-1).  Stage operands:
 //   pack_site (kind 0) A^H as A operand [r'][(l s)]; (kind 1) A as A operand [(l s)][r];
@@ -323,13 +342,13 @@ cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* 
 //              (which 1) T2[w][(l s')][r'] as B operand [(w l)][(s' r')]
 // Every pack covers the padded tiles (zeros outside the valid region).
 cudaError_t launch_pack_site(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                             long long max_rows, long long max_k, int split, cudaStream_t st);
+                             long long max_rows, long long max_k, int pm, cudaStream_t st);
 cudaError_t launch_pack_renv_rows(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                                  long long max_rows, long long max_k, int split, cudaStream_t st);
+                                  long long max_rows, long long max_k, int pm, cudaStream_t st);
 cudaError_t launch_wapply_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
-                              long long max_rows, long long max_k, int split, cudaStream_t st);
+                              long long max_rows, long long max_k, int pm, cudaStream_t st);
 cudaError_t launch_wapply_tc(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int max_xy,
-                             int n_rows, int split, cudaStream_t st);
+                             int n_rows, int pm, cudaStream_t st);
 
 // Controller training (kernels_mlp.cu)
 int mlp_partial_floats(int B);

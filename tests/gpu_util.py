@@ -6,6 +6,20 @@ import paper_1907_12044_b300 as pkg
 from oracle import TDVPState, populations, energy
 
 
+# Relative error bounds of one mixed-precision contraction, ||y - y_ref|| / ||y_ref||: 10 u of
+# the operand format for the 4M modes (TF32 u = 2^-11, BF16 u = 2^-8), 20 u for 3M (one more
+# rounding per operand), 2e-5 for TF32x3 and 10 x 2^-16 for BF16x3 (compensated products).
+U_TF32, U_BF16 = 2.0 ** -11, 2.0 ** -8
+MIXED_TOL = {pkg.PREC_TF32: 10 * U_TF32, pkg.PREC_TF32X3: 2e-5, pkg.PREC_BF16: 10 * U_BF16,
+             pkg.PREC_BF16X3: 10 * 2.0 ** -16, pkg.PREC_TF32_3M: 20 * U_TF32, pkg.PREC_BF16_3M: 20 * U_BF16}
+PREC_NAME = {pkg.PREC_TF32: "TF32", pkg.PREC_TF32X3: "TF32x3", pkg.PREC_BF16: "BF16",
+             pkg.PREC_BF16X3: "BF16x3", pkg.PREC_TF32_3M: "TF32-3M", pkg.PREC_BF16_3M: "BF16-3M"}
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
 def engine_for(params, D=None, tensors=None, R=1, kmax=64):
     eng = pkg.Engine(n_realisations=R, kmax=kmax)
     for r in range(R):

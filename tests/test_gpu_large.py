@@ -27,7 +27,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_1907_12044_b300 as pkg  # noqa: E402
-from gpu_util import engine_for, debug_qr_or_rejected  # noqa: E402
+from gpu_util import engine_for, debug_qr_or_rejected, MIXED_TOL, PREC_NAME, rel_err  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -57,6 +57,10 @@ def test_large_chain_heff_and_expm_match_oracle_at_d128(large128):
     assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
     y3 = eng.apply_heff(0, site, x, precision=pkg.PREC_TF32X3)
     assert np.abs(y3 - yo).max() <= 2e-5 * np.abs(yo).max()
+    for prec in pkg.MIXED_PRECISIONS:
+        e = rel_err(eng.apply_heff(0, site, x, precision=prec), yo)
+        print(f"D = 128 site {site}: {PREC_NAME[prec]} rel err {e:.2e}")
+        assert e <= MIXED_TOL[prec], (prec, e)
     C = mps[site]
     tau = 10.0 * PHASE_PER_CM_FS / 2
     out, k = eng.debug_expm(0, site, -1j * tau, 1e-12, C)

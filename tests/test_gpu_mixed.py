@@ -1,9 +1,13 @@
-"""Mixed-precision (tensor-core) Lanczos matvecs against the FP64 oracle.
+"""Mixed-precision (tensor-core) contractions against the FP64 oracle.
 
-TF32 rounds every operand to 11 significant bits (relative error <= 2^-12 per operand), so a
-complex contraction carries a relative error of order 1e-3 of its terms; the compensated mode
-(hi/lo split, three products) reaches FP32-level products (~1e-6).  The bounds below are those
-orders with a margin: ||y - y_ref|| / ||y_ref|| <= 5e-3 (TF32) and <= 2e-5 (TF32x3).
+Each mode rounds the operands of the real products to its input format: TF32 keeps 11
+significant bits (unit roundoff u = 2^-11), BF16 8 (u = 2^-8); the compensated x3 modes carry
+the rounded remainder as a second term, so their products are good to about u^2 of the format
+(limited to ~FP32 by the accumulator for TF32x3, ~2^-16 for BF16x3); the 3M (Gauss) form adds
+one more rounding (of re + im) per operand and a subtraction of larger partial products.  A
+complex contraction of many terms then carries a relative error of a few u of its terms.  The
+bounds (tests/gpu_util.py) are 10 u (4M), 20 u (3M), with the x3 modes at 2e-5 (TF32x3) and
+10 x 2^-16 (BF16x3): ||y - y_ref|| / ||y_ref|| against the oracle's complex128 contraction.
 """
 import numpy as np
 import pytest
@@ -18,13 +22,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_1907_12044_b300 as pkg  # noqa: E402
-from gpu_util import engine_for, rel_pop_err  # noqa: E402
-
-TOL = {pkg.PREC_TF32: 5e-3, pkg.PREC_TF32X3: 2e-5}
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+from gpu_util import engine_for, rel_pop_err, MIXED_TOL as TOL, PREC_NAME as NAME, rel_err as _rel  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -51,10 +49,10 @@ def test_mixed_heff_matches_oracle(c1_random, site):
         x = rng.normal(size=mps[site].shape) + 1j * rng.normal(size=mps[site].shape)
         yo = heff_apply(L, W[site], R, x)
         errs = {}
-        for prec in (pkg.PREC_TF32, pkg.PREC_TF32X3):
+        for prec in pkg.MIXED_PRECISIONS:
             y = eng.apply_heff(0, site, x, precision=prec)
             errs[prec] = _rel(y, yo)
-        print(f"site {site}: rel err TF32 {errs[pkg.PREC_TF32]:.2e}  TF32x3 {errs[pkg.PREC_TF32X3]:.2e}")
+        print(f"site {site}: rel err " + "  ".join(f"{NAME[q]} {e:.2e}" for q, e in errs.items()))
         for prec, e in errs.items():
             assert e <= TOL[prec], (prec, e)
     finally:
@@ -81,16 +79,23 @@ def test_mixed_zero_site_matches_oracle(c1_random, bond):
         yo = h0_apply(L, R, x)
         y64 = eng.apply_h0(0, bond, x, precision=pkg.PREC_FP64)
         assert _rel(y64, yo) <= 1e-12
-        for prec in (pkg.PREC_TF32, pkg.PREC_TF32X3):
+        for prec in pkg.MIXED_PRECISIONS:
             e = _rel(eng.apply_h0(0, bond, x, precision=prec), yo)
-            print(f"bond {bond}: prec {prec} rel err {e:.2e}")
+            print(f"bond {bond}: {NAME[prec]} rel err {e:.2e}")
             assert e <= TOL[prec], (prec, e)
     finally:
         eng.center_to_zero(0)
 
 
-@pytest.mark.parametrize("prec,tol", [(2, 1e-5), (1, 3e-3)])
-def test_mixed_steps_track_fp64_oracle(prec, tol):
+# relative population error over 10 steps: the matvec bound above times a few (the error of
+# each local exponential adds up over the 2N - 1 site updates of a step and over the steps)
+STEP_TOL = {pkg.PREC_TF32X3: 1e-5, pkg.PREC_TF32: 3e-3, pkg.PREC_BF16X3: 3e-4, pkg.PREC_BF16: 2.5e-2,
+            pkg.PREC_TF32_3M: 6e-3, pkg.PREC_BF16_3M: 5e-2}
+
+
+@pytest.mark.parametrize("prec", list(STEP_TOL))
+def test_mixed_steps_track_fp64_oracle(prec):
+    tol = STEP_TOL[prec]
     p = wl.tiny_chain()
     tens = wl.random_mps_tensors(p.phys_dims(), 16, seed=9)
     eng = engine_for(p, tensors=tens)
