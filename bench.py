@@ -71,9 +71,10 @@ def parse(argv=None):
     ap.add_argument("--plain-tol", type=float, default=1e-12, help="Lanczos tolerance of the plain FP64 arm")
     ap.add_argument("--rank-rtol", type=float, default=1e-6,
                     help="rank threshold of the gauge-shift QR, the same on every arm")
-    ap.add_argument("--arms", default="mixed,fp64,plain",
-                    help="GPU arms to run (mixed = the timed arm, fp64 = the same with FP64 matvecs, "
-                         "plain = FP64 at --plain-tol, every k tested, launch by launch)")
+    ap.add_argument("--arms", default="mixed,adaptive,fp64,plain",
+                    help="GPU arms to run (mixed = the timed arm, adaptive = the same without the learned "
+                         "controller (the library's default test rule), fp64 = the timed arm with FP64 "
+                         "matvecs, plain = FP64 at --plain-tol, every k tested, launch by launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-prof", action="store_true", help="skip the per-kernel breakdown step")
@@ -170,16 +171,19 @@ def sig(x, n=4):
     return float(f"{x:.{n}g}")
 
 
-def train_controller(eng, seed=0):
-    """Train the learned Krylov controller on the solve log of the warm-up steps (GPU)."""
+def train_controller(eng, seed=0, samples=None):
+    """Train the learned Krylov controller on the solve log of the warm-up steps (GPU): 150 passes
+    over a small log, fewer over a large one (at least 8, about 3e6 sample visits)."""
     from paper_1907_12044_b300.controller import init_weights
     eng.controller_set_weights(init_weights(seed))
-    return eng.controller_train(epochs=150, batch=256, lr=3e-3)
+    epochs = 150 if not samples else int(min(150, max(8, 3e6 / samples)))
+    return eng.controller_train(epochs=epochs, batch=256, lr=3e-3)
 
 
 ARMS = {
     # name: (precision, tolerance attribute, graph, learned, test every k)
     "mixed": (None, "tol", True, True, False),
+    "adaptive": (None, "tol", True, False, False),
     "fp64": ("fp64", "tol", True, True, False),
     "plain": ("fp64", "plain_tol", False, False, True),
 }
@@ -219,7 +223,7 @@ def timed_run(args, p, name, world, dev, stream, flush):
     if learned:
         nlog = eng.stats()["krylov_solves"]
         eng.controller_logging(0)
-        ctl = {"train_loss": sig(train_controller(eng)), "samples": int(nlog)}
+        ctl = {"train_loss": [sig(x, 3) for x in train_controller(eng, samples=nlog)], "samples": int(nlog)}
     mode = pkg.KRYLOV_LEARNED if learned else pkg.KRYLOV_ADAPTIVE
     if graph:
         eng.set_option(pkg.OPT_GRAPH, 1)
@@ -399,6 +403,11 @@ def run_ours(args, rank, world):
     if "fp64" in runs and main is not runs["fp64"]:
         e, m = pop_error(args.dt, main["pops"], runs["fp64"]["pops"])
         out["pop_error_vs_fp64_arm"] = {"eq_error": sig(e, 3), "max_abs_dP": sig(m, 3)}
+    if "adaptive" in runs and main is not runs["adaptive"]:
+        ad, ms = runs["adaptive"], main
+        out["controller_gain"] = {"wall": sig(ad["ms"] / ms["ms"]),
+                                  "tri_evals": sig(ad["stats"]["tri_evals"] / max(ms["stats"]["tri_evals"], 1)),
+                                  "against": "default rule (tests from the previous k - 2)"}
     out["arms"] = {("timed" if r is main else a): arm_summary(args, r, N, world) for a, r in runs.items()}
     if main["controller"]:
         out["learned_controller"] = main["controller"]
@@ -446,6 +455,7 @@ def run_batched(args, R, rank=0, world=1):
     eng.autotune()
     graph = not args.no_graph and args.warmup >= 1
     learned = not args.no_learned
+    ctl_loss, nlog = None, 0
     if learned:
         eng.controller_logging(1 << 22)
     for _ in range(args.warmup - (1 if graph else 0)):
@@ -453,7 +463,8 @@ def run_batched(args, R, rank=0, world=1):
     mode = pkg.KRYLOV_ADAPTIVE
     if learned:
         eng.controller_logging(0)
-        train_controller(eng)
+        nlog = eng.stats()["krylov_solves"]
+        ctl_loss = train_controller(eng, samples=nlog)
         mode = pkg.KRYLOV_LEARNED
     if graph:
         eng.set_option(pkg.OPT_GRAPH, 1)
@@ -480,6 +491,9 @@ def run_batched(args, R, rank=0, world=1):
             "value": sig((2 * N - 1) * R * steps / (ms_max / 1e3)), "unit": UNIT,
             "ms_per_step": sig(ms_max / steps), "gpu_launches": int(st["kernel_launches"]),
             "krylov": "learned controller" if learned else "adaptive",
+            "controller": {"samples": int(nlog), "train_loss": [sig(x, 3) for x in ctl_loss]} if ctl_loss else None,
+            "krylov_mean": sig(st["krylov_dim_sum"] / max(st["krylov_solves"], 1), 3),
+            "tri_evals_per_solve": sig(st["tri_evals"] / max(st["krylov_solves"], 1), 3),
             "execution": "CUDA-graph steps" if graph else "launch by launch",
             "sharding": f"realisation r on rank r mod {world}" if world > 1 else "one GPU"}, pops
 

@@ -258,22 +258,33 @@ void tdvp_reset_stats(tdvp_ctx* ctx);
  * Returns TDVP_ERR_DEVICE_TIMEOUT if a bounded device-side wait gave up. */
 int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* cuda_stream);
 
-/* Learned Krylov controller (not in the paper): a two-layer MLP, 8 features -> 64 -> 64 -> 1, ReLU,
- * FP32, MLP_NPARAM = 4801 floats laid out W1[8][64], b1[64], W2[64][64], b2[64], W3[64], b3.
+/* Learned Krylov controller (not in the paper): a two-layer MLP, 8 features -> 64 -> 64, ReLU,
+ * FP32, with two heads on the second hidden layer: the Krylov dimension y (linear) and the logit a
+ * of the acceptance of the dimension kp = floor(y) clamped to [1, 126] (logistic: will the residual
+ * test pass at kp).  MLP_NPARAM = 4866 floats laid out W1[8][64], b1[64], W2[64][64], b2[64],
+ * W3[64], b3 (head 1), W4[64], b4 (head 2).
  * Features of a local exponential, known after its first Lanczos step: log10(1 + |tau| ||H v||),
  * kind (site 0 / bond 1), previous k of the same site and kind / 32, site / (N-1),
  * log2(vector length) / 20, log10|tau| / 4, -log10(tol) / 12, log10(1 + |tau| |alpha_0|).
- * Its prediction only moves the first convergence test; the stopping rule is unchanged. */
-int tdvp_controller_set_weights(tdvp_ctx* ctx, const float* w, int n);   /* n = 4801, host array */
+ * With TDVP_KRYLOV_LEARNED the Lanczos iterations run without any convergence test up to kp (kp + 1
+ * when a < 0); from there the adaptive test (same estimate, same tolerance) decides where the solve
+ * stops, so a wrong prediction costs iterations or tests, never accuracy. */
+int tdvp_controller_set_weights(tdvp_ctx* ctx, const float* w, int n);   /* n = 4866, host array */
 int tdvp_controller_get_weights(tdvp_ctx* ctx, float* w, int n);
 /* Log every finished exponential (features, k) into a device buffer of `capacity` rows; 0 stops. */
 int tdvp_controller_logging(tdvp_ctx* ctx, long long capacity);
 /* Copy up to max_rows log rows (9 floats each) to the host; rows receives the logged count. */
 int tdvp_controller_log(tdvp_ctx* ctx, float* out, long long max_rows, long long* rows);
-/* Adam (beta 0.9/0.999) on the mean-squared error of k over the log, in mini-batches, on the GPU. */
+/* Training on the log, on the GPU, in two stages of `epochs` passes over mini-batches of `batch`
+ * rows, Adam (beta 0.9/0.999, moments reset per stage): (1) trunk and head 1 by the mean-squared
+ * error of k; (2) head 2 alone (trunk frozen) by the logistic loss of [k <= kp].  final_loss[0],
+ * final_loss[1] receive each stage's mean loss over its last epoch (final_loss may be NULL). */
 int tdvp_controller_train(tdvp_ctx* ctx, int epochs, int batch, float lr, float* final_loss);
-/* Loss and gradient of the current weights on B rows X[B][8], targets t[B] (host), for checking. */
-int tdvp_controller_loss_grad(tdvp_ctx* ctx, const float* X, const float* t, int B, float* loss, float* grad);
+/* Loss and gradient (all MLP_NPARAM entries) of head `head` (0: squared error of k over trunk and
+ * head 1; 1: logistic loss of the acceptance over head 2) of the current weights on B rows
+ * X[B][8] with final dimensions t[B] (host), for checking. */
+int tdvp_controller_loss_grad(tdvp_ctx* ctx, int head, const float* X, const float* t, int B, float* loss,
+                              float* grad);
 
 /* Autotuner: for every distinct gauge-shift QR shape of the chain, time the cooperative-grid QR
  * kernel with several block counts per realisation and the cluster QR kernel with several

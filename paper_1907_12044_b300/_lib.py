@@ -18,7 +18,7 @@ PREC_BF16_3M = 6
 MIXED_PRECISIONS = (PREC_TF32, PREC_TF32X3, PREC_BF16, PREC_BF16X3, PREC_TF32_3M, PREC_BF16_3M)
 KRYLOV_ADAPTIVE = 0
 KRYLOV_LEARNED = 1
-MLP_NPARAM = 4801
+MLP_NPARAM = 4866
 
 ERRORS = {
     -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
@@ -119,7 +119,7 @@ def load_library():
     lib.tdvp_controller_logging.argtypes = [P, C.c_longlong]
     lib.tdvp_controller_log.argtypes = [P, fp, C.c_longlong, C.POINTER(C.c_longlong)]
     lib.tdvp_controller_train.argtypes = [P, C.c_int, C.c_int, C.c_float, fp]
-    lib.tdvp_controller_loss_grad.argtypes = [P, fp, fp, C.c_int, fp, fp]
+    lib.tdvp_controller_loss_grad.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, fp]
     lib.tdvp_lq_noalloc.argtypes = [C.c_int, C.c_int, P, P, P, P]
     lib.tdvp_reset_stats.argtypes = [P]
     lib.tdvp_reset_stats.restype = None
@@ -309,16 +309,18 @@ class Engine:
         return out
 
     def controller_train(self, epochs=20, batch=1024, lr=1e-3):
-        loss = C.c_float()
-        self._check(self.lib.tdvp_controller_train(self._h, int(epochs), int(batch), float(lr), C.byref(loss)))
-        return loss.value
+        """Both training stages; returns (mean-squared error of k, logistic loss of acceptance)."""
+        loss = np.zeros(2, np.float32)
+        self._check(self.lib.tdvp_controller_train(self._h, int(epochs), int(batch), float(lr), _fptr(loss)))
+        return float(loss[0]), float(loss[1])
 
-    def controller_loss_grad(self, X, t):
+    def controller_loss_grad(self, X, t, head=0):
         X = np.ascontiguousarray(X, dtype=np.float32)
         t = np.ascontiguousarray(t, dtype=np.float32)
         loss = C.c_float()
         g = np.zeros(MLP_NPARAM, np.float32)
-        self._check(self.lib.tdvp_controller_loss_grad(self._h, _fptr(X), _fptr(t), X.shape[0], C.byref(loss), _fptr(g)))
+        self._check(self.lib.tdvp_controller_loss_grad(self._h, int(head), _fptr(X), _fptr(t), X.shape[0],
+                                                       C.byref(loss), _fptr(g)))
         return loss.value, g
 
     def autotune(self):

@@ -132,10 +132,12 @@ __device__ __forceinline__ zc warp_transpose_sum(zc (&v)[G]) {
   return s;
 }
 
-// Partial dots p_t = sum_{e in chunk} conj(V_t[e]) w[e] for t <= j into table `tab`.
-__device__ void chunk_dots(const WorkDev& W, const VecGeom& g, int j, int tab, int b, double* red) {
-  constexpr int G = 8;
-  zc* wsum = reinterpret_cast<zc*>(red);    // [NT/32][G] complex
+constexpr int DOT_G = 8;   // coefficients summed per pass over the chunk
+
+// Partial dots p_t = sum_{e in chunk} conj(V_t[e]) w[e] for t <= j into table `tab`.  `wsum` is a
+// shared buffer of (NT/32) * DOT_G complex values (16-byte aligned as a zc array).
+__device__ void chunk_dots(const WorkDev& W, const VecGeom& g, int j, int tab, int b, zc* wsum) {
+  constexpr int G = DOT_G;
   const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
   for (int t0 = 0; t0 <= j; t0 += G) {
     zc acc[G];
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(NT) lz_start2(LzArgs a) {
 
 __global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
   pdl_enter();
-  __shared__ double red[2 * 8 * NT / 32];
+  __shared__ zc wsum[DOT_G * NT / 32];
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
   if (W.ks->done) return;
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(NT) lz_dots(LzArgs a, int j) {
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
   if (b >= g.nblk) return;
-  chunk_dots(W, g, j, 0, b, red);
+  chunk_dots(W, g, j, 0, b, wsum);
 }
 
 __device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, double* al, double* be,
@@ -247,7 +249,8 @@ __device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, doubl
 // block to finish then takes the tridiagonal step)
 __global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
   pdl_enter();
-  __shared__ double red[2 * 8 * NT / 32];
+  __shared__ double red[2 * NT / 32];
+  __shared__ zc wsum[DOT_G * NT / 32];
   __shared__ zc h[TDVP_KMAX_HARD];
   const int r = blockIdx.y, b = blockIdx.x;
   const WorkDev& W = a.wk[r];
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(NT) lz_upd(LzArgs a, int j, int pass) {
   }
   if (pass == 1) {
     __syncthreads();
-    chunk_dots(W, g, j, 1, b, red);
+    chunk_dots(W, g, j, 1, b, wsum);
     if (b == 0 && threadIdx.x == 0) W.ks->alpha[j] = h[j].x;
   } else {
     const zc s = block_zsum(zmake(nn, 0), red);
@@ -603,8 +606,15 @@ __device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, doubl
     }
     __syncthreads();
     if (a.mlp) {
-      const float y = mlp_infer(ks->feat, a.mlp, reinterpret_cast<float*>(sh));
-      if (threadIdx.x == 0) ks->kpred = (int)fminf(fmaxf(floorf(y), 1.f), 126.f);
+      float za;
+      const float y = mlp_infer(ks->feat, a.mlp, reinterpret_cast<float*>(sh), &za);
+      if (threadIdx.x == 0) {
+        // the dimension the controller predicts; when its acceptance head predicts that the
+        // residual test fails there, the first test is made one dimension later
+        int kp = (int)fminf(fmaxf(floorf(y), 1.f), 126.f);
+        if (za < 0.f) kp += 1;
+        ks->kpred = kp;
+      }
       __syncthreads();
     }
   }
@@ -721,7 +731,8 @@ __device__ bool lz_group_sync(const WorkDev& W, int nblocks, int b, unsigned lon
 //   4. unless the solve is done: V_{j+1} = x = w / beta_j (and its packed tensor-core operand)
 // The arithmetic and its order are those of lz_dots, lz_upd (both passes) and lz_next.
 __global__ void __launch_bounds__(NT) lz_iter(LzArgs a, int j) {
-  __shared__ double red[2 * 8 * NT / 32];
+  __shared__ double red[2 * NT / 32];
+  __shared__ zc wsum[DOT_G * NT / 32];
   __shared__ zc h[TDVP_KMAX_HARD];
   __shared__ int last;
   __shared__ double sh[TRI_SH];
@@ -735,7 +746,7 @@ __global__ void __launch_bounds__(NT) lz_iter(LzArgs a, int j) {
   const SiteDev* sdr = a.sd + (long long)r * a.N_sites;
   const VecGeom g = geom(vec_len(sdr, a.site, a.kind), b, a.bcap);
   if (b >= g.nblk) return;
-  chunk_dots(W, g, j, 0, b, red);
+  chunk_dots(W, g, j, 0, b, wsum);
   // failure-path test: the first barrier counts one block more than the launch has, a participant
   // that never arrives, so every block's bounded wait runs out
   if (!lz_group_sync(W, a.stall ? g.nblk + 1 : g.nblk, b, a.wait_ns)) return;
@@ -747,7 +758,7 @@ __global__ void __launch_bounds__(NT) lz_iter(LzArgs a, int j) {
     W.w[e] = we;
   }
   __syncthreads();
-  chunk_dots(W, g, j, 1, b, red);
+  chunk_dots(W, g, j, 1, b, wsum);
   if (b == 0 && threadIdx.x == 0) W.ks->alpha[j] = h[j].x;
   if (!lz_group_sync(W, g.nblk, b, a.wait_ns)) return;
   // second pass and the norm partials

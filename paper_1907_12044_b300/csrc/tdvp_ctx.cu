@@ -1716,22 +1716,22 @@ int tdvp_controller_log(tdvp_ctx* ctx, float* out, long long max_rows, long long
   return TDVP_OK;
 }
 
-// mean-squared-error loss and gradient of the controller on B rows of `data` (device or host)
-int controller_grad(tdvp_ctx* ctx, const float* d_data, long long idx0, int B, float* d_grad, float* loss) {
-  float* partial = nullptr;
-  CK(cudaMalloc(&partial, sizeof(float) * mlp_partial_floats(B)));
-  cudaError_t e = launch_mlp_grad(d_data, idx0, B, ctx->d_mlp, partial, d_grad, ctx->st);
+// loss and gradient of controller head `head` on B rows of `data` (device); `partial` holds
+// mlp_partial_floats(B) floats; *loss (host, may be null) synchronises to read the loss
+int controller_grad(tdvp_ctx* ctx, int head, const float* d_data, long long idx0, int B, float* partial, float* d_grad,
+                    float* loss_acc, float* loss) {
+  cudaError_t e = launch_mlp_grad(head, d_data, idx0, B, ctx->d_mlp, partial, d_grad, loss_acc, ctx->st);
   if (e == cudaSuccess && loss) {
     e = cudaMemcpyAsync(loss, d_grad + MLP_NPARAM, sizeof(float), cudaMemcpyDeviceToHost, ctx->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
   }
-  cudaFree(partial);
   if (e != cudaSuccess) return fail(ctx, TDVP_ERR_CUDA, std::string("controller gradient: ") + cudaGetErrorString(e));
   return TDVP_OK;
 }
 
-int tdvp_controller_loss_grad(tdvp_ctx* ctx, const float* X, const float* t, int B, float* loss, float* grad) {
-  if (!ctx || !X || !t || B < 1 || !grad || !loss) return TDVP_ERR_INVALID_ARG;
+int tdvp_controller_loss_grad(tdvp_ctx* ctx, int head, const float* X, const float* t, int B, float* loss,
+                              float* grad) {
+  if (!ctx || !X || !t || B < 1 || !grad || !loss || (head != 0 && head != 1)) return TDVP_ERR_INVALID_ARG;
   if (!ctx->mlp_ready) return fail(ctx, TDVP_ERR_STATE, "controller: set weights first");
   CK(cudaSetDevice(ctx->dev));
   std::vector<float> rows((size_t)B * (MLP_NIN + 1));
@@ -1739,53 +1739,91 @@ int tdvp_controller_loss_grad(tdvp_ctx* ctx, const float* X, const float* t, int
     for (int q = 0; q < MLP_NIN; ++q) rows[(size_t)b * (MLP_NIN + 1) + q] = X[(size_t)b * MLP_NIN + q];
     rows[(size_t)b * (MLP_NIN + 1) + MLP_NIN] = t[b];
   }
-  float *d_rows = nullptr, *d_grad = nullptr;
+  float *d_rows = nullptr, *d_grad = nullptr, *d_part = nullptr;
   const cudaError_t e1 = cudaMalloc(&d_rows, sizeof(float) * rows.size());
   const cudaError_t e2 = cudaMalloc(&d_grad, sizeof(float) * (MLP_NPARAM + 1));
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+  const cudaError_t e3 = cudaMalloc(&d_part, sizeof(float) * mlp_partial_floats(B));
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
     cudaFree(d_rows);
     cudaFree(d_grad);
+    cudaFree(d_part);
     return fail(ctx, TDVP_ERR_OOM, "controller: cudaMalloc of the gradient buffers failed");
   }
   int rc = TDVP_OK;
   if (cudaMemcpyAsync(d_rows, rows.data(), sizeof(float) * rows.size(), cudaMemcpyHostToDevice, ctx->st) != cudaSuccess)
     rc = fail(ctx, TDVP_ERR_CUDA, "controller: upload failed");
-  if (!rc) rc = controller_grad(ctx, d_rows, 0, B, d_grad, loss);
+  if (!rc) rc = controller_grad(ctx, head, d_rows, 0, B, d_part, d_grad, nullptr, loss);
   if (!rc && (cudaMemcpyAsync(grad, d_grad, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
               cudaStreamSynchronize(ctx->st) != cudaSuccess))
     rc = fail(ctx, TDVP_ERR_CUDA, "controller: download failed");
   cudaFree(d_rows);
   cudaFree(d_grad);
+  cudaFree(d_part);
   return rc;
 }
 
+// Two stages on the solve log, each `epochs` passes in mini-batches of `batch`: (1) trunk and the
+// Krylov-dimension head by mean-squared error, (2) the acceptance head alone by the logistic loss
+// (its labels depend on the stage-1 prediction).  Adam moments start from zero in each stage.  The
+// mean loss of each stage's last epoch goes to final_loss[0], final_loss[1]; the host reads them
+// once at the end.
 int tdvp_controller_train(tdvp_ctx* ctx, int epochs, int batch, float lr, float* final_loss) {
   if (!ctx || epochs < 1 || batch < 1 || !(lr > 0)) return TDVP_ERR_INVALID_ARG;
   if (!ctx->mlp_ready) return fail(ctx, TDVP_ERR_STATE, "controller: set (initial) weights first");
   CK(cudaSetDevice(ctx->dev));
   const long long n = log_size(ctx);
   if (n < 1) return fail(ctx, TDVP_ERR_STATE, "controller: the solve log is empty");
-  float* d_grad = nullptr;
-  CK(cudaMalloc(&d_grad, sizeof(float) * (MLP_NPARAM + 1)));
-  float loss = 0.f, acc = 0.f;
-  int rc = TDVP_OK;
-  for (int ep = 0; ep < epochs && !rc; ++ep) {
-    acc = 0.f;
-    int nb = 0;
-    for (long long i0 = 0; i0 < n && !rc; i0 += batch) {
-      const int B = (int)std::min<long long>(batch, n - i0);
-      rc = controller_grad(ctx, ctx->d_log, i0, B, d_grad, &loss);
-      if (rc) break;
-      ++ctx->mlp_step;
-      if (launch_mlp_adam(ctx->d_mlp, d_grad, ctx->d_mlp_m, ctx->d_mlp_v, lr, ctx->mlp_step, ctx->st) != cudaSuccess)
-        rc = fail(ctx, TDVP_ERR_CUDA, "controller: Adam update failed");
-      acc += loss;
-      ++nb;
-    }
-    acc /= std::max(1, nb);
+  const int Bmax = (int)std::min<long long>(batch, n);
+  float *d_grad = nullptr, *d_part = nullptr, *d_loss = nullptr;
+  const cudaError_t e1 = cudaMalloc(&d_grad, sizeof(float) * (MLP_NPARAM + 1));
+  const cudaError_t e2 = cudaMalloc(&d_part, sizeof(float) * mlp_partial_floats(Bmax));
+  const cudaError_t e3 = cudaMalloc(&d_loss, sizeof(float) * 2);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    cudaFree(d_grad);
+    cudaFree(d_part);
+    cudaFree(d_loss);
+    return fail(ctx, TDVP_ERR_OOM, "controller: cudaMalloc of the training buffers failed");
   }
+  int rc = TDVP_OK;
+  long long nbatches = 0;
+  for (int stage = 0; stage < 2 && !rc; ++stage) {
+    const int p0 = stage == 0 ? 0 : MLP_NPARAM_K, p1 = stage == 0 ? MLP_NPARAM_K : MLP_NPARAM;
+    if (cudaMemsetAsync(ctx->d_mlp_m, 0, sizeof(float) * MLP_NPARAM, ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_mlp_v, 0, sizeof(float) * MLP_NPARAM, ctx->st) != cudaSuccess) {
+      rc = fail(ctx, TDVP_ERR_CUDA, "controller: clearing the Adam moments failed");
+      break;
+    }
+    int t = 0;
+    for (int ep = 0; ep < epochs && !rc; ++ep) {
+      if (cudaMemsetAsync(d_loss + stage, 0, sizeof(float), ctx->st) != cudaSuccess) {
+        rc = fail(ctx, TDVP_ERR_CUDA, "controller: loss reset failed");
+        break;
+      }
+      nbatches = 0;
+      for (long long i0 = 0; i0 < n && !rc; i0 += batch) {
+        const int B = (int)std::min<long long>(batch, n - i0);
+        rc = controller_grad(ctx, stage, ctx->d_log, i0, B, d_part, d_grad, d_loss + stage, nullptr);
+        if (rc) break;
+        ++t;
+        if (launch_mlp_adam(ctx->d_mlp, d_grad, ctx->d_mlp_m, ctx->d_mlp_v, lr, t, p0, p1, ctx->st) != cudaSuccess)
+          rc = fail(ctx, TDVP_ERR_CUDA, "controller: Adam update failed");
+        ++nbatches;
+      }
+    }
+    ctx->mlp_step += t;
+  }
+  float h[2] = {0.f, 0.f};
+  if (!rc && (cudaMemcpyAsync(h, d_loss, sizeof(float) * 2, cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+              cudaStreamSynchronize(ctx->st) != cudaSuccess))
+    rc = fail(ctx, TDVP_ERR_CUDA, "controller: reading the loss failed");
   cudaFree(d_grad);
-  if (final_loss) *final_loss = acc;
+  cudaFree(d_part);
+  cudaFree(d_loss);
+  if (final_loss) {
+    final_loss[0] = h[0] / (float)std::max(1LL, nbatches);
+    final_loss[1] = h[1] / (float)std::max(1LL, nbatches);
+  }
+  graph_reset(ctx);        // captured steps hold no copy of the weights, but keep the rule simple
   return rc;
 }
 

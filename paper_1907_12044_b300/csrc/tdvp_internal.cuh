@@ -47,10 +47,12 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
                                   // vector also spreads over 128 SMs
 #define TDVP_QR_THREADS 256
 
-// Learned Krylov controller (kernels_mlp.cu): 8 features -> 64 -> 64 -> 1
+// Learned Krylov controller (kernels_mlp.cu): 8 features -> 64 -> 64 -> two heads, the Krylov
+// dimension (linear) and the acceptance logit of that dimension (logistic)
 #define MLP_NIN 8
 #define MLP_NH 64
-#define MLP_NPARAM (MLP_NIN * MLP_NH + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1)
+#define MLP_NPARAM_K (MLP_NIN * MLP_NH + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1)   // trunk + k head
+#define MLP_NPARAM (MLP_NPARAM_K + MLP_NH + 1)                                              // + acceptance head
 
 __host__ __device__ __forceinline__ zc zmake(double re, double im) { return make_double2(re, im); }
 __host__ __device__ __forceinline__ zc zadd(zc a, zc b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -245,12 +247,14 @@ struct LzArgs {
   int loop_id;
 };
 
-// Controller inference by the first MLP_NH threads of a block; y is returned to every thread.
-// `sm` holds at least 2*MLP_NH + MLP_NIN floats of shared memory.
-__device__ __forceinline__ float mlp_infer(const float* feat, const float* w, float* sm) {
+// Controller inference by the first MLP_NH threads of a block: returns the predicted Krylov
+// dimension y (head 1) to every thread and the acceptance logit of that dimension (head 2) in
+// *za.  `sm` holds at least 3*MLP_NH + MLP_NIN floats of shared memory.
+__device__ __forceinline__ float mlp_infer(const float* feat, const float* w, float* sm, float* za) {
   float* x = sm;
   float* h1 = sm + MLP_NIN;
   float* h2 = h1 + MLP_NH;
+  float* h4 = h2 + MLP_NH;
   const int j = threadIdx.x;
   if (j < MLP_NIN) x[j] = feat[j];
   __syncthreads();
@@ -261,19 +265,24 @@ __device__ __forceinline__ float mlp_infer(const float* feat, const float* w, fl
   }
   __syncthreads();
   const int ow2 = MLP_NIN * MLP_NH + MLP_NH, ob2 = ow2 + MLP_NH * MLP_NH, ow3 = ob2 + MLP_NH;
+  const int ow4 = MLP_NPARAM_K;
   if (j < MLP_NH) {
     float z = w[ob2 + j];
     for (int i = 0; i < MLP_NH; ++i) z = fmaf(h1[i], w[ow2 + i * MLP_NH + j], z);
-    h2[j] = fmaxf(z, 0.f) * w[ow3 + j];
+    const float h = fmaxf(z, 0.f);
+    h2[j] = h * w[ow3 + j];
+    h4[j] = h * w[ow4 + j];
   }
   __syncthreads();
   if (j == 0) {
-    float y = w[ow3 + MLP_NH];
-    for (int i = 0; i < MLP_NH; ++i) y += h2[i];
+    float y = w[ow3 + MLP_NH], a = w[ow4 + MLP_NH];
+    for (int i = 0; i < MLP_NH; ++i) { y += h2[i]; a += h4[i]; }
     x[0] = y;
+    x[1] = a;
   }
   __syncthreads();
   const float y = x[0];
+  *za = x[1];
   __syncthreads();
   return y;
 }
@@ -350,8 +359,12 @@ cudaError_t launch_wapply_env(int which, int site, const SiteDev* sd, const Work
 cudaError_t launch_wapply_tc(int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int max_xy,
                              int n_rows, int pm, cudaStream_t st);
 
-// Controller training (kernels_mlp.cu)
+// Controller training (kernels_mlp.cu).  head 0: mean-squared error of the Krylov dimension
+// (gradient over the trunk and head 1); head 1: logistic loss of the acceptance of the predicted
+// dimension (gradient over head 2 only, the trunk is frozen).  grad[MLP_NPARAM] receives the loss,
+// which is also added to *loss_acc when that is non-null.  The Adam step updates params [p0, p1).
 int mlp_partial_floats(int B);
-cudaError_t launch_mlp_grad(const float* data, long long idx0, int B, const float* w, float* partial, float* grad,
+cudaError_t launch_mlp_grad(int head, const float* data, long long idx0, int B, const float* w, float* partial,
+                            float* grad, float* loss_acc, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* w, const float* g, float* m, float* v, float lr, int t, int p0, int p1,
                             cudaStream_t st);
-cudaError_t launch_mlp_adam(float* w, const float* g, float* m, float* v, float lr, int t, cudaStream_t st);

@@ -55,7 +55,7 @@ class FakeEngine:
         pass
 
     def controller_train(self, epochs=20, batch=1024, lr=1e-3):
-        return 0.5
+        return 0.5, 0.4
 
     def reset_stats(self):
         self._reset()
@@ -142,6 +142,9 @@ def test_bench_line_is_complete_with_a_stand_in_engine(monkeypatch):
     # and controller; the plain arm is FP64 at the tight tolerance, launch by launch, every k
     t, f, pl = line["arms"]["timed"], line["arms"]["fp64"], line["arms"]["plain"]
     assert (t["tol"], t["graph"], t["learned"]) == (f["tol"], f["graph"], f["learned"]) == (1e-8, True, True)
+    a = line["arms"]["adaptive"]
+    assert (a["precision"], a["tol"], a["graph"], a["learned"]) == ("tf32x3", 1e-8, True, False)
+    assert line["controller_gain"]["wall"] > 0
     assert t["precision"] == "tf32x3" and f["precision"] == "fp64"
     assert (pl["precision"], pl["tol"], pl["graph"], pl["learned"], pl["every_k"]) == ("fp64", 1e-12, False, False, True)
     assert set(t["phase_ms"]) == set(PHASES)

@@ -1,9 +1,11 @@
 """Learned Krylov controller: GPU training kernels against the reference MLP, and its gain.
 
-The controller only decides where the convergence tests of a Lanczos exponential start; the
-a-posteriori estimate and tolerance still decide where it stops.  Its gain is measured as the
-number of tridiagonal exponentials (convergence tests) evaluated, against the plain method that
-tests at every k, with the populations unchanged.
+The controller decides where the convergence tests of a Lanczos exponential start (its predicted
+dimension, one later when its acceptance head predicts a failed test there); the a-posteriori
+estimate and tolerance still decide where it stops.  Its gain is counted in tridiagonal
+exponentials (convergence tests) against the library's default rule (tests from the previous
+Krylov dimension of the same site minus 2) and against testing at every k, with the populations
+unchanged.  The bench measures the same comparison in wall time.
 """
 import numpy as np
 import pytest
@@ -21,18 +23,21 @@ import paper_1907_12044_b300 as pkg  # noqa: E402
 from gpu_util import engine_for, rel_pop_err  # noqa: E402
 
 
-def test_gpu_gradients_match_reference_mlp():
+@pytest.mark.parametrize("head", [0, 1])
+def test_gpu_gradients_match_reference_mlp(head):
     eng = pkg.Engine()
     w = mlp.init(5)
     eng.controller_set_weights(w)
-    rng = np.random.default_rng(6)
+    rng = np.random.default_rng(6 + head)
     X = rng.normal(size=(333, mlp.NIN))
-    t = rng.uniform(2, 20, size=333)
-    loss, g = eng.controller_loss_grad(X, t)
-    L_ref, g_ref = mlp.loss_and_grad(w.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64),
-                                     t.astype(np.float32).astype(np.float64))
+    t = rng.uniform(2, 20, size=333) if head == 0 else rng.integers(1, 9, size=333).astype(float)
+    loss, g = eng.controller_loss_grad(X, t, head=head)
+    f32 = lambda a: np.asarray(a).astype(np.float32).astype(np.float64)
+    L_ref, g_ref = mlp.loss_and_grad(f32(w), f32(X), f32(t), head=head)
     assert abs(loss - L_ref) <= 1e-5 * L_ref
     assert np.linalg.norm(g - g_ref) <= 1e-5 * np.linalg.norm(g_ref)
+    if head == 1:
+        assert np.all(g[:mlp.NPARAM - 65] == 0)
     assert np.allclose(eng.controller_get_weights(), w.astype(np.float32))
 
 
@@ -55,21 +60,28 @@ def test_trained_controller_reduces_convergence_tests_without_changing_results()
     tests_plain = plain.stats()["tri_evals"]
     log = plain.controller_log()
     assert log.shape[0] == plain.stats()["krylov_solves"]
-    # train on the GPU (Adam, mean-squared error of k)
+    # train on the GPU (Adam): the dimension head, then the acceptance head
     plain.controller_set_weights(mlp.init(0))
     l0 = plain.controller_train(epochs=1, batch=256, lr=1e-3)
     l1 = plain.controller_train(epochs=150, batch=256, lr=3e-3)
-    print(f"controller loss: first epoch {l0:.3f}, after training {l1:.3f}, samples {log.shape[0]}")
-    assert l1 < 0.3 * l0
+    print(f"controller loss (k MSE, acceptance): first epoch {l0}, after training {l1}, samples {log.shape[0]}")
+    assert l1[0] < 0.3 * l0[0]
+    assert l1[1] < 0.6931                     # better than chance (log 2) on the acceptance labels
     w = plain.controller_get_weights()
-    # the same steps with the trained controller, from the same start
+    # the library's default rule (tests from the previous dimension minus 2), same start
+    default = engine_for(p, D=64)
+    default.reset_stats()
+    P_default = _run(default, 3, pkg.KRYLOV_ADAPTIVE)
+    tests_default = default.stats()["tri_evals"]
+    # the same steps with the trained controller
     learned = engine_for(p, D=64)
-    learned.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1)
     learned.controller_set_weights(w)
     learned.reset_stats()
     P_learned = _run(learned, 3, pkg.KRYLOV_LEARNED)
     tests_learned = learned.stats()["tri_evals"]
-    print(f"convergence tests: plain {tests_plain}, learned {tests_learned}")
+    print(f"convergence tests: every k {tests_plain}, default rule {tests_default}, learned {tests_learned}")
     assert tests_learned < 0.6 * tests_plain
-    for a, b in zip(P_learned, P_plain):
+    assert tests_learned < tests_default
+    for a, b, c in zip(P_learned, P_plain, P_default):
         assert rel_pop_err(a, b) <= 1e-9
+        assert rel_pop_err(c, b) <= 1e-9
