@@ -94,6 +94,11 @@ def parse(argv=None):
     ap.add_argument("--long", type=int, default=0,
                     help="accuracy run instead of the bench line: this many steps of the timed arm and "
                          "of the plain FP64 arm from the same start, Eq. error and max |dP| every 100 steps")
+    ap.add_argument("--lz-chunks", type=int, default=None, help="chunk cap per Lanczos vector (library option)")
+    ap.add_argument("--fused", type=int, default=1, help="0: four Lanczos launches per iteration instead of one")
+    ap.add_argument("--batched-kmax", type=int, default=48, help="Krylov cap of the batched section")
+    ap.add_argument("--long-dir", default=os.path.join(ROOT, "gpurun_out"),
+                    help="where the long run writes its population checkpoints")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args(argv)
 
@@ -186,6 +191,7 @@ ARMS = {
     "adaptive": (None, "tol", True, False, False),
     "fp64": ("fp64", "tol", True, True, False),
     "plain": ("fp64", "plain_tol", False, False, True),
+    "fp64ref": ("fp64", "plain_tol", True, False, False),
 }
 
 
@@ -209,6 +215,9 @@ def timed_run(args, p, name, world, dev, stream, flush):
     P = PREC[prec]
     eng = pkg.Engine(n_realisations=1, stream=stream.cuda_stream)
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
+    if args.lz_chunks:
+        eng.set_option(pkg.OPT_LANCZOS_CHUNKS, args.lz_chunks)
+    eng.set_option(pkg.OPT_FUSED_LANCZOS, args.fused)
     eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1 if every else 0)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
@@ -446,8 +455,11 @@ def run_batched(args, R, rank=0, world=1):
     steps = args.batched_steps or args.steps
     tol = args.tol
     P = PREC[args.precision]
-    eng = pkg.Engine(n_realisations=len(mine))
+    eng = pkg.Engine(n_realisations=len(mine), kmax=args.batched_kmax)
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
+    eng.set_option(pkg.OPT_FUSED_LANCZOS, args.fused)
+    if args.lz_chunks:
+        eng.set_option(pkg.OPT_LANCZOS_CHUNKS, args.lz_chunks)
     for q, r in enumerate(mine):
         p = wl.disorder_realisation(base, r)
         eng.build_mpo(q, p)
@@ -667,14 +679,17 @@ def run_reference(args, world):
 
 
 def run_long(args):
-    """Accuracy of the timed arm over a long run: `--long` steps of the timed arm and of the plain
-    FP64 arm from the same product start, Eq. error and max |dP| every 100 steps (no timing)."""
+    """Accuracy of the timed arm over a long run: `--long` steps of the timed arm and of the FP64
+    reference (FP64 matvecs at --plain-tol, CUDA-graph steps) from the same product start; Eq.
+    error and max |dP| every 100 steps (no timing).  Populations are written to
+    <--long-dir>/long_<arm>.npy every 100 steps, so a run cut short still leaves its prefix."""
     import torch
     import paper_1907_12044_b300 as pkg
     p, cfg = workload(args)
     torch.cuda.set_device(0)
+    os.makedirs(args.long_dir, exist_ok=True)
     res = {}
-    for name in ("mixed", "plain"):
+    for name in ("mixed", "fp64ref"):
         prec, tol, graph, learned, every = arm_setup(args, name)
         eng = pkg.Engine(n_realisations=1)
         eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
@@ -691,24 +706,30 @@ def run_long(args):
         mode = pkg.KRYLOV_ADAPTIVE
         if learned:
             eng.controller_logging(0)
-            train_controller(eng)
+            train_controller(eng, samples=eng.stats()["krylov_solves"])
             mode = pkg.KRYLOV_LEARNED
         if graph:
             eng.set_option(pkg.OPT_GRAPH, 1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        path = os.path.join(args.long_dir, f"long_{name}.npy")
         while len(pops) <= args.long:
             eng.step(args.dt, 1, precision=PREC[prec], krylov_mode=mode, tol=tol)
             pops.append(eng.observables(0)[0])
+            if len(pops) % 100 == 1:
+                np.save(path, np.array(pops))
+        np.save(path, np.array(pops))
         res[name] = (np.array(pops), time.perf_counter() - t0, eng.stats())
         eng.close()
-    P, Pref = res["mixed"][0], res["plain"][0]
+    P, Pref = res["mixed"][0], res["fp64ref"][0]
     rows = []
     for s in list(range(100, args.long + 1, 100)) or [args.long]:
         e, m = pop_error(args.dt, P[:s + 1], Pref[:s + 1])
         rows.append({"step": s, "t_fs": s * args.dt, "eq_error": sig(e, 3), "max_abs_dP": sig(m, 3)})
     return {"long_run": args.long, "config": cfg, "precision": args.precision, "tol": args.tol,
-            "plain_tol": args.plain_tol, "host_seconds": {k: sig(v[1]) for k, v in res.items()},
+            "reference": f"fp64, tol {args.plain_tol:g}, CUDA-graph steps",
+            "host_seconds": {k: sig(v[1]) for k, v in res.items()},
+            "krylov_mean": {k: sig(v[2]["krylov_dim_sum"] / max(v[2]["krylov_solves"], 1), 3) for k, v in res.items()},
             "errors": rows, "final_pops_mixed": [sig(x, 6) for x in P[-1]],
             "final_pops_fp64": [sig(x, 6) for x in Pref[-1]]}
 

@@ -266,9 +266,11 @@ int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* c
  * Features of a local exponential, known after its first Lanczos step: log10(1 + |tau| ||H v||),
  * kind (site 0 / bond 1), previous k of the same site and kind / 32, site / (N-1),
  * log2(vector length) / 20, log10|tau| / 4, -log10(tol) / 12, log10(1 + |tau| |alpha_0|).
- * With TDVP_KRYLOV_LEARNED the Lanczos iterations run without any convergence test up to kp (kp + 1
- * when a < 0); from there the adaptive test (same estimate, same tolerance) decides where the solve
- * stops, so a wrong prediction costs iterations or tests, never accuracy. */
+ * With TDVP_KRYLOV_LEARNED the Lanczos iterations run without any convergence test up to kp, or up
+ * to kp - 1 when a >= 0 (a predicted pass at kp means the solve may have converged earlier, and an
+ * iteration past convergence costs a whole matvec while a failed test costs one tridiagonal
+ * exponential); from there the adaptive test (same estimate, same tolerance) decides where the
+ * solve stops, so a wrong prediction costs iterations or tests, never accuracy. */
 int tdvp_controller_set_weights(tdvp_ctx* ctx, const float* w, int n);   /* n = 4866, host array */
 int tdvp_controller_get_weights(tdvp_ctx* ctx, float* w, int n);
 /* Log every finished exponential (features, k) into a device buffer of `capacity` rows; 0 stops. */
@@ -327,7 +329,10 @@ int tdvp_autotune(tdvp_ctx* ctx);
  *     the first group barrier of every fused Lanczos iteration wait for one block more than the
  *     launch has (a participant that never arrives) and limits every wait of that kernel to t, so
  *     the waits run out and the step returns TDVP_ERR_DEVICE_TIMEOUT (nothing faults or hangs; the
- *     context stays usable, the state must be initialised again).  0 (default) = off. */
+ *     context stays usable, the state must be initialised again).  0 (default) = off.
+ *   TDVP_OPT_LANCZOS_CHUNKS: at most this many chunks (thread blocks) per Lanczos vector, 1..148
+ *     (default 148); fewer chunks make the fused iteration's partial-sum reductions and group
+ *     barriers shorter.  Results depend on it only through the summation order. */
 #define TDVP_OPT_RANK_RTOL         1
 #define TDVP_OPT_KRYLOV_CHECK_ALL  2
 #define TDVP_OPT_QR_KERNEL         3
@@ -335,6 +340,7 @@ int tdvp_autotune(tdvp_ctx* ctx);
 #define TDVP_OPT_PDL               5
 #define TDVP_OPT_FUSED_LANCZOS     6
 #define TDVP_OPT_STALL_TEST        7
+#define TDVP_OPT_LANCZOS_CHUNKS    8
 int tdvp_set_option(tdvp_ctx* ctx, int option, double value);
 
 const char* tdvp_last_error(const tdvp_ctx* ctx);

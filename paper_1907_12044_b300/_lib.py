@@ -63,6 +63,7 @@ OPT_GRAPH = 4
 OPT_PDL = 5
 OPT_FUSED_LANCZOS = 6
 OPT_STALL_TEST = 7
+OPT_LANCZOS_CHUNKS = 8
 
 
 class StatsC(C.Structure):

@@ -609,10 +609,12 @@ __device__ void tri_step(const LzArgs& a, int r, int j, double* sh, zc* c, doubl
       float za;
       const float y = mlp_infer(ks->feat, a.mlp, reinterpret_cast<float*>(sh), &za);
       if (threadIdx.x == 0) {
-        // the dimension the controller predicts; when its acceptance head predicts that the
-        // residual test fails there, the first test is made one dimension later
+        // the dimension the controller predicts.  An iteration past the converged dimension costs
+        // a whole matvec, a failed test only a tridiagonal exponential, so when the acceptance
+        // head predicts that the test at kp passes (the solve may have converged earlier) the
+        // first test is made one dimension before kp
         int kp = (int)fminf(fmaxf(floorf(y), 1.f), 126.f);
-        if (za < 0.f) kp += 1;
+        if (za >= 0.f && kp > 1) kp -= 1;
         ks->kpred = kp;
       }
       __syncthreads();

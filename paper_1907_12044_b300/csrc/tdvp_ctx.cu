@@ -62,6 +62,7 @@ struct tdvp_ctx {
   int check_every = 0;        // 1: test Lanczos convergence at every k (else from the last k - 2 on)
   int fused_lz = 1;           // TDVP_OPT_FUSED_LANCZOS: one cooperative launch per Lanczos iteration
   double stall_test = 0.0;    // TDVP_OPT_STALL_TEST: > 0 = failure-path test with this wait limit (s)
+  int lz_chunks = TDVP_MAX_VEC_BLOCKS;   // TDVP_OPT_LANCZOS_CHUNKS: chunk cap per Lanczos vector
   int lz_cap = 0;             // co-resident blocks of the fused iteration kernel
   // per-launch timing
   // learned Krylov controller
@@ -907,8 +908,9 @@ int nblk_for(long long n, int cap) {
 
 // Lanczos arguments shared by the launch-by-launch and the graph-captured exponential.  The fused
 // iteration kernel runs when every realisation's chunks fit co-resident (the chunk count per
-// vector is capped at capacity / R for that); the mixed precisions let the Lanczos kernels write
-// each new Krylov vector as the packed tensor-core operand of the next matvec.
+// vector is capped at capacity / R for that) and that cap leaves at least 8 chunks per vector; the
+// mixed precisions let the Lanczos kernels write each new Krylov vector as the packed
+// tensor-core operand of the next matvec.
 LzArgs lz_args(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, double theta, double tol,
                int prec, bool* fused) {
   const Dims m = maxdims(ctx, site, v);
@@ -916,8 +918,11 @@ LzArgs lz_args(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int d
   LzArgs a{};
   a.sd = v.sd; a.wk = v.wk; a.R = v.R; a.N_sites = ctx->N; a.site = site; a.kind = kind;
   a.src = src; a.dst = dst; a.theta = theta; a.tol = tol; a.kmax = ctx->kmax;
-  *fused = ctx->fused_lz && ctx->lz_cap >= v.R;
-  a.bcap = *fused ? std::min(TDVP_MAX_VEC_BLOCKS, ctx->lz_cap / v.R) : TDVP_MAX_VEC_BLOCKS;
+  // fused only while every vector keeps at least 8 chunks (or all it needs) under the
+  // co-residency cap: with many realisations one block per vector would leave most SMs idle
+  const int want = nblk_for(n, ctx->lz_chunks);
+  *fused = ctx->fused_lz && ctx->lz_cap / v.R >= std::min(8, want);
+  a.bcap = *fused ? std::min(ctx->lz_chunks, ctx->lz_cap / v.R) : ctx->lz_chunks;
   a.nblk = nblk_for(n, a.bcap);
   a.pack_pm = prec != TDVP_PREC_FP64 ? tc_mode(prec) : -1;
   a.stall = ctx->stall_test > 0.0 ? 1 : 0;
@@ -1941,6 +1946,14 @@ int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
       graph_reset(ctx);
       ctx->fused_lz = value != 0.0 ? 1 : 0;
       return TDVP_OK;
+    case TDVP_OPT_LANCZOS_CHUNKS: {
+      const int c = (int)value;
+      if ((double)c != value || c < 1 || c > TDVP_MAX_VEC_BLOCKS)
+        return fail(ctx, TDVP_ERR_INVALID_ARG, "Lanczos chunks: an integer in [1, 148]");
+      graph_reset(ctx);
+      ctx->lz_chunks = c;
+      return TDVP_OK;
+    }
     case TDVP_OPT_STALL_TEST:
       if (!(value >= 0.0 && value <= 1.0)) return fail(ctx, TDVP_ERR_INVALID_ARG, "stall test: wait limit in [0, 1] s");
       graph_reset(ctx);

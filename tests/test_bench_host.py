@@ -181,3 +181,13 @@ def test_realisation_shards_cover_every_index_once():
         assert got == list(range(R))
         sizes = [len(bench.shard(R, rank, world)) for rank in range(world)]
         assert max(sizes) - min(sizes) <= 1
+
+
+def test_long_accuracy_run_with_a_stand_in_engine(monkeypatch, tmp_path):
+    _patch(monkeypatch)
+    args = bench.parse(["--long", "250", "--warmup", "1", "--long-dir", str(tmp_path)])
+    out = json.loads(json.dumps(bench.run_long(args)))
+    assert [r["step"] for r in out["errors"]] == [100, 200]
+    assert all(r["max_abs_dP"] > 0 for r in out["errors"])
+    assert np.load(tmp_path / "long_mixed.npy").shape == (251, 7)
+    assert np.load(tmp_path / "long_fp64ref.npy").shape == (251, 7)
