@@ -97,6 +97,10 @@ def parse(argv=None):
     ap.add_argument("--lz-chunks", type=int, default=None, help="chunk cap per Lanczos vector (library option)")
     ap.add_argument("--fused", type=int, default=1, help="0: four Lanczos launches per iteration instead of one")
     ap.add_argument("--batched-kmax", type=int, default=48, help="Krylov cap of the batched section")
+    ap.add_argument("--batched-compare", action="store_true",
+                    help="also time the batched steps without the learned controller")
+    ap.add_argument("--batched-prof", action="store_true",
+                    help="per-kernel breakdown of one more batched step (launch by launch, CUDA events)")
     ap.add_argument("--long-dir", default=os.path.join(ROOT, "gpurun_out"),
                     help="where the long run writes its population checkpoints")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
@@ -495,6 +499,39 @@ def run_batched(args, R, rank=0, world=1):
     ms = e0.elapsed_time(e1)
     st = eng.stats()
     pops = {r: eng.observables(q)[0].tolist() for q, r in enumerate(mine)}
+    cmp = None
+    if args.batched_compare and learned:
+        # the following steps without the controller (the library's default test rule), timed
+        # the same way: the controller's wall-time gain on the batched sweep
+        eng.step(args.dt, 1, precision=P, krylov_mode=pkg.KRYLOV_ADAPTIVE, tol=tol)   # capture
+        torch.cuda.synchronize()
+        eng.reset_stats()
+        e0.record(stream)
+        eng.step(args.dt, steps, precision=P, krylov_mode=pkg.KRYLOV_ADAPTIVE, tol=tol)
+        e1.record(stream)
+        e1.synchronize()
+        ms_ad = e0.elapsed_time(e1)
+        sa = eng.stats()
+        cmp = {"adaptive_ms_per_step": sig(ms_ad / steps), "learned_ms_per_step": sig(ms / steps),
+               "wall_gain": sig(ms_ad / ms), "tri_evals_per_solve_adaptive":
+               sig(sa["tri_evals"] / max(sa["krylov_solves"], 1), 3)}
+    prof = None
+    if args.batched_prof:
+        # per-kernel CUDA-event breakdown of one more (untimed) step, launch by launch
+        eng.set_option(pkg.OPT_GRAPH, 0)
+        eng.reset_stats()
+        eng.set_profiling(True)
+        eng.step(args.dt, 1, precision=P, krylov_mode=mode, tol=tol)
+        eng.set_profiling(False)
+        pr = eng.stats()
+        pr["lz_alg_bytes"] = lz_alg_bytes(pr)
+        cat_ms = pr["prof_ms"]
+        ranked = sorted((c for c in ROOF_KERNELS if cat_ms.get(c, 0) > 0), key=lambda c: -cat_ms[c])
+        prof = {"phase_ms": {k: sig(v, 3) for k, v in pr["prof_phase_ms"].items() if v > 0},
+                "kernel_ms": {k: sig(v, 3) for k, v in cat_ms.items() if v > 0},
+                "roofline": {c: {k: v for k, v in roofline(pr, c, args.precision).items()
+                                 if k in ("achieved", "peak", "unit", "frac", "avg_launch_us", "bound", "launches")}
+                             for c in ranked}}
     eng.close()
     ms_max = max_over_ranks(ms, world)
     N = len(base.chain())
@@ -507,7 +544,8 @@ def run_batched(args, R, rank=0, world=1):
             "krylov_mean": sig(st["krylov_dim_sum"] / max(st["krylov_solves"], 1), 3),
             "tri_evals_per_solve": sig(st["tri_evals"] / max(st["krylov_solves"], 1), 3),
             "execution": "CUDA-graph steps" if graph else "launch by launch",
-            "sharding": f"realisation r on rank r mod {world}" if world > 1 else "one GPU"}, pops
+            "sharding": f"realisation r on rank r mod {world}" if world > 1 else "one GPU",
+            "profile": prof, "controller_vs_default": cmp}, pops
 
 
 def gather_pops(pops, rank, world):
