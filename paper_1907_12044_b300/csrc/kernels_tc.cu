@@ -751,9 +751,13 @@ int tc_splits(int tiles, int R, int maxK) {
 }
 
 cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
-                           int maxN, int maxK, int pm, cudaStream_t st) {
+                           int maxN, int maxK, int pm, cudaStream_t st, int S_force) {
   const int tn = cdivh(maxN, BN), tm = cdivh(maxM, BM);
-  const int S = tc_splits(tn * tm, R, maxK);
+  int S = tc_splits(tn * tm, R, maxK);
+  if (S_force > 0) {
+    if (S_force > MAX_SPLIT || (S_force & (S_force - 1)) || S_force > cdivh(maxK, BK)) return cudaErrorInvalidValue;
+    S = S_force;
+  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   if (S > 1) {

@@ -57,6 +57,8 @@ struct tdvp_ctx {
   double rank_rtol = kRankRtolDefault;
   // (R, m, n) -> QR kernel: B > 0 grid kernel with B blocks per realisation, -C cluster kernel
   std::map<std::tuple<int, int, int>, int> qr_tuned;
+  // (op, R, M, N, K) of a Lanczos-matvec tensor-core GEMM -> CTAs per output tile along K
+  std::map<std::tuple<int, int, int, int, int>, int> tc_tuned;
   int qr_force = -1;          // TDVP_OPT_QR_KERNEL
   bool cqr_ok[17] = {};       // cluster size launchable with the largest shared-memory slab
   int check_every = 0;        // 1: test Lanczos convergence at every k (else from the last k - 2 on)
@@ -559,6 +561,12 @@ int tc_mode(int P) {
   }
 }
 
+// autotuned split-K of a tensor-core GEMM shape (0: the heuristic)
+int tc_split_pick(tdvp_ctx* ctx, int op, int R, int M, int N, int K) {
+  auto it = ctx->tc_tuned.find(std::make_tuple(op, R, M, N, K));
+  return it == ctx->tc_tuned.end() ? 0 : it->second;
+}
+
 // algorithmic real flops of one batched GEMM launch (8 per complex multiply-add)
 double gemm_flops(tdvp_ctx* ctx, const Views& v, int op, int site) {
   double f = 0;
@@ -766,9 +774,11 @@ int matvec_site_tc(tdvp_ctx* ctx, const Views& v, int i, int pm, bool prepacked 
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   if (!prepacked) LAUNCH(launch_pack_x(0, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dl * d * m.Dr, pm, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, m.Dl, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV1, i, v.sd, v.wk, v.R, ctx->N, Wl * m.Dl, d * m.Dr, m.Dl, pm, ctx->st,
+                                      tc_split_pick(ctx, TC_MV1, v.R, Wl * m.Dl, d * m.Dr, m.Dl)));
   LAUNCHC(TDVP_CAT_WAPPLY, launch_wapply_tc(i, v.sd, v.wk, v.R, ctx->N, m.Dl * m.Dr, Wr * d, pm, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV3, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, Wr * m.Dr, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_MV3, i, v.sd, v.wk, v.R, ctx->N, m.Dl * d, m.Dr, Wr * m.Dr, pm, ctx->st,
+                                      tc_split_pick(ctx, TC_MV3, v.R, m.Dl * d, m.Dr, Wr * m.Dr)));
   if (ctx->prof) {
     double f = 0;
     for (int r = v.r0; r < v.r0 + v.R; ++r) {
@@ -785,8 +795,10 @@ int matvec_bond_tc(tdvp_ctx* ctx, const Views& v, int i, int pm, bool prepacked 
   const Dims m = maxdims(ctx, i, v);
   const int Wb = ctx->Wb[i + 1];
   if (!prepacked) LAUNCH(launch_pack_x(1, i, v.sd, v.wk, v.R, ctx->N, (long long)m.Dr * m.Dr, pm, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z1, i, v.sd, v.wk, v.R, ctx->N, Wb * m.Dr, m.Dr, m.Dr, pm, ctx->st));
-  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, m.Dr, Wb * m.Dr, pm, ctx->st));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z1, i, v.sd, v.wk, v.R, ctx->N, Wb * m.Dr, m.Dr, m.Dr, pm, ctx->st,
+                                      tc_split_pick(ctx, TC_Z1, v.R, Wb * m.Dr, m.Dr, m.Dr)));
+  LAUNCHC(TDVP_CAT_TC, launch_tc_gemm(TC_Z3, i, v.sd, v.wk, v.R, ctx->N, m.Dr, m.Dr, Wb * m.Dr, pm, ctx->st,
+                                      tc_split_pick(ctx, TC_Z3, v.R, m.Dr, m.Dr, Wb * m.Dr)));
   if (ctx->prof) {
     double f = 0;
     for (int r = v.r0; r < v.r0 + v.R; ++r) {
@@ -1918,6 +1930,46 @@ int tdvp_autotune(tdvp_ctx* ctx) {
         if (total < best) { best = total; best_mode = mode; }
       }
       ctx->qr_tuned[key] = best_mode;
+    }
+  }
+  // the tensor-core GEMMs of the Lanczos matvecs: for every distinct (op, M, N, K) of the chain,
+  // time each split-K cluster size on the work buffers (operand contents do not change the time;
+  // the outputs are scratch: T1, the packed T of the bond matvec, w) in the TF32x3 mode, and keep
+  // the fastest.  The solves are marked unfinished so that the stages do not skip themselves; the
+  // next exponential's start resets that mark.
+  if (ctx->h_work[0].tc_x) {
+    for (int r = 0; r < ctx->R; ++r)
+      CK(cudaMemsetAsync(&ctx->h_work[r].ks->done, 0, sizeof(int), ctx->st));
+    for (int i = 0; i < ctx->N; ++i) {
+      const Dims m = maxdims(ctx, i, v);
+      const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
+      struct Shape { int op, M, N, K; };
+      std::vector<Shape> shapes = {{TC_MV1, Wl * m.Dl, d * m.Dr, m.Dl}, {TC_MV3, m.Dl * d, m.Dr, Wr * m.Dr}};
+      if (i < ctx->N - 1) {
+        shapes.push_back({TC_Z1, Wr * m.Dr, m.Dr, m.Dr});
+        shapes.push_back({TC_Z3, m.Dr, m.Dr, Wr * m.Dr});
+      }
+      for (const Shape& sh : shapes) {
+        const auto key = std::make_tuple(sh.op, ctx->R, sh.M, sh.N, sh.K);
+        if (ctx->tc_tuned.count(key)) continue;
+        int best_S = 0;
+        float best = 1e30f;
+        for (int S : {1, 2, 4, 8}) {
+          if (S > (sh.K + 31) / 32) break;
+          float tmin = 1e30f;
+          for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaEventRecord(e0, ctx->st));
+            CK(launch_tc_gemm(sh.op, i, v.sd, v.wk, v.R, ctx->N, sh.M, sh.N, sh.K, TC_PM_SPLIT, ctx->st, S));
+            CK(cudaEventRecord(e1, ctx->st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tmin = std::min(tmin, ms);
+          }
+          if (tmin < best) { best = tmin; best_S = S; }
+        }
+        ctx->tc_tuned[key] = best_S;
+      }
     }
   }
   cudaEventDestroy(e0);

@@ -336,8 +336,10 @@ cudaError_t tc_setup();
 // maxM x maxN output over maxK bound every realisation's product; long-K products are split over
 // a thread-block cluster (tc_splits)
 int tc_splits(int tiles, int R, int maxK);
+// S_force > 0: that many CTAs per output tile along K (a power of two <= 8, at most the K tiles),
+// else the tc_splits heuristic
 cudaError_t launch_tc_gemm(int op, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites, int maxM,
-                           int maxN, int maxK, int pm, cudaStream_t st);
+                           int maxN, int maxK, int pm, cudaStream_t st, int S_force = 0);
 cudaError_t launch_pack_env(int which, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,
                             long long max_elems, int pm, cudaStream_t st);
 cudaError_t launch_pack_x(int kind, int site, const SiteDev* sd, const WorkDev* wk, int R, int N_sites,

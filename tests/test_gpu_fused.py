@@ -68,3 +68,18 @@ def test_stall_test_reports_device_timeout_and_the_context_stays_usable():
     tdvp_ps_step(st, 10.0)
     assert rel_pop_err(eng.observables(0)[0], populations(st, p)) <= 1e-10
     eng.close()
+
+
+def test_autotuned_tensor_core_splits_keep_mixed_steps_on_the_oracle():
+    """The autotuner's split-K choice for every Lanczos-matvec GEMM shape changes only the FP32
+    summation order: two TF32x3 steps stay on the FP64 oracle within the mixed-precision bound."""
+    p = wl.fmo_sized()
+    eng = engine_for(p, D=64)
+    eng.set_option(pkg.OPT_RANK_RTOL, 1e-6)
+    eng.autotune()
+    st = TDVPState.start(p, D=64)
+    for _ in range(2):
+        eng.step(10.0, precision=pkg.PREC_TF32X3, tol=1e-10)
+        tdvp_ps_step(st, 10.0, rank_rtol=1e-6)
+    assert rel_pop_err(eng.observables(0)[0], populations(st, p)) <= 1e-5
+    eng.close()
