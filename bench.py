@@ -315,9 +315,11 @@ ROOF_KERNELS = {"qr": ("bqr_kernel/cqr_kernel (FP64 gauge-shift QR)", "alu"),
                 "lanczos_vec": ("lz_* (FP64 Lanczos vectors)", "hbm")}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel as it is built now, on the bench's shapes: (bytes, capture).  A kernel missing here has no
-# capture of its current form, and its `traffic` is null.
-TRAFFIC = {}
+# kernel as it is built now, on the bench's workload (three launches each, cold caches, launch by
+# launch): (bytes, what was captured).  A kernel missing here has no capture of its current form,
+# and its `traffic` is null.
+TRAFFIC = {"lanczos_vec": (2.099e6, "lz_iter, mean of 3 launches at a 64x10x64 site"),
+           "tc_gemm": (0.703e6, "tc_cgemm_kernel<TF32x3>, mean of 3 launches (H0 stages, one finished solve)")}
 
 
 def peaks():
