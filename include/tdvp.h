@@ -213,7 +213,8 @@ typedef struct {
    * algorithmic bytes of the Lanczos vector kernels (TDVP_CAT_LZVEC): per solve of dimension k
    * on vectors of n complex elements, 16 n (2 k (k+1) + 10 k + 5) -- iteration j reads
    * V_0..V_j four times (dot and update of each of the two Gram-Schmidt passes) and moves w,
-   * V_{j+1} and x nine times; start and combination add k + 5 vectors. */
+   * V_{j+1} and x nine times; start and combination add k + 5 vectors -- and their FP64 flops,
+   * 16 n k (k+1) per solve (the two passes). */
   double prof_ms[TDVP_NCAT];
   long long prof_launches[TDVP_NCAT];
   double prof_flops[TDVP_NCAT];

@@ -280,7 +280,7 @@ int tdvp_create(tdvp_ctx** out, int device, void* cuda_stream, int n_realisation
   if (tc_setup() != cudaSuccess) { tdvp_destroy(ctx); return TDVP_ERR_CUDA; }
   if (cqr_setup(device) != cudaSuccess) { tdvp_destroy(ctx); return TDVP_ERR_CUDA; }
   for (int C : {1, 2, 4, 8, 16}) ctx->cqr_ok[C] = cqr_max_clusters(C, TDVP_CQR_SMEM_MAX) >= 1;
-  if (ctx->qr_cap < ctx->R) { tdvp_destroy(ctx); return TDVP_ERR_INVALID_ARG; }
+  if (ctx->qr_cap < 1) { tdvp_destroy(ctx); return TDVP_ERR_CUDA; }
   *out = ctx;
   return TDVP_OK;
 }
@@ -877,9 +877,16 @@ int run_qr(tdvp_ctx* ctx, const Views& v, int dir, int i, int m, int n, int mode
   }
   const int gdir = dir == 4 ? 0 : dir;      // the grid kernel's left-to-right shape lives in scratch
   if (dir == 0) CK(launch_transpose_site(1, i, v.sd, v.wk, v.R, ctx->N, m, n, ctx->st));
-  CK(launch_row_qr(gdir, i, v.sd, v.wk, v.R, ctx->N, mode, rtol, dn, dm, ctx->st));
+  // the cooperative grid kernel needs every block it launches co-resident: realisations go in
+  // groups of at most qr_cap / B per launch
+  const int G = std::max(1, ctx->qr_cap / std::max(1, mode));
+  for (int r0 = 0; r0 < v.R; r0 += G) {
+    const int Rg = std::min(G, v.R - r0);
+    CK(launch_row_qr(gdir, i, v.sd + (size_t)r0 * ctx->N, v.wk + r0, Rg, ctx->N, mode, rtol, dn, dm, ctx->st));
+    ctx->stats.kernel_launches++;
+  }
   if (dir == 0) CK(launch_transpose_site(0, i, v.sd, v.wk, v.R, ctx->N, m, n, ctx->st));
-  ctx->stats.kernel_launches += dir == 0 ? 3 : 1;
+  ctx->stats.kernel_launches += dir == 0 ? 2 : 0;
   return TDVP_OK;
 }
 
@@ -1086,6 +1093,9 @@ int expm(tdvp_ctx* ctx, const Views& v, int kind, int site, int src, int dst, do
       const auto& bd = ctx->rh[v.r0 + r].bd;
       const double nr = kind == 0 ? (double)bd[site] * ctx->d[site] * bd[site + 1] : (double)bd[site + 1] * bd[site + 1];
       ctx->stats.prof_bytes[TDVP_CAT_LZVEC] += 16.0 * nr * (2.0 * k * (k + 1) + 10.0 * k + 5.0);
+      // FP64 flops of the two classical Gram-Schmidt passes (dot and update against V_0..V_j in
+      // each, 8 real flops per complex multiply-add): 32 n (j + 1) at iteration j
+      ctx->stats.prof_flops[TDVP_CAT_LZVEC] += 16.0 * nr * k * (k + 1.0);
     }
     ctx->stats.krylov_dim_sum += k;
     ctx->stats.krylov_dim_max = std::max(ctx->stats.krylov_dim_max, k);
@@ -1889,7 +1899,7 @@ int tdvp_autotune(tdvp_ctx* ctx) {
       }
       std::vector<int> cands;
       for (int B : {1, 2, 4, 8, 16, 24, 32, 48, 64, 80, 96, 128, 148})
-        if (B <= mm && (long long)B * ctx->R <= ctx->qr_cap) cands.push_back(B);
+        if (B <= mm && B <= ctx->qr_cap) cands.push_back(B);
       for (int C : {1, 2, 4, 8, 16})
         if (cqr_fits(ctx, C, mm, nn)) cands.push_back(-C);
       int best_mode = qr_mode(ctx, ctx->R, mm, nn);
