@@ -103,6 +103,9 @@ def parse(argv=None):
                     help="also time the batched steps without the learned controller")
     ap.add_argument("--batched-prof", action="store_true",
                     help="per-kernel breakdown of one more batched step (launch by launch, CUDA events)")
+    ap.add_argument("--long-precisions", default=None,
+                    help="comma-separated precisions for the long run (default: --precision), each against "
+                         "the same FP64 reference")
     ap.add_argument("--long-dir", default=os.path.join(ROOT, "gpurun_out"),
                     help="where the long run writes its population checkpoints")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
@@ -749,18 +752,19 @@ def run_reference(args, world):
 
 
 def run_long(args):
-    """Accuracy of the timed arm over a long run: `--long` steps of the timed arm and of the FP64
-    reference (FP64 matvecs at --plain-tol, CUDA-graph steps) from the same product start; Eq.
-    error and max |dP| every 100 steps (no timing).  Populations are written to
-    <--long-dir>/long_<arm>.npy every 100 steps, so a run cut short still leaves its prefix."""
+    """Accuracy of the timed arm over a long run: `--long` steps of the timed arm (for every
+    precision of --long-precisions) and of the FP64 reference (FP64 matvecs at --plain-tol,
+    CUDA-graph steps) from the same product start; Eq. error and max |dP| every 100 steps (no
+    timing).  Populations are written to <--long-dir>/long_<arm>.npy every 100 steps, so a run cut
+    short still leaves its prefix."""
     import torch
     import paper_1907_12044_b300 as pkg
     p, cfg = workload(args)
     torch.cuda.set_device(0)
     os.makedirs(args.long_dir, exist_ok=True)
-    res = {}
-    for name in ("mixed", "fp64ref"):
-        prec, tol, graph, learned, every = arm_setup(args, name)
+    precs = (args.long_precisions or args.precision).split(",")
+
+    def run_arm(name, prec, tol, graph, learned, every):
         eng = pkg.Engine(n_realisations=1)
         eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
         eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1 if every else 0)
@@ -789,19 +793,28 @@ def run_long(args):
             if len(pops) % 100 == 1:
                 np.save(path, np.array(pops))
         np.save(path, np.array(pops))
-        res[name] = (np.array(pops), time.perf_counter() - t0, eng.stats())
+        st = eng.stats()
         eng.close()
-    P, Pref = res["mixed"][0], res["fp64ref"][0]
-    rows = []
-    for s in list(range(100, args.long + 1, 100)) or [args.long]:
-        e, m = pop_error(args.dt, P[:s + 1], Pref[:s + 1])
-        rows.append({"step": s, "t_fs": s * args.dt, "eq_error": sig(e, 3), "max_abs_dP": sig(m, 3)})
-    return {"long_run": args.long, "config": cfg, "precision": args.precision, "tol": args.tol,
-            "reference": f"fp64, tol {args.plain_tol:g}, CUDA-graph steps",
-            "host_seconds": {k: sig(v[1]) for k, v in res.items()},
-            "krylov_mean": {k: sig(v[2]["krylov_dim_sum"] / max(v[2]["krylov_solves"], 1), 3) for k, v in res.items()},
-            "errors": rows, "final_pops_mixed": [sig(x, 6) for x in P[-1]],
-            "final_pops_fp64": [sig(x, 6) for x in Pref[-1]]}
+        return np.array(pops), time.perf_counter() - t0, st
+
+    ref = run_arm("fp64ref", *arm_setup(args, "fp64ref"))
+    out = {"long_run": args.long, "config": cfg, "tol": args.tol,
+           "reference": f"fp64, tol {args.plain_tol:g}, CUDA-graph steps",
+           "reference_seconds": sig(ref[1]), "final_pops_fp64": [sig(x, 6) for x in ref[0][-1]], "arms": {}}
+    for prec in precs:
+        _, tol, graph, learned, every = arm_setup(args, "mixed")
+        P, secs, st = run_arm("mixed" if len(precs) == 1 else prec, prec, tol, graph, learned, every)
+        rows = []
+        for s in list(range(100, args.long + 1, 100)) or [args.long]:
+            e, m = pop_error(args.dt, P[:s + 1], ref[0][:s + 1])
+            rows.append({"step": s, "t_fs": s * args.dt, "eq_error": sig(e, 3), "max_abs_dP": sig(m, 3)})
+        out["arms"][prec] = {"errors": rows, "seconds": sig(secs),
+                             "krylov_mean": sig(st["krylov_dim_sum"] / max(st["krylov_solves"], 1), 3),
+                             "final_pops": [sig(x, 6) for x in P[-1]]}
+    if len(precs) == 1:
+        out["precision"] = precs[0]
+        out["errors"] = out["arms"][precs[0]]["errors"]
+    return out
 
 
 def run_kernel_case(args):

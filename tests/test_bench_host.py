@@ -194,3 +194,7 @@ def test_long_accuracy_run_with_a_stand_in_engine(monkeypatch, tmp_path):
     assert all(r["max_abs_dP"] > 0 for r in out["errors"])
     assert np.load(tmp_path / "long_mixed.npy").shape == (251, 7)
     assert np.load(tmp_path / "long_fp64ref.npy").shape == (251, 7)
+    args = bench.parse(["--long", "120", "--warmup", "1", "--long-dir", str(tmp_path),
+                        "--long-precisions", "tf32x3,bf16x3"])
+    out = json.loads(json.dumps(bench.run_long(args)))
+    assert sorted(out["arms"]) == ["bf16x3", "tf32x3"] and out["arms"]["bf16x3"]["errors"][0]["step"] == 100

@@ -46,3 +46,21 @@ def test_batched_fmo_realisations_match_single_runs(prec, tol):
         assert rel_pop_err(Pb, Ps) <= tol, (r, rel_pop_err(Pb, Ps))
         single.close()
 
+
+
+def test_batched_fmo_realisations_match_the_oracle():
+    """Two FMO-sized disorder realisations with different bond dimensions in the same launches,
+    one FP64 step: each realisation's populations against its own oracle run (<= 1e-10 relative)."""
+    from oracle import TDVPState, tdvp_ps_step, populations
+    base = wl.fmo_sized()
+    Ds = [16, 24]
+    params = [wl.disorder_realisation(base, r) for r in (3, 7)]
+    eng = _engine(params, Ds, 1e-6, tune=True)
+    eng.step(10.0, precision=pkg.PREC_FP64)
+    for r, (q, D) in enumerate(zip(params, Ds)):
+        st = TDVPState.start(q, D=D)
+        tdvp_ps_step(st, 10.0, rank_rtol=1e-6)
+        err = rel_pop_err(eng.observables(r)[0], populations(st, q))
+        print(f"realisation {r} (D = {D}): relative population error {err:.2e}")
+        assert err <= 1e-10
+    eng.close()
