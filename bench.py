@@ -62,6 +62,9 @@ def parse(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=sorted(PREC),
                     help="arithmetic of the Lanczos matvecs on the timed arm")
+    ap.add_argument("--workload", default="fmo", choices=["fmo", "large"],
+                    help="fmo: 7 x 10 Debye modes with 10 levels (77 sites); large: 20 modes with 16 levels "
+                         "(147 sites)")
     ap.add_argument("--D", type=int, default=64)
     ap.add_argument("--dt", type=float, default=10.0)
     ap.add_argument("--tol", type=float, default=1e-8,
@@ -114,7 +117,7 @@ def parse(argv=None):
 
 def workload(args):
     import workloads as wl
-    p = wl.fmo_sized()
+    p = wl.fmo_sized() if args.workload == "fmo" else wl.fmo_large()
     return p, {"workload": f"{p.name}: {len(p.chain())} sites, D={args.D}, dt={args.dt} fs, product start",
                "sites": len(p.chain()), "bond_dim": args.D, "dt_fs": args.dt, "rank_rtol": args.rank_rtol}
 
