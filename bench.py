@@ -470,7 +470,9 @@ def run_batched(args, R, rank=0, world=1):
     base = wl.fmo_sized()
     choices = tuple(c for c in (32, 48, 64, 96, 128) if c <= args.batched_dmax)
     Ds = wl.ragged_bond_dims(R, choices=choices)
-    mine = shard(R, rank, world)
+    # this rank's realisations, placed in the engine in order of bond dimension: the gauge-shift
+    # QR is launched per run of equal shapes, so equal D side by side share launches
+    mine = sorted(shard(R, rank, world), key=lambda r: (Ds[r], r))
     steps = args.batched_steps or args.steps
     tol = args.tol
     P = PREC[args.precision]
@@ -535,7 +537,8 @@ def run_batched(args, R, rank=0, world=1):
             P1 = one.observables(0)[0]
             one.close()
             worst = max(worst, float(np.max(np.abs(P1 - np.asarray(pops[r]))) / max(np.max(np.abs(P1)), 1e-300)))
-        check = {"realisations": [mine[0], mine[-1]], "steps": nsteps, "max_rel_dP": sig(worst, 3)}
+        check = {"realisations": [mine[0], mine[-1]], "bond_dims": [Ds[mine[0]], Ds[mine[-1]]], "steps": nsteps,
+                 "max_rel_dP": sig(worst, 3)}
     cmp = None
     if args.batched_compare and learned:
         # the following steps without the controller (the library's default test rule), timed

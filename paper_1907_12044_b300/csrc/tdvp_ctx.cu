@@ -901,11 +901,30 @@ int run_qr_timed(tdvp_ctx* ctx, int cat, const Views& v, int dir, int i, int m, 
 }
 
 // dir 0: C_i = L_i D (left-to-right), dir 1: C_i = D R_i (right-to-left); D lands in `bond`
+// Runs of consecutive realisations of a view whose gauge-shift QR at site i (direction dir, 0 =
+// left-to-right, else right-to-left) has the same (m, n) shape.  Ragged realisations differ in
+// cost by ~(D_max/D_min)^3; one launch over all of them with one block count leaves most SMs idle
+// while the largest finish, so every run gets its own launch and block count.
+struct QrRun { int r0, R, m, n; };
+std::vector<QrRun> qr_runs(tdvp_ctx* ctx, const Views& v, int i, int dir) {
+  std::vector<QrRun> runs;
+  const int d = ctx->d[i];
+  for (int q = 0; q < v.R; ++q) {
+    const auto& bd = ctx->rh[v.r0 + q].bd;
+    const int m = dir == 0 ? bd[i] * d : d * bd[i + 1], n = dir == 0 ? bd[i + 1] : bd[i];
+    if (!runs.empty() && runs.back().m == m && runs.back().n == n) runs.back().R++;
+    else runs.push_back(QrRun{q, 1, m, n});
+  }
+  return runs;
+}
+
+Views sub_view(tdvp_ctx* ctx, const Views& v, int q0, int R) {
+  return Views{v.sd + (size_t)q0 * ctx->N, v.wk + q0, R, v.flags + q0, v.r0 + q0};
+}
+
 int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
   PhaseScope ps(ctx, TDVP_PH_QR);
-  const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i];
-  const int mm = dir == 0 ? m.Dl * d : d * m.Dr, nn = dir == 0 ? m.Dr : m.Dl;
   if (ctx->prof) {
     // algorithmic flops of the definition: two Gram-Schmidt passes (dots and updates) per row,
     // 2 n^2 m complex multiply-adds of 8 real flops
@@ -917,7 +936,14 @@ int gauge_qr(tdvp_ctx* ctx, const Views& v, int i, int dir) {
     }
     ctx->stats.prof_flops[TDVP_CAT_QR] += f;
   }
-  return run_qr_timed(ctx, TDVP_CAT_QR, v, dir, i, mm, nn, qr_mode(ctx, v.R, mm, nn), ctx->rank_rtol, 0, 0);
+  for (const QrRun& run : qr_runs(ctx, v, i, dir)) {
+    const Views sv = sub_view(ctx, v, run.r0, run.R);
+    const int rc = run_qr_timed(ctx, TDVP_CAT_QR, sv, dir, i, run.m, run.n, qr_mode(ctx, run.R, run.m, run.n),
+                                ctx->rank_rtol, 0, 0);
+    if (rc) return rc;
+  }
+  (void)d;
+  return TDVP_OK;
 }
 
 int nblk_for(long long n, int cap) {
@@ -1865,81 +1891,75 @@ int tdvp_autotune(tdvp_ctx* ctx) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  // every QR shape of the sweep, timed with each realisation's own site dims in its QR scratch
-  // (the state is not touched) on a random full-rank and a random rank-deficient matrix (rank
-  // n/8): the sweep meets both, and the kernels' row-by-row paths differ in cost
+  // every QR launch of the sweep (one per run of consecutive realisations with equal shape), timed
+  // in the realisations' QR scratch (the state is not touched) on a random full-rank and a random
+  // rank-deficient matrix (rank n/8) of the run's shape: the sweep meets both, and the kernels'
+  // row-by-row paths differ in cost
   for (int i = 0; i < ctx->N; ++i) {
     for (int dir : {0, 3}) {
       if ((dir == 0 && i == ctx->N - 1) || (dir == 3 && i == 0)) continue;
-      const Dims mx = maxdims(ctx, i, v);
-      const int mm = dir == 0 ? mx.Dl * ctx->d[i] : ctx->d[i] * mx.Dr;
-      const int nn = dir == 0 ? mx.Dr : mx.Dl;
-      const auto key = std::make_tuple(ctx->R, mm, nn);
-      if (ctx->qr_tuned.count(key) || nn > 256) continue;
-      // M[kind][r]: n_r x m_r row-major; kind 0 full rank, kind 1 rank max(1, n_r / 8)
-      std::vector<std::vector<zc>> M[2];
-      std::vector<int> nr(ctx->R), mr(ctx->R);
-      for (int r = 0; r < ctx->R; ++r) {
-        const auto& bd = ctx->rh[r].bd;
-        nr[r] = dir == 0 ? bd[i + 1] : bd[i];
-        mr[r] = dir == 0 ? bd[i] * ctx->d[i] : ctx->d[i] * bd[i + 1];
-        const int n = nr[r], m = mr[r], rk = std::max(1, n / 8);
-        M[0].emplace_back((size_t)n * m);
-        for (auto& z : M[0].back()) z = zmake(nd(rng), nd(rng));
-        std::vector<zc> P((size_t)n * rk), Qm((size_t)rk * m);
-        for (auto& z : P) z = zmake(nd(rng), nd(rng));
-        for (auto& z : Qm) z = zmake(nd(rng), nd(rng));
-        M[1].emplace_back((size_t)n * m);
-        for (int a = 0; a < n; ++a)
-          for (int c = 0; c < m; ++c) {
-            zc s = zmake(0, 0);
-            for (int t = 0; t < rk; ++t) s = zfma(P[(size_t)a * rk + t], Qm[(size_t)t * m + c], s);
-            M[1].back()[(size_t)a * m + c] = s;
-          }
-      }
-      std::vector<int> cands;
-      for (int B : {1, 2, 4, 8, 16, 24, 32, 48, 64, 80, 96, 128, 148})
-        if (B <= mm && B <= ctx->qr_cap) cands.push_back(B);
-      for (int C : {1, 2, 4, 8, 16})
-        if (cqr_fits(ctx, C, mm, nn)) cands.push_back(-C);
-      int best_mode = qr_mode(ctx, ctx->R, mm, nn);
-      float best = 1e30f;
-      std::vector<zc> buf;
-      for (int mode : cands) {
-        // the cluster kernel reads the left-to-right shape through its transposed view
-        const bool trans = mode < 0 && dir == 0;
-        const int tdir = dir == 0 ? 4 : 3;
-        float total = 0;
-        for (int kind = 0; kind < 2; ++kind) {
-          float tmin = 1e30f;
-          for (int rep = 0; rep < 2; ++rep) {
-            for (int r = 0; r < ctx->R; ++r) {
-              const int n = nr[r], m = mr[r];
-              const std::vector<zc>& src = M[kind][r];
-              const zc* h = src.data();
-              if (trans) {
-                buf.resize(src.size());
-                for (int a = 0; a < n; ++a)
-                  for (int c = 0; c < m; ++c) buf[(size_t)c * n + a] = src[(size_t)a * m + c];
-                h = buf.data();
-              }
-              CK(cudaMemcpyAsync(ctx->h_work[r].scratch, h, src.size() * sizeof(zc), cudaMemcpyHostToDevice, ctx->st));
-              if (trans) CK(cudaStreamSynchronize(ctx->st));    // buf is reused by the next realisation
+      for (const QrRun& run : qr_runs(ctx, v, i, dir == 0 ? 0 : 1)) {
+        const int mm = run.m, nn = run.n;
+        const auto key = std::make_tuple(run.R, mm, nn);
+        if (ctx->qr_tuned.count(key) || nn > 256) continue;
+        const Views sv = sub_view(ctx, v, run.r0, run.R);
+        // M[kind]: nn x mm row-major; kind 0 full rank, kind 1 rank max(1, nn / 8)
+        std::vector<zc> M[2];
+        {
+          const int rk = std::max(1, nn / 8);
+          M[0].resize((size_t)nn * mm);
+          for (auto& z : M[0]) z = zmake(nd(rng), nd(rng));
+          std::vector<zc> P((size_t)nn * rk), Qm((size_t)rk * mm);
+          for (auto& z : P) z = zmake(nd(rng), nd(rng));
+          for (auto& z : Qm) z = zmake(nd(rng), nd(rng));
+          M[1].assign((size_t)nn * mm, zmake(0, 0));
+          for (int a = 0; a < nn; ++a)
+            for (int c = 0; c < mm; ++c) {
+              zc acc = zmake(0, 0);
+              for (int t = 0; t < rk; ++t) acc = zfma(P[(size_t)a * rk + t], Qm[(size_t)t * mm + c], acc);
+              M[1][(size_t)a * mm + c] = acc;
             }
-            CK(cudaEventRecord(e0, ctx->st));
-            const int rc = run_qr(ctx, v, tdir, i, mm, nn, mode, 1e-13, 0, 0);
-            if (rc) return rc;
-            CK(cudaEventRecord(e1, ctx->st));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            tmin = std::min(tmin, ms);
-          }
-          total += tmin;
         }
-        if (total < best) { best = total; best_mode = mode; }
+        // the cluster kernel reads the left-to-right shape through its transposed view
+        std::vector<zc> MT[2];
+        for (int kind = 0; kind < 2; ++kind) {
+          MT[kind].resize(M[kind].size());
+          for (int a = 0; a < nn; ++a)
+            for (int c = 0; c < mm; ++c) MT[kind][(size_t)c * nn + a] = M[kind][(size_t)a * mm + c];
+        }
+        std::vector<int> cands;
+        for (int B : {1, 2, 4, 8, 16, 24, 32, 48, 64, 80, 96, 128, 148})
+          if (B <= mm && B <= ctx->qr_cap) cands.push_back(B);
+        for (int C : {1, 2, 4, 8, 16})
+          if (cqr_fits(ctx, C, mm, nn)) cands.push_back(-C);
+        int best_mode = qr_mode(ctx, run.R, mm, nn);
+        float best = 1e30f;
+        for (int mode : cands) {
+          const bool trans = mode < 0 && dir == 0;
+          const int tdir = dir == 0 ? 4 : 3;
+          float total = 0;
+          for (int kind = 0; kind < 2; ++kind) {
+            const std::vector<zc>& src = trans ? MT[kind] : M[kind];
+            float tmin = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+              for (int q = 0; q < run.R; ++q)
+                CK(cudaMemcpyAsync(ctx->h_work[v.r0 + run.r0 + q].scratch, src.data(), src.size() * sizeof(zc),
+                                   cudaMemcpyHostToDevice, ctx->st));
+              CK(cudaEventRecord(e0, ctx->st));
+              const int rc = run_qr(ctx, sv, tdir, i, mm, nn, mode, 1e-13, 0, 0);
+              if (rc) return rc;
+              CK(cudaEventRecord(e1, ctx->st));
+              CK(cudaEventSynchronize(e1));
+              float ms = 0;
+              CK(cudaEventElapsedTime(&ms, e0, e1));
+              tmin = std::min(tmin, ms);
+            }
+            total += tmin;
+          }
+          if (total < best) { best = total; best_mode = mode; }
+        }
+        ctx->qr_tuned[key] = best_mode;
       }
-      ctx->qr_tuned[key] = best_mode;
     }
   }
   // the tensor-core GEMMs of the Lanczos matvecs: for every distinct (op, M, N, K) of the chain,
