@@ -108,7 +108,10 @@ def parse(argv=None):
                     help="per-kernel breakdown of one more batched step (launch by launch, CUDA events)")
     ap.add_argument("--long-precisions", default=None,
                     help="comma-separated precisions for the long run (default: --precision), each against "
-                         "the same FP64 reference")
+                         "the same FP64 reference; an entry prec@tol sets that arm's Lanczos tolerance")
+    ap.add_argument("--long-ref", default=None,
+                    help="populations of an earlier FP64 reference run of the same workload (.npy, one row "
+                         "per step) instead of running it again")
     ap.add_argument("--long-dir", default=os.path.join(ROOT, "gpurun_out"),
                     help="where the long run writes its population checkpoints")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
@@ -803,18 +806,28 @@ def run_long(args):
         eng.close()
         return np.array(pops), time.perf_counter() - t0, st
 
-    ref = run_arm("fp64ref", *arm_setup(args, "fp64ref"))
+    if args.long_ref:
+        refP = np.load(args.long_ref)
+        if refP.shape[0] < args.long + 1:
+            raise SystemExit(f"--long-ref holds {refP.shape[0] - 1} steps, fewer than --long {args.long}")
+        ref = (refP[:args.long + 1], None, None)
+    else:
+        ref = run_arm("fp64ref", *arm_setup(args, "fp64ref"))
     out = {"long_run": args.long, "config": cfg, "tol": args.tol,
-           "reference": f"fp64, tol {args.plain_tol:g}, CUDA-graph steps",
-           "reference_seconds": sig(ref[1]), "final_pops_fp64": [sig(x, 6) for x in ref[0][-1]], "arms": {}}
-    for prec in precs:
+           "reference": f"fp64, tol {args.plain_tol:g}, CUDA-graph steps" + (" (stored run)" if args.long_ref else ""),
+           "reference_seconds": sig(ref[1]) if ref[1] else None, "final_pops_fp64": [sig(x, 6) for x in ref[0][-1]],
+           "arms": {}}
+    for entry in precs:
+        prec, _, tol_s = entry.partition("@")
         _, tol, graph, learned, every = arm_setup(args, "mixed")
-        P, secs, st = run_arm("mixed" if len(precs) == 1 else prec, prec, tol, graph, learned, every)
+        tol = float(tol_s) if tol_s else tol
+        P, secs, st = run_arm("mixed" if len(precs) == 1 else entry.replace("@", "_"), prec, tol, graph, learned,
+                              every)
         rows = []
         for s in list(range(100, args.long + 1, 100)) or [args.long]:
             e, m = pop_error(args.dt, P[:s + 1], ref[0][:s + 1])
             rows.append({"step": s, "t_fs": s * args.dt, "eq_error": sig(e, 3), "max_abs_dP": sig(m, 3)})
-        out["arms"][prec] = {"errors": rows, "seconds": sig(secs),
+        out["arms"][entry] = {"errors": rows, "seconds": sig(secs), "precision": prec, "tol": tol,
                              "krylov_mean": sig(st["krylov_dim_sum"] / max(st["krylov_solves"], 1), 3),
                              "final_pops": [sig(x, 6) for x in P[-1]]}
     if len(precs) == 1:

@@ -198,3 +198,8 @@ def test_long_accuracy_run_with_a_stand_in_engine(monkeypatch, tmp_path):
                         "--long-precisions", "tf32x3,bf16x3"])
     out = json.loads(json.dumps(bench.run_long(args)))
     assert sorted(out["arms"]) == ["bf16x3", "tf32x3"] and out["arms"]["bf16x3"]["errors"][0]["step"] == 100
+    # a stored reference and a per-arm tolerance
+    args = bench.parse(["--long", "100", "--warmup", "1", "--long-dir", str(tmp_path / "b"),
+                        "--long-ref", str(tmp_path / "long_fp64ref.npy"), "--long-precisions", "tf32x3@1e-10"])
+    out = json.loads(json.dumps(bench.run_long(args)))
+    assert out["arms"]["tf32x3@1e-10"]["tol"] == 1e-10 and out["reference_seconds"] is None
