@@ -99,6 +99,8 @@ def parse(argv=None):
                          "of the plain FP64 arm from the same start, Eq. error and max |dP| every 100 steps")
     ap.add_argument("--lz-chunks", type=int, default=None, help="chunk cap per Lanczos vector (library option)")
     ap.add_argument("--fused", type=int, default=1, help="0: four Lanczos launches per iteration instead of one")
+    ap.add_argument("--env-fp64", type=int, default=0,
+                    help="1: environment updates in FP64 in the mixed precisions (matvecs on the tensor cores)")
     ap.add_argument("--batched-kmax", type=int, default=48, help="Krylov cap of the batched section")
     ap.add_argument("--batched-check", action="store_true",
                     help="re-run the first and last realisation alone and compare populations")
@@ -233,6 +235,7 @@ def timed_run(args, p, name, world, dev, stream, flush):
     if args.lz_chunks:
         eng.set_option(pkg.OPT_LANCZOS_CHUNKS, args.lz_chunks)
     eng.set_option(pkg.OPT_FUSED_LANCZOS, args.fused)
+    eng.set_option(pkg.OPT_ENV_FP64, args.env_fp64)
     eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1 if every else 0)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
@@ -481,6 +484,7 @@ def run_batched(args, R, rank=0, world=1):
     P = PREC[args.precision]
     eng = pkg.Engine(n_realisations=len(mine), kmax=args.batched_kmax)
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
+    eng.set_option(pkg.OPT_ENV_FP64, args.env_fp64)
     eng.set_option(pkg.OPT_FUSED_LANCZOS, args.fused)
     if args.lz_chunks:
         eng.set_option(pkg.OPT_LANCZOS_CHUNKS, args.lz_chunks)
@@ -624,6 +628,7 @@ def run_e2e(args, p):
     t0 = time.perf_counter()
     eng = pkg.Engine(n_realisations=1)
     eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
+    eng.set_option(pkg.OPT_ENV_FP64, args.env_fp64)
     eng.build_mpo(0, p)
     eng.init_mps(0, args.D, p.exciton_site)
     eng.autotune()
@@ -773,9 +778,10 @@ def run_long(args):
     os.makedirs(args.long_dir, exist_ok=True)
     precs = (args.long_precisions or args.precision).split(",")
 
-    def run_arm(name, prec, tol, graph, learned, every):
+    def run_arm(name, prec, tol, graph, learned, every, env_fp64=0):
         eng = pkg.Engine(n_realisations=1)
         eng.set_option(pkg.OPT_RANK_RTOL, args.rank_rtol)
+        eng.set_option(pkg.OPT_ENV_FP64, env_fp64)
         eng.set_option(pkg.OPT_KRYLOV_CHECK_ALL, 1 if every else 0)
         eng.build_mpo(0, p)
         eng.init_mps(0, args.D, p.exciton_site)
@@ -818,16 +824,19 @@ def run_long(args):
            "reference_seconds": sig(ref[1]) if ref[1] else None, "final_pops_fp64": [sig(x, 6) for x in ref[0][-1]],
            "arms": {}}
     for entry in precs:
-        prec, _, tol_s = entry.partition("@")
+        # entry: prec[@tol][+env64]
+        body, plus, flag = entry.partition("+")
+        prec, _, tol_s = body.partition("@")
         _, tol, graph, learned, every = arm_setup(args, "mixed")
         tol = float(tol_s) if tol_s else tol
-        P, secs, st = run_arm("mixed" if len(precs) == 1 else entry.replace("@", "_"), prec, tol, graph, learned,
-                              every)
+        env64 = 1 if (flag == "env64" or args.env_fp64) else 0
+        P, secs, st = run_arm("mixed" if len(precs) == 1 else entry.replace("@", "_").replace("+", "_"), prec, tol,
+                              graph, learned, every, env64)
         rows = []
         for s in list(range(100, args.long + 1, 100)) or [args.long]:
             e, m = pop_error(args.dt, P[:s + 1], ref[0][:s + 1])
             rows.append({"step": s, "t_fs": s * args.dt, "eq_error": sig(e, 3), "max_abs_dP": sig(m, 3)})
-        out["arms"][entry] = {"errors": rows, "seconds": sig(secs), "precision": prec, "tol": tol,
+        out["arms"][entry] = {"errors": rows, "seconds": sig(secs), "precision": prec, "tol": tol, "env_fp64": env64,
                              "krylov_mean": sig(st["krylov_dim_sum"] / max(st["krylov_solves"], 1), 3),
                              "final_pops": [sig(x, 6) for x in P[-1]]}
     if len(precs) == 1:

@@ -331,6 +331,10 @@ int tdvp_autotune(tdvp_ctx* ctx);
  *     launch has (a participant that never arrives) and limits every wait of that kernel to t, so
  *     the waits run out and the step returns TDVP_ERR_DEVICE_TIMEOUT (nothing faults or hangs; the
  *     context stays usable, the state must be initialised again).  0 (default) = off.
+ *   TDVP_OPT_ENV_FP64: 1 = in the mixed precisions the environment updates (Eq. tdvp1_h1i,
+ *     tdvp1_hiN) stay FP64 and only the Lanczos matvecs run on the tensor cores; 0 (default) = the
+ *     environment updates use the tensor cores too.  An environment error is seen by every H_eff
+ *     of the following sweep, while a matvec error stays inside one Krylov space.
  *   TDVP_OPT_LANCZOS_CHUNKS: at most this many chunks (thread blocks) per Lanczos vector, 1..148
  *     (default 148); fewer chunks make the fused iteration's partial-sum reductions and group
  *     barriers shorter.  Results depend on it only through the summation order. */
@@ -342,6 +346,7 @@ int tdvp_autotune(tdvp_ctx* ctx);
 #define TDVP_OPT_FUSED_LANCZOS     6
 #define TDVP_OPT_STALL_TEST        7
 #define TDVP_OPT_LANCZOS_CHUNKS    8
+#define TDVP_OPT_ENV_FP64          9
 int tdvp_set_option(tdvp_ctx* ctx, int option, double value);
 
 const char* tdvp_last_error(const tdvp_ctx* ctx);

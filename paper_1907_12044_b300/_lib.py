@@ -64,6 +64,7 @@ OPT_PDL = 5
 OPT_FUSED_LANCZOS = 6
 OPT_STALL_TEST = 7
 OPT_LANCZOS_CHUNKS = 8
+OPT_ENV_FP64 = 9
 
 
 class StatsC(C.Structure):

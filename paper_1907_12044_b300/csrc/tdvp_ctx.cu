@@ -65,6 +65,7 @@ struct tdvp_ctx {
   int fused_lz = 1;           // TDVP_OPT_FUSED_LANCZOS: one cooperative launch per Lanczos iteration
   double stall_test = 0.0;    // TDVP_OPT_STALL_TEST: > 0 = failure-path test with this wait limit (s)
   int lz_chunks = TDVP_MAX_VEC_BLOCKS;   // TDVP_OPT_LANCZOS_CHUNKS: chunk cap per Lanczos vector
+  int env_fp64 = 0;           // TDVP_OPT_ENV_FP64: environment updates in FP64 in the mixed precisions
   int lz_cap = 0;             // co-resident blocks of the fused iteration kernel
   // per-launch timing
   // learned Krylov controller
@@ -817,7 +818,7 @@ int env_right_tc(tdvp_ctx* ctx, const Views& v, int i, int pm);
 // tensor cores in the mixed-precision sweep.
 int env_left(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
   PhaseScope ps(ctx, TDVP_PH_GET_ENV);
-  if (P != TDVP_PREC_FP64) return env_left_tc(ctx, v, i, tc_mode(P));
+  if (P != TDVP_PREC_FP64 && !ctx->env_fp64) return env_left_tc(ctx, v, i, tc_mode(P));
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
@@ -830,7 +831,7 @@ int env_left(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
 // Right environment of site i-1 from site i (Eq. tdvp1_hiN); FP64 or on the tensor cores.
 int env_right(tdvp_ctx* ctx, const Views& v, int i, int P = TDVP_PREC_FP64) {
   PhaseScope ps(ctx, TDVP_PH_GET_ENV);
-  if (P != TDVP_PREC_FP64) return env_right_tc(ctx, v, i, tc_mode(P));
+  if (P != TDVP_PREC_FP64 && !ctx->env_fp64) return env_right_tc(ctx, v, i, tc_mode(P));
   const Dims m = maxdims(ctx, i, v);
   const int d = ctx->d[i], Wl = ctx->Wb[i], Wr = ctx->Wb[i + 1];
   int rc;
@@ -2036,6 +2037,10 @@ int tdvp_set_option(tdvp_ctx* ctx, int option, double value) {
       ctx->lz_chunks = c;
       return TDVP_OK;
     }
+    case TDVP_OPT_ENV_FP64:
+      graph_reset(ctx);
+      ctx->env_fp64 = value != 0.0 ? 1 : 0;
+      return TDVP_OK;
     case TDVP_OPT_STALL_TEST:
       if (!(value >= 0.0 && value <= 1.0)) return fail(ctx, TDVP_ERR_INVALID_ARG, "stall test: wait limit in [0, 1] s");
       graph_reset(ctx);
