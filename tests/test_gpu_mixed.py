@@ -118,3 +118,21 @@ def test_mixed_fmo_step_tracks_fp64_oracle():
     err = rel_pop_err(eng.observables(0)[0], populations(st, p))
     print(f"FMO-sized chain, one TF32x3 step: relative population error {err:.2e}")
     assert err <= 1e-5
+
+
+def test_mixed_matvecs_with_fp64_environments_track_the_oracle():
+    """TDVP_OPT_ENV_FP64: the mixed sweep with the environment updates kept in FP64 (only the
+    Lanczos matvecs on the tensor cores) stays on the FP64 oracle like the all-tensor-core sweep."""
+    p = wl.tiny_chain()
+    tens = wl.random_mps_tensors(p.phys_dims(), 16, seed=9)
+    eng = engine_for(p, tensors=tens)
+    eng.set_option(pkg.OPT_ENV_FP64, 1)
+    st = TDVPState.start(p, tensors=tens)
+    worst = 0.0
+    for _ in range(10):
+        eng.step(10.0, precision=pkg.PREC_TF32X3, tol=1e-10)
+        tdvp_ps_step(st, 10.0)
+        worst = max(worst, rel_pop_err(eng.observables(0)[0], populations(st, p)))
+    print(f"tiny chain, TF32x3 with FP64 environments: worst relative population error {worst:.2e}")
+    assert worst <= STEP_TOL[pkg.PREC_TF32X3]
+    eng.close()
