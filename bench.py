@@ -583,7 +583,7 @@ def run_batched(args, R, rank=0, world=1):
     eng.close()
     ms_max = max_over_ranks(ms, world)
     N = len(base.chain())
-    return {"realisations": R, "per_rank": len(mine), "bond_dims": f"ragged from {list(choices)} (seed 12044)",
+    return {"realisations": R, "per_rank": len(mine), "bond_dims": f"ragged {list(choices)}",
             "precision": args.precision, "steps": steps,
             "value": sig((2 * N - 1) * R * steps / (ms_max / 1e3)), "unit": UNIT,
             "ms_per_step": sig(ms_max / steps), "gpu_launches": int(st["kernel_launches"]),
@@ -657,8 +657,7 @@ def run_e2e(args, p):
     return {"value": sig(site_update_rate(N, nsteps, 1, 1e3 * dt)), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d / nsteps), "d2h_bytes_per_step": 8 * (p.n_el + 2),
             "steps": nsteps, "seconds": sig(dt),
-            "includes": "engine, build_mpo (host params), init_mps, autotune, warm-up + controller training, "
-                        "graph capture, steps with a populations/energy/norm read after each"}
+            "includes": "create, build_mpo, init, autotune, warm-up, training, steps + observables"}
 
 
 def oracle_threads():
@@ -883,7 +882,17 @@ def run_kernel_case(args):
                       "device_ms_per_call": dev_ms, "launches_per_call": st["kernel_launches"] / args.steps}))
 
 
+def _compact(x):
+    """Nested dicts without their null entries (the top level keeps every key)."""
+    if isinstance(x, dict):
+        return {k: _compact(v) for k, v in x.items() if v is not None}
+    if isinstance(x, list):
+        return [_compact(v) for v in x]
+    return x
+
+
 def emit(out, args):
+    out = {k: (_compact(v) if isinstance(v, (dict, list)) else v) for k, v in out.items()}
     line = json.dumps(out, ensure_ascii=False)
     print(line, flush=True)
     if args.out:
