@@ -114,8 +114,8 @@ def parse(argv=None):
     ap.add_argument("--long-ref", default=None,
                     help="populations of an earlier FP64 reference run of the same workload (.npy, one row "
                          "per step) instead of running it again")
-    ap.add_argument("--long-dir", default=os.path.join(ROOT, "gpurun_out"),
-                    help="where the long run writes its population checkpoints")
+    ap.add_argument("--long-dir", default=None,
+                    help="where the long run writes its population checkpoints (none if unset)")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args(argv)
 
@@ -774,7 +774,8 @@ def run_long(args):
     import paper_1907_12044_b300 as pkg
     p, cfg = workload(args)
     torch.cuda.set_device(0)
-    os.makedirs(args.long_dir, exist_ok=True)
+    if args.long_dir:
+        os.makedirs(args.long_dir, exist_ok=True)
     precs = (args.long_precisions or args.precision).split(",")
 
     def run_arm(name, prec, tol, graph, learned, every, env_fp64=0):
@@ -800,13 +801,14 @@ def run_long(args):
             eng.set_option(pkg.OPT_GRAPH, 1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        path = os.path.join(args.long_dir, f"long_{name}.npy")
+        path = os.path.join(args.long_dir, f"long_{name}.npy") if args.long_dir else None
         while len(pops) <= args.long:
             eng.step(args.dt, 1, precision=PREC[prec], krylov_mode=mode, tol=tol)
             pops.append(eng.observables(0)[0])
-            if len(pops) % 100 == 1:
+            if path and len(pops) % 100 == 1:
                 np.save(path, np.array(pops))
-        np.save(path, np.array(pops))
+        if path:
+            np.save(path, np.array(pops))
         st = eng.stats()
         eng.close()
         return np.array(pops), time.perf_counter() - t0, st
