@@ -203,3 +203,15 @@ def test_long_accuracy_run_with_a_stand_in_engine(monkeypatch, tmp_path):
                         "--long-ref", str(tmp_path / "long_fp64ref.npy"), "--long-precisions", "tf32x3@1e-10"])
     out = json.loads(json.dumps(bench.run_long(args)))
     assert out["arms"]["tf32x3@1e-10"]["tol"] == 1e-10 and out["reference_seconds"] is None
+
+
+def test_bench_population_error_equals_the_oracle_metric():
+    """bench.pop_error (Eq. error at the last time, trapezoid in time) against the oracle's
+    mean_cumulative_deviation on the same random populations, and max |dP|."""
+    from oracle import mean_cumulative_deviation
+    rng = np.random.default_rng(5)
+    P, Pref = rng.random((41, 7)), rng.random((41, 7))
+    e, m = bench.pop_error(10.0, P, Pref)
+    t = 10.0 * np.arange(41)
+    assert abs(e - mean_cumulative_deviation(t, P, Pref)) <= 1e-15 * max(1.0, e)
+    assert m == np.abs(P - Pref).max()
