@@ -561,7 +561,8 @@ def run_batched(args, R, rank=0, world=1):
         sa = eng.stats()
         cmp = {"adaptive_ms_per_step": sig(ms_ad / steps), "learned_ms_per_step": sig(ms / steps),
                "wall_gain": sig(ms_ad / ms), "tri_evals_per_solve_adaptive":
-               sig(sa["tri_evals"] / max(sa["krylov_solves"], 1), 3)}
+               sig(sa["tri_evals"] / max(sa["krylov_solves"], 1), 3),
+               "krylov_mean_adaptive": sig(sa["krylov_dim_sum"] / max(sa["krylov_solves"], 1), 3)}
     prof = None
     if args.batched_prof:
         # per-kernel CUDA-event breakdown of one more (untimed) step, launch by launch

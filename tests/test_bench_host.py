@@ -178,6 +178,21 @@ def test_batched_and_e2e_sections_with_a_stand_in_engine(monkeypatch):
     assert e["steps"] == args.warmup + args.steps
 
 
+def test_batched_compare_check_and_profile_sections_with_a_stand_in_engine(monkeypatch):
+    _patch(monkeypatch)
+    args = bench.parse(["--steps", "1", "--batched-compare", "--batched-check", "--batched-prof"])
+    b, _ = bench.run_batched(args, 4)
+    b = json.loads(json.dumps(b))
+    cmp = b["controller_vs_default"]
+    for k in ("adaptive_ms_per_step", "learned_ms_per_step", "wall_gain", "tri_evals_per_solve_adaptive",
+              "krylov_mean_adaptive"):
+        assert k in cmp and cmp[k] > 0, k
+    chk = b["check_vs_single"]                  # smallest and largest D of this rank's realisations
+    assert len(chk["realisations"]) == 2 and set(chk["realisations"]) <= set(range(4))
+    assert chk["bond_dims"][0] <= chk["bond_dims"][1] and chk["max_rel_dP"] >= 0
+    assert b["profile"]["phase_ms"] and b["profile"]["kernel_ms"]
+
+
 def test_realisation_shards_cover_every_index_once():
     for R, world in ((256, 8), (32, 3), (5, 8), (1, 2)):
         got = sorted(r for rank in range(world) for r in bench.shard(R, rank, world))
