@@ -94,7 +94,11 @@ def canonicalize_right(tensors):
     """Right-canonical form by LQ from the last site to the first (Eq. QR, "RQ").
 
     Returns new tensors with sites 1..N-1 right-canonical and the centre at site 0,
-    normalised to ||Psi|| = 1.
+    normalised to ||Psi|| = 1.  The carried tensor is rescaled to unit norm after each
+    absorbed factor: the norm of a product of generic tensors grows or shrinks
+    geometrically with the chain length and would leave the float64 range on long
+    chains, while a positive scale changes neither the right-canonical factors (the
+    LQ of s*C is (s*Dm) Qr) nor the normalised state.
     """
     mps = [np.array(t, dtype=complex) for t in tensors]
     for i in range(len(mps) - 1, 0, -1):
@@ -102,7 +106,7 @@ def canonicalize_right(tensors):
         Dm, Qr = lq_rr(mps[i].reshape(Dl, d * Dr))
         mps[i] = Qr.reshape(Dl, d, Dr)
         mps[i - 1] = np.einsum("asb,bc->asc", mps[i - 1], Dm)
-    mps[0] = mps[0] / np.linalg.norm(mps[0])
+        mps[i - 1] = mps[i - 1] / np.linalg.norm(mps[i - 1])
     return mps
 
 

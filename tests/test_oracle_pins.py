@@ -193,6 +193,27 @@ def test_product_mps_is_right_canonical_product_state():
         assert np.allclose(mps_to_dense(mps), product_state(p))
 
 
+def test_right_canonicalisation_keeps_the_state_and_survives_any_scale():
+    """canonicalize_right (Eq. QR, right-to-left): sites 1..N-1 right-canonical (Eq. rcanon), the
+    dense state equal to the raw tensors' product divided by its norm (no phase: every LQ factor
+    has a positive diagonal), and tensors scaled by 1e70 each (a product of 1e420, beyond the
+    float64 range, on this 6-site chain) give the same tensors."""
+    p = wl.tiny_chain()
+    d = p.phys_dims()
+    assert len(d) == 6
+    tens = wl.random_mps_tensors(d, 6, seed=15)
+    psi = mps_to_dense(tens)
+    psi = psi / np.linalg.norm(psi)
+    mps = canonicalize_right(tens)
+    for A in mps[1:]:
+        M = A.reshape(A.shape[0], -1)
+        assert np.allclose(M @ M.conj().T, np.eye(A.shape[0]), atol=1e-13)
+    assert np.allclose(mps_to_dense(mps), psi, atol=1e-12)
+    big = canonicalize_right([1e70 * t for t in tens])
+    for A, B in zip(mps, big):
+        assert np.all(np.isfinite(B)) and np.allclose(A, B, atol=1e-12)
+
+
 def _dense_heff(p, mps, i):
     """P^H H P for the site projector of site i, from the dense H (no environments)."""
     H = hamiltonian_kron(p)
