@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import paper_1907_12044_b300 as pkg
-from oracle import TDVPState, populations, energy
+from oracle import TDVPState, populations, energy, canonicalize_right, qr_rr, env_left, env_right
 
 
 # Relative error bounds of one mixed-precision contraction, ||y - y_ref|| / ||y_ref||: 10 u of
@@ -31,17 +31,32 @@ def engine_for(params, D=None, tensors=None, R=1, kmax=64):
     return eng
 
 
-def oracle_from_gpu_tensors(params, mps):
-    """Oracle state over the given (right-canonical, centre at 0) tensors, with oracle-built envs."""
-    st = TDVPState.start(params, D=1)
-    st.mps = [np.array(a) for a in mps]
-    from oracle.mps import env_right
-    N = len(st.mps)
-    st.Renv = [None] * N
-    st.Renv[N - 1] = np.ones((1, 1, 1), complex)
-    for i in range(N - 1, 0, -1):
-        st.Renv[i - 1] = env_right(st.Renv[i], st.mps[i], st.W[i])
-    return st
+def oracle_centred(params, tensors, site):
+    """The oracle's own mixed-canonical form of the start tensors with the centre at `site`, and
+    the environments of that site, computed from the seeded tensors alone (nothing from the CUDA
+    path): right-canonicalised by LQ (Eq. QR, right to left), then the centre moved right by QR
+    shifts (Eq. QR), the environments built from these tensors (Eq. tdvp1_h1i, tdvp1_hiN).
+    Returns (mps, W, L, R)."""
+    W = TDVPState.start(params, D=1).W
+    mps = canonicalize_right(tensors)
+    for i in range(site):
+        Dl, d, Dr = mps[i].shape
+        Q, Rm = qr_rr(mps[i].reshape(Dl * d, Dr))
+        mps[i] = Q.reshape(Dl, d, Dr)
+        mps[i + 1] = np.einsum("ab,bsc->asc", Rm, mps[i + 1])
+    L = np.ones((1, 1, 1), complex)
+    for j in range(site):
+        L = env_left(L, mps[j], W[j])
+    R = np.ones((1, 1, 1), complex)
+    for j in range(len(mps) - 1, site, -1):
+        R = env_right(R, mps[j], W[j])
+    return mps, W, L, R
+
+
+def gauge_err(gpu_mps, mps, sites):
+    """max over the given sites of max |A_gpu - A| / max |A| (the canonical form is unique for
+    full-rank tensors: every QR factor has a positive diagonal)."""
+    return max(float(np.abs(gpu_mps[i] - mps[i]).max() / np.abs(mps[i]).max()) for i in sites)
 
 
 def rel_pop_err(P, Pref):

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import heff_apply, h0_apply, env_left, env_right, TDVPState, tdvp_ps_step, populations
+from oracle import heff_apply, h0_apply, TDVPState, tdvp_ps_step, populations
 
 pytestmark = pytest.mark.gpu
 
@@ -22,29 +22,26 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_1907_12044_b300 as pkg  # noqa: E402
-from gpu_util import engine_for, rel_pop_err, MIXED_TOL as TOL, PREC_NAME as NAME, rel_err as _rel  # noqa: E402
+from gpu_util import (engine_for, oracle_centred, gauge_err, rel_pop_err, MIXED_TOL as TOL,  # noqa: E402
+                      PREC_NAME as NAME, rel_err as _rel)
 
 
 @pytest.fixture(scope="module")
 def c1_random():
     p = wl.fmo_sized()
     tens = wl.random_mps_tensors(p.phys_dims(), 64, seed=21)
-    return p, engine_for(p, tensors=tens)
+    return p, engine_for(p, tensors=tens), tens
 
 
 @pytest.mark.parametrize("site", [0, 1, 5, 38, 76])
 def test_mixed_heff_matches_oracle(c1_random, site):
-    p, eng = c1_random
-    W = TDVPState.start(p, D=1).W
+    """H_eff x in every mixed mode against the oracle's contraction over its own gauge and
+    environments (built from the seeded tensors alone)."""
+    p, eng, tens = c1_random
+    mps, W, L, R = oracle_centred(p, tens, site)
     eng.move_center(0, site)
     try:
-        mps = eng.get_mps(0)
-        L = np.ones((1, 1, 1), complex)
-        for j in range(site):
-            L = env_left(L, mps[j], W[j])
-        R = np.ones((1, 1, 1), complex)
-        for j in range(len(mps) - 1, site, -1):
-            R = env_right(R, mps[j], W[j])
+        assert gauge_err(eng.get_mps(0), mps, sorted({0, site, len(mps) - 1})) <= 1e-10
         rng = np.random.default_rng(100 + site)
         x = rng.normal(size=mps[site].shape) + 1j * rng.normal(size=mps[site].shape)
         yo = heff_apply(L, W[site], R, x)
@@ -61,24 +58,20 @@ def test_mixed_heff_matches_oracle(c1_random, site):
 
 @pytest.mark.parametrize("bond", [0, 4, 40, 75])
 def test_mixed_zero_site_matches_oracle(c1_random, bond):
-    p, eng = c1_random
-    W = TDVPState.start(p, D=1).W
-    mps0 = eng.get_mps(0)                         # centre at 0: sites > bond right-canonical
-    R = np.ones((1, 1, 1), complex)
-    for j in range(len(mps0) - 1, bond, -1):
-        R = env_right(R, mps0[j], W[j])
+    """H0 on the bond (bond, bond + 1): the oracle's left environment through site `bond` (centre
+    moved to bond + 1) and right environment of the sites after `bond` (centre at bond)."""
+    p, eng, tens = c1_random
+    _, _, _, R = oracle_centred(p, tens, bond)
+    mps1, W, L, _ = oracle_centred(p, tens, bond + 1)
     eng.move_center(0, bond + 1)
     try:
-        mps1 = eng.get_mps(0)                     # sites <= bond left-canonical
-        L = np.ones((1, 1, 1), complex)
-        for j in range(bond + 1):
-            L = env_left(L, mps1[j], W[j])
+        assert gauge_err(eng.get_mps(0), mps1, sorted({0, bond, bond + 1})) <= 1e-10
         Db = mps1[bond].shape[2]
         rng = np.random.default_rng(7 + bond)
         x = rng.normal(size=(Db, Db)) + 1j * rng.normal(size=(Db, Db))
         yo = h0_apply(L, R, x)
         y64 = eng.apply_h0(0, bond, x, precision=pkg.PREC_FP64)
-        assert _rel(y64, yo) <= 1e-12
+        assert _rel(y64, yo) <= 1e-11
         for prec in pkg.MIXED_PRECISIONS:
             e = _rel(eng.apply_h0(0, bond, x, precision=prec), yo)
             print(f"bond {bond}: {NAME[prec]} rel err {e:.2e}")
