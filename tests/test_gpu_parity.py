@@ -113,31 +113,32 @@ def test_qr_rank_deficient_matches_oracle(c1_random, qr_kernel):
 # ------------------------------------------------------------------ H_eff and Lanczos at full size
 
 @pytest.mark.parametrize("site", [0, 5, 38, 76])
-def test_heff_and_expm_match_oracle_at_c1_sites(c1_random, site):
+def test_heff_and_expm_match_oracle_at_c1_sites(site):
     """The oracle builds its own gauge and environments from the seeded tensors; the device's
     gauge after the same shifts, H_eff x and the exponential of the oracle's centre tensor are
-    compared with them."""
-    p, eng = c1_random
-    mps, W, L, R = oracle_centred(p, wl.random_mps_tensors(p.phys_dims(), 64, seed=21), site)
+    compared with them.  A fresh context per site: moving the centre out and back re-gauges the
+    sites it passes, so only a context that has made exactly the oracle's shifts holds its gauge."""
+    p = wl.fmo_sized()
+    tens = wl.random_mps_tensors(p.phys_dims(), 64, seed=21)
+    mps, W, L, R = oracle_centred(p, tens, site)
+    eng = engine_for(p, tensors=tens)
     eng.move_center(0, site)
-    try:
-        assert gauge_err(eng.get_mps(0), mps, sorted({0, max(site - 1, 0), site, len(mps) - 1})) <= 1e-10
-        rng = np.random.default_rng(site)
-        x = rng.normal(size=mps[site].shape) + 1j * rng.normal(size=mps[site].shape)
-        y = eng.apply_heff(0, site, x)
-        yo = heff_apply(L, W[site], R, x)
-        assert np.abs(y - yo).max() <= 1e-11 * np.abs(yo).max()
-        C = mps[site]
-        tau = 10.0 * PHASE_PER_CM_FS / 2
-        out, k = eng.debug_expm(0, site, -1j * tau, 1e-12, C)
-        ks = []
-        outo = lanczos_expm(lambda v: heff_apply(L, W[site], R, v), C, -1j * tau, 1e-12, 64, stats=ks)
-        # the Krylov dimension at which the a-posteriori estimate first meets the tolerance may
-        # differ near its rounding floor; the exponentials themselves must agree
-        assert 1 <= k <= 64 and 1 <= ks[0] <= 64
-        assert np.abs(out - outo).max() <= 1e-10 * np.abs(outo).max()
-    finally:
-        eng.center_to_zero(0)
+    assert gauge_err(eng.get_mps(0), mps, sorted({0, max(site - 1, 0), site, len(mps) - 1})) <= 1e-10
+    rng = np.random.default_rng(site)
+    x = rng.normal(size=mps[site].shape) + 1j * rng.normal(size=mps[site].shape)
+    y = eng.apply_heff(0, site, x)
+    yo = heff_apply(L, W[site], R, x)
+    assert np.abs(y - yo).max() <= 1e-11 * np.abs(yo).max()
+    C = mps[site]
+    tau = 10.0 * PHASE_PER_CM_FS / 2
+    out, k = eng.debug_expm(0, site, -1j * tau, 1e-12, C)
+    ks = []
+    outo = lanczos_expm(lambda v: heff_apply(L, W[site], R, v), C, -1j * tau, 1e-12, 64, stats=ks)
+    # the Krylov dimension at which the a-posteriori estimate first meets the tolerance may
+    # differ near its rounding floor; the exponentials themselves must agree
+    assert 1 <= k <= 64 and 1 <= ks[0] <= 64
+    assert np.abs(out - outo).max() <= 1e-10 * np.abs(outo).max()
+    eng.close()
 
 
 @pytest.mark.parametrize("x_target", [30.0, 250.0, 1500.0, 6000.0])
