@@ -85,7 +85,7 @@ def parse(argv=None):
     ap.add_argument("--no-graph", action="store_true", help="launch by launch instead of CUDA-graph steps")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the step's kernels in plain stream order (no programmatic dependent launch)")
-    ap.add_argument("--kernel-case", choices=["heff", "qr"], default=None,
+    ap.add_argument("--kernel-case", choices=["heff", "qr", "ozaki"], default=None,
                     help="time one hot operation at the bench's full-size shapes instead of steps (for "
                          "kernel captures): heff = one H_eff matvec at a bath-mode site of a random D-bond "
                          "state, qr = one gauge-shift QR of a rank-8 640 x 64 matrix")
@@ -885,6 +885,55 @@ def run_kernel_case(args):
                       "device_ms_per_call": dev_ms, "launches_per_call": st["kernel_launches"] / args.steps}))
 
 
+def run_ozaki_case(args):
+    """The FP64 complex GEMM emulated on the BF16 tensor cores (tdvp_zgemm_ozaki) against cuBLAS
+    ZGEMM (torch.matmul on complex128, the FP64 library GEMM) on the same device operands: CUDA
+    events per call over --steps calls after --warmup, FLOP rate at 8 m n k, and the largest
+    difference from the ZGEMM result relative to its largest element."""
+    import torch
+    import paper_1907_12044_b300 as pkg
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device=dev).manual_seed(1907)
+    rows = []
+    for (m, n, k) in ((640, 64, 64), (1024, 1024, 1024), (4096, 4096, 4096)):
+        A = torch.randn(m, k, dtype=torch.complex128, device=dev, generator=gen)
+        B = torch.randn(k, n, dtype=torch.complex128, device=dev, generator=gen)
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / args.steps
+        Cref = torch.empty(m, n, dtype=torch.complex128, device=dev)
+        ms_ref = timed(lambda: torch.matmul(A, B, out=Cref))
+        row = {"m": m, "n": n, "k": k, "zgemm_ms": round(ms_ref, 4),
+               "zgemm_tflops": round(8.0 * m * n * k / (ms_ref * 1e-3) / 1e12, 3), "ozaki": {}}
+        for sl in (8, 6):
+            wsb = pkg.zgemm_ozaki_workspace(m, n, k, sl)
+            ws = torch.empty(wsb // 8 + 128, dtype=torch.float64, device=dev)
+            wp = (ws.data_ptr() + 1023) // 1024 * 1024
+            C = torch.empty(m, n, dtype=torch.complex128, device=dev)
+            call = lambda: pkg.zgemm_ozaki(m, n, k, A.data_ptr(), B.data_ptr(), C.data_ptr(), sl, wp, wsb,
+                                           stream.cuda_stream)
+            ms = timed(call)
+            pkg.zgemm_ozaki_status(wp, stream.cuda_stream)
+            rel = float((C - Cref).abs().max() / Cref.abs().max())
+            row["ozaki"][f"slices{sl}"] = {"ms": round(ms, 4), "tflops_fp64_equiv": round(8.0 * m * n * k / (ms * 1e-3) / 1e12, 3),
+                                           "speedup_vs_zgemm": round(ms_ref / ms, 2), "max_rel_diff": float(f"{rel:.2e}")}
+            del ws, C
+        rows.append(row)
+        del A, B, Cref
+        torch.cuda.empty_cache()
+    print(json.dumps({"kernel_case": "ozaki", "calls": args.steps, "warmup": args.warmup, "cases": rows}))
+
+
 def _compact(x):
     """Nested dicts without their null entries (the top level keeps every key)."""
     if isinstance(x, dict):
@@ -910,7 +959,9 @@ def main():
         e = pkg.Engine()
         e.set_option(pkg.OPT_PDL, 0)     # process-wide
         e.close()
-    if args.kernel_case:
+    if args.kernel_case == "ozaki":
+        run_ozaki_case(args)
+    elif args.kernel_case:
         run_kernel_case(args)
         return
     if args.long:

@@ -30,6 +30,8 @@
 #ifndef TDVP_H
 #define TDVP_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -258,6 +260,34 @@ void tdvp_reset_stats(tdvp_ctx* ctx);
  * GPU (other streams, other host threads) race and give wrong results; serialise them.
  * Returns TDVP_ERR_DEVICE_TIMEOUT if a bounded device-side wait gave up. */
 int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* cuda_stream);
+
+/* FP64 complex GEMM emulated on the BF16 tensor cores (Ozaki splitting).  The paper's FP64
+ * contractions (Eq. tdvp1_H, the absorption C_{i+1} = D_i R_{i+1} after Eq. QR) are complex GEMMs
+ * on B300's FP64 pipe, which is far slower than its tensor cores; this computes the same product
+ * from exact BF16 pieces of the operands.
+ *
+ * C = A B with A (m x k), B (k x n), C (m x n): complex, row-major, interleaved (re, im) doubles,
+ * device memory, 16-byte aligned.  Method: the complex product as the real product
+ * [[Ar, -Ai], [Ai, Ar]] [Br; Bi]; every row of the left factor and column of the right one scaled
+ * by a power of two below 1 in magnitude and cut into `slices` (1..8) integer slices of 7 bits
+ * (exact in BF16); the slice products of total order < slices accumulated exactly in FP32 tensor
+ * memory over windows of 128 K values and summed in a float-float register pair.  Error per
+ * element <= 2k (slices + 3) 2^(-7 slices) 2^(eR + fc) + ~2^-47 k 2^(eR + fc), where 2^eR and
+ * 2^fc are the powers of two just above max|A row| and max|B column| (slices = 8: ~1e-14 of
+ * k max|A_r| max|B_c|).  Integer inputs of at most 7 bits per row scale are exact at slices = 1.
+ *
+ * Workspace: `workspace` (device, 1024-byte aligned, at least tdvp_zgemm_ozaki_workspace(m, n, k,
+ * slices) bytes; 0 means invalid sizes) holds the slices, the scale exponents and an error word;
+ * it is owned by the caller, who must not share it between calls in flight.  No allocation.
+ * Asynchronous on `cuda_stream`; the buffers must not overlap (checked on the host).
+ * Limits: 1 <= m, k <= 2^21, 1 <= n <= 2^28, 4 m k <= 2^36, 2 k n <= 2^36, 1 <= slices <= 8;
+ * otherwise TDVP_ERR_INVALID_ARG without touching the device.  Every device-side wait is bounded
+ * (1 s); tdvp_zgemm_ozaki_status() synchronises the stream and returns TDVP_ERR_DEVICE_TIMEOUT if a
+ * wait of the last call on this workspace gave up (C is then not written), else TDVP_OK. */
+size_t tdvp_zgemm_ozaki_workspace(int m, int n, int k, int slices);
+int tdvp_zgemm_ozaki(int m, int n, int k, const double* A, const double* B, double* C, int slices,
+                     void* workspace, size_t workspace_bytes, void* cuda_stream);
+int tdvp_zgemm_ozaki_status(const void* workspace, void* cuda_stream);
 
 /* Learned Krylov controller (not in the paper): a two-layer MLP, 8 features -> 64 -> 64, ReLU,
  * FP32, with two heads on the second hidden layer: the Krylov dimension y (linear) and the logit a

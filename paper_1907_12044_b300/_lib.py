@@ -34,6 +34,7 @@ EXPORTED_SYMBOLS = [
     "tdvp_lq_noalloc", "tdvp_apply_h0", "tdvp_set_option", "tdvp_autotune",
     "tdvp_controller_set_weights", "tdvp_controller_get_weights", "tdvp_controller_logging",
     "tdvp_controller_log", "tdvp_controller_train", "tdvp_controller_loss_grad",
+    "tdvp_zgemm_ozaki_workspace", "tdvp_zgemm_ozaki", "tdvp_zgemm_ozaki_status",
 ]
 
 
@@ -123,6 +124,10 @@ def load_library():
     lib.tdvp_controller_train.argtypes = [P, C.c_int, C.c_int, C.c_float, fp]
     lib.tdvp_controller_loss_grad.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, fp]
     lib.tdvp_lq_noalloc.argtypes = [C.c_int, C.c_int, P, P, P, P]
+    lib.tdvp_zgemm_ozaki_workspace.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.tdvp_zgemm_ozaki_workspace.restype = C.c_size_t
+    lib.tdvp_zgemm_ozaki.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, C.c_int, P, C.c_size_t, P]
+    lib.tdvp_zgemm_ozaki_status.argtypes = [P, P]
     lib.tdvp_reset_stats.argtypes = [P]
     lib.tdvp_reset_stats.restype = None
     lib.tdvp_last_error.argtypes = [P]
@@ -336,6 +341,28 @@ class Engine:
 
     def reset_stats(self):
         self.lib.tdvp_reset_stats(self._h)
+
+
+def zgemm_ozaki_workspace(m, n, k, slices):
+    """Bytes of device workspace tdvp_zgemm_ozaki needs (0: sizes out of its limits)."""
+    return int(load_library().tdvp_zgemm_ozaki_workspace(int(m), int(n), int(k), int(slices)))
+
+
+def zgemm_ozaki(m, n, k, a_ptr, b_ptr, c_ptr, slices, ws_ptr, ws_bytes, stream):
+    """C = A B (complex FP64, device pointers as ints) emulated on the BF16 tensor cores with
+    `slices` 7-bit slices per operand; see tdvp_zgemm_ozaki in include/tdvp.h.  Asynchronous."""
+    rc = load_library().tdvp_zgemm_ozaki(int(m), int(n), int(k), C.c_void_p(a_ptr), C.c_void_p(b_ptr),
+                                         C.c_void_p(c_ptr), int(slices), C.c_void_p(ws_ptr), int(ws_bytes),
+                                         C.c_void_p(stream))
+    if rc != 0:
+        raise TDVPError(rc, "tdvp_zgemm_ozaki failed")
+
+
+def zgemm_ozaki_status(ws_ptr, stream):
+    """Synchronise the stream; raise TDVPError if a device wait of the last call gave up."""
+    rc = load_library().tdvp_zgemm_ozaki_status(C.c_void_p(ws_ptr), C.c_void_p(stream))
+    if rc != 0:
+        raise TDVPError(rc, "tdvp_zgemm_ozaki: device wait timed out")
 
 
 def lq_noalloc(n, m, x_ptr, q_ptr, l_ptr, stream):

@@ -75,3 +75,27 @@ def test_noalloc_lq_rejects_overlapping_buffers_before_touching_the_device():
             pkg.lq_noalloc(n, m, x, q, l, 0)
         assert e.value.code == -1
     assert lb < xb
+
+
+def test_ozaki_gemm_rejects_bad_arguments_before_touching_the_device():
+    """tdvp_zgemm_ozaki checks sizes, slice count, workspace size and alignment, 16-byte operand
+    alignment and overlap on the host before any CUDA call (the pointers are never dereferenced)."""
+    assert pkg.zgemm_ozaki_workspace(0, 4, 4, 8) == 0
+    assert pkg.zgemm_ozaki_workspace(4, 4, 4, 0) == 0 and pkg.zgemm_ozaki_workspace(4, 4, 4, 9) == 0
+    assert pkg.zgemm_ozaki_workspace(4, 4, (1 << 21) + 1, 8) == 0
+    m, n, k = 40, 30, 20
+    wsb = pkg.zgemm_ozaki_workspace(m, n, k, 8)
+    assert wsb > 0 and wsb % 1024 == 0
+    A, B, C, W = 1 << 24, 1 << 25, 1 << 26, 1 << 30
+    cases = [
+        dict(slices=0), dict(slices=9), dict(ws_bytes=wsb - 1), dict(a=0), dict(w=0),
+        dict(w=W + 512),                       # workspace not 1024-byte aligned
+        dict(a=A + 8),                         # operand not 16-byte aligned
+        dict(c=A + 16),                        # C overlaps A
+        dict(w=B),                             # workspace overlaps B
+    ]
+    for cs in cases:
+        with pytest.raises(pkg.TDVPError) as e:
+            pkg.zgemm_ozaki(m, n, k, cs.get("a", A), cs.get("b", B), cs.get("c", C), cs.get("slices", 8),
+                            cs.get("w", W), cs.get("ws_bytes", wsb), 0)
+        assert e.value.code == -1, cs
