@@ -243,7 +243,9 @@ def timed_run(args, p, name, world, dev, stream, flush):
     pops = [eng.observables(0)[0]]
     if learned:
         eng.controller_logging(1 << 20)
-    for _ in range(args.warmup - (1 if graph else 0)):
+    # the launch-by-launch warm-up steps (at least one when the controller learns from them), then
+    # the graph capture step
+    for _ in range(max(1 if learned else 0, args.warmup - (1 if graph else 0))):
         eng.step(args.dt, 1, precision=P, tol=tol)
         pops.append(eng.observables(0)[0])
     ctl = None
@@ -499,7 +501,7 @@ def run_batched(args, R, rank=0, world=1):
     if learned:
         eng.controller_logging(1 << 22)
     nsteps = 0
-    for _ in range(args.warmup - (1 if graph else 0)):
+    for _ in range(max(1 if learned else 0, args.warmup - (1 if graph else 0))):
         eng.step(args.dt, 1, precision=P, tol=tol)
         nsteps += 1
     mode = pkg.KRYLOV_ADAPTIVE
@@ -636,7 +638,7 @@ def run_e2e(args, p):
     if learned:
         eng.controller_logging(1 << 20)
     nsteps = 0
-    for _ in range(args.warmup - (1 if graph else 0)):
+    for _ in range(max(1 if learned else 0, args.warmup - (1 if graph else 0))):
         eng.step(args.dt, 1, precision=P, tol=tol)
         eng.observables(0)
         nsteps += 1
@@ -961,7 +963,8 @@ def main():
         e.close()
     if args.kernel_case == "ozaki":
         run_ozaki_case(args)
-    elif args.kernel_case:
+        return
+    if args.kernel_case:
         run_kernel_case(args)
         return
     if args.long:
