@@ -945,8 +945,15 @@ def _compact(x):
     return x
 
 
+# headline comparisons, written last so that they sit in the end of the line a log keeps
+TAIL_KEYS = ("speedup_vs_fp64", "speedup_vs_plain_fp64", "pop_error_vs_fp64", "pop_error_vs_fp64_arm",
+             "controller_gain")
+
+
 def emit(out, args):
     out = {k: (_compact(v) if isinstance(v, (dict, list)) else v) for k, v in out.items()}
+    out = {**{k: v for k, v in out.items() if k not in TAIL_KEYS},
+           **{k: out[k] for k in TAIL_KEYS if k in out}}
     line = json.dumps(out, ensure_ascii=False)
     print(line, flush=True)
     if args.out:

@@ -164,6 +164,19 @@ def test_bench_line_is_complete_with_a_stand_in_engine(monkeypatch):
     assert len(json.dumps(out)) < 4000
 
 
+def test_headline_comparisons_close_the_line(monkeypatch, tmp_path, capsys):
+    """A log that keeps only the end of the line still holds the mixed-vs-FP64 comparisons."""
+    _patch(monkeypatch)
+    args = bench.parse(["--batched", "0", "--no-e2e", "--no-cpu-baseline", "--out", str(tmp_path / "l.json")])
+    out, _ = bench.run_ours(args, 0, 1)
+    out["cpu_baseline"] = {"value": 1.0, "unit": bench.UNIT, "cores": 1, "kind": "oracle", "sample": "x" * 300}
+    bench.emit(out, args)
+    line = capsys.readouterr().out.strip().splitlines()[-1]
+    assert list(json.loads(line))[-len(bench.TAIL_KEYS):] == list(bench.TAIL_KEYS)
+    for k in bench.TAIL_KEYS:
+        assert f'"{k}"' in line[-1500:], k
+
+
 def test_batched_and_e2e_sections_with_a_stand_in_engine(monkeypatch):
     _patch(monkeypatch)
     args = bench.parse(["--steps", "2"])
