@@ -274,7 +274,8 @@ int tdvp_lq_noalloc(int n, int m, const double* X, double* Q, double* L, void* c
  * memory over windows of 128 K values and summed in a float-float register pair.  Error per
  * element <= 2k (slices + 3) 2^(-7 slices) 2^(eR + fc) + ~2^-47 k 2^(eR + fc), where 2^eR and
  * 2^fc are the powers of two just above max|A row| and max|B column| (slices = 8: ~1e-14 of
- * k max|A_r| max|B_c|).  Integer inputs of at most 7 bits per row scale are exact at slices = 1.
+ * k max|A_r| max|B_c|).  Operands whose parts are integers of magnitude below 128 give the exact
+ * product with slices = 1 (as long as its elements stay below 2^24).
  *
  * Workspace: `workspace` (device, 1024-byte aligned, at least tdvp_zgemm_ozaki_workspace(m, n, k,
  * slices) bytes; 0 means invalid sizes) holds the slices, the scale exponents and an error word;
