@@ -17,8 +17,8 @@ The operations, each written from its equation:
 * one RK4 step (Eq. RK4) for the time-independent Frenkel-Holstein H.
 
 Readings (the paper does not fix them):
-* k_i and the stage states are compressed after each operation ("after each operation ...
-  compressed"); the final combination Psi + tau/6 (k1 + 2 k2 + 2 k3 + k4) is formed as one
+* every k_i and every stage state is compressed before it is used again (Sec. II.A.1 asks for
+  a compression after each operation); the final combination Psi + tau/6 (k1 + 2 k2 + 2 k3 + k4) is formed as one
   block-diagonal sum of the five MPSs (Eq. mps+mps with five blocks) and compressed once;
 * the canonicalisation QR is numpy's reduced QR (no rank decision: a bond larger than the
   rank of its matrix shrinks to min(rows, columns), and the SVD then drops the zero
@@ -116,8 +116,8 @@ def svd_compress(mps, M, zeta=0.0):
 
 
 def compress(mps, M, zeta=0.0):
-    """Canonicalisation followed by compression (Sec. II.A.1: "canonicalisation should be
-    carried out before the actual compression")."""
+    """Canonicalisation followed by compression: the sum or MPO product is not canonical, and
+    Sec. II.A.1 canonicalises it before the SVD sweep."""
     return svd_compress(canonicalise_left(mps), M, zeta)
 
 
