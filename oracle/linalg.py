@@ -84,7 +84,8 @@ def lanczos_expm(matvec, v, z, tol=1e-12, kmax=60, dim=None, stats=None):
     against every earlier Krylov vector) builds V_k and T_k; the result is
     ||v|| V_k exp(z T_k) e_1.  The Krylov dimension grows until the a-posteriori
     estimate ||v|| beta_k |[exp(z T_k) e_1]_k| is <= tol, or k reaches kmax or the
-    dimension of the space (reading of "until Psi(t+tau) converges").
+    dimension of the space (the paper stops the iteration once the evolved state has
+    converged, Sec. II.A.2; this estimate is the reading of that test).
     """
     shape = v.shape
     v = np.asarray(v, dtype=complex).reshape(-1)
